@@ -1,0 +1,114 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests, the oracle's tests and the benchmark.
+
+This module holds input recipes only (initial order-parameter and velocity fields and the
+workload parameter sets); none of the scheme's arithmetic lives here. Arrays are FP64,
+shaped (nz, ny, nx) with x fastest; vector fields carry a leading axis of 3.
+
+The static droplet profile is Eq. initial_droplet of arXiv:2407.12263 (Sec. 3.1):
+phi = 1/2 [1 + tanh(2 (|z| - D/2) / delta)], so phi = 0 inside the droplet.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+CS2 = 1.0 / 3.0
+
+# Workloads. Lattice units throughout; tau_phi follows from M (M = tau_phi cs^2).
+WORKLOADS = {
+    # 2D static droplet, D2Q9, 64x64 periodic, R = 16, xi = 4, 5000 steps (FP64 oracle size).
+    "droplet2d_64": dict(Q=9, grid=(64, 64, 1), R=16.0, xi=4.0, sigma=1e-3, tau_f=0.8, tau_g=0.8,
+                         M=0.02, rho_ratio=1.0, mu_ratio=1.0, body_force=(0.0, 0.0, 0.0), steps=5000),
+    # 3D static droplet, D3Q19, 128^3 periodic, R = 24, xi = 4 (the measured workload).
+    "droplet3d_128": dict(Q=19, grid=(128, 128, 128), R=24.0, xi=4.0, sigma=1e-3, tau_f=0.8,
+                          tau_g=0.8, M=0.02, rho_ratio=1.0, mu_ratio=1.0,
+                          body_force=(0.0, 0.0, 0.0), steps=5000),
+}
+
+
+def cell_coords(grid):
+    """Integer cell-centre coordinates (x, y, z) broadcast to (nz, ny, nx)."""
+    nx, ny, nz = grid
+    z, y, x = np.meshgrid(np.arange(nz, dtype=np.float64), np.arange(ny, dtype=np.float64),
+                          np.arange(nx, dtype=np.float64), indexing="ij")
+    return x, y, z
+
+
+def periodic_distance(grid, centre):
+    """Minimum-image distance of every cell centre from `centre` on the periodic grid."""
+    nx, ny, nz = grid
+    x, y, z = cell_coords(grid)
+    d2 = np.zeros_like(x)
+    for coord, c, n in ((x, centre[0], nx), (y, centre[1], ny), (z, centre[2], nz)):
+        if n == 1:
+            continue
+        dd = np.abs(coord - c)
+        dd = np.minimum(dd, n - dd)
+        d2 += dd * dd
+    return np.sqrt(d2)
+
+
+def droplet_phi(grid, radius, xi, centre=None):
+    """Static droplet (Eq. initial_droplet): phi = 0 inside, 1 outside, tanh interface of width xi."""
+    nx, ny, nz = grid
+    if centre is None:
+        centre = ((nx - 1) / 2.0, (ny - 1) / 2.0, (nz - 1) / 2.0 if nz > 1 else 0.0)
+    r = periodic_distance(grid, centre)
+    return 0.5 * (1.0 + np.tanh(2.0 * (r - radius) / xi))
+
+
+def slab_phi(grid, half_width, xi, axis=0, centre=None):
+    """Planar slab of phi = 0 between two flat interfaces normal to `axis` (1D tanh profile)."""
+    n = grid[axis]
+    if centre is None:
+        centre = (n - 1) / 2.0
+    coords = cell_coords(grid)[axis]
+    d = np.abs(coords - centre)
+    d = np.minimum(d, n - d)
+    return 0.5 * (1.0 + np.tanh(2.0 * (d - half_width) / xi))
+
+
+def droplet_workload_phi(name):
+    w = WORKLOADS[name]
+    return droplet_phi(w["grid"], w["R"], w["xi"])
+
+
+def multi_droplet_phi(grid, seed, count, r_range, xi):
+    """Seeded union of `count` droplets with radii in r_range (phi = product of the profiles)."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = grid
+    phi = np.ones((nz, ny, nx))
+    for _ in range(count):
+        c = (rng.uniform(0, nx), rng.uniform(0, ny), rng.uniform(0, nz) if nz > 1 else 0.0)
+        phi *= droplet_phi(grid, rng.uniform(*r_range), xi, centre=c)
+    return phi
+
+
+def smooth_velocity(grid, seed, amplitude, modes=3):
+    """Seeded smooth periodic velocity field: a few random Fourier modes per component."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = grid
+    x, y, z = cell_coords(grid)
+    u = np.zeros((3, nz, ny, nx))
+    dims = 3 if nz > 1 else 2
+    for a in range(dims):
+        for _ in range(modes):
+            kx, ky = rng.integers(-2, 3, size=2)
+            kz = rng.integers(-2, 3) if nz > 1 else 0
+            ph = rng.uniform(0, 2 * np.pi)
+            amp = amplitude * rng.uniform(0.3, 1.0) / modes
+            u[a] += amp * np.sin(2 * np.pi * (kx * x / nx + ky * y / ny + kz * z / max(nz, 1)) + ph)
+    return u
+
+
+def shear_wave(grid, amplitude, axis_u=0, axis_k=1, k=1):
+    """u_axis_u = A sin(2 pi k x_axis_k / L): a single decaying shear mode."""
+    coords = cell_coords(grid)
+    L = grid[axis_k]
+    u = np.zeros((3,) + coords[0].shape)
+    u[axis_u] = amplitude * np.sin(2 * np.pi * k * coords[axis_k] / L)
+    return u
+
+
+def sine_phi(grid, mean, amplitude, axis=0, k=1):
+    coords = cell_coords(grid)
+    return mean + amplitude * np.sin(2 * np.pi * k * coords[axis] / grid[axis])
