@@ -1,0 +1,359 @@
+#!/usr/bin/env python3
+"""Benchmark of the difference-free conservative phase-field LBM step on GB300.
+
+Prints ONE JSON line (rank 0). A "step" is one lattice update of the whole grid: one launch
+of the fused difference-free kernel (the finite-difference variant, timed beside it, takes two
+launches). The workload is the 3D static droplet: D3Q19, 128^3 periodic, R = 24, xi = 4,
+sigma = 1e-3, density and viscosity ratio 1, tau_f = 0.8, M = 0.02, FP32 populations.
+
+  value        MLUPS = cells x steps / (seconds x 1e6), populations resident in HBM, CUDA events
+               on the stream the kernel runs on; whole-job aggregate over ranks
+  roofline     algorithmic bytes per launch (2 x 2 x 19 x 4 B = 304 B per cell) / mean launch time,
+               against the measured HBM copy bandwidth
+  e2e          the same metric through the C ABI with host buffers: init from a pinned host phi0,
+               the steps, moments and mass back to pinned host arrays, all inside the timed region
+  fd           the finite-difference variant of the same step on the same GPU
+  cpu_baseline the FP64 oracle on the host cores (bounded sample) and the GPU's error against it
+
+--impl reference times the oracle alone (the reference arm of this metric). With --gpus N > 1
+(launched by torchrun) every rank advances its own replica of the workload (the method needs no
+exchange between independent replicas); rank 0 prints the aggregate over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+from paper_2407_12263_gb300 import inputs as I  # noqa: E402
+
+METRIC = "MLUPS and % of HBM roofline, 1 GB300, vs same-GPU FD variant & FP32 at stated error"
+WORKLOAD = "droplet3d_128"
+BYTES_PER_CELL = {"df": 2 * 2 * 19 * 4, "fd": 2 * 2 * 19 * 4 + 19 * 4 + 4 + 4}
+PROFILE = ROOT / "profiles" / "step_kernel_droplet3d_128.md"
+KERNEL_SOURCES = ["paper_2407_12263_gb300/csrc/cell.cuh", "paper_2407_12263_gb300/csrc/lattice.cuh",
+                  "paper_2407_12263_gb300/csrc/step_kernels.cu", "paper_2407_12263_gb300/csrc/lbm_internal.h"]
+
+
+# ---------------------------------------------------------------- multi-rank helpers (host logic)
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def aggregate_mlups(cells: int, steps: int, seconds_max: float, world: int) -> float:
+    """Whole-job MLUPS: every rank advanced its own `cells` for `steps`; time is the slowest rank's."""
+    return cells * steps * world / (seconds_max * 1e6)
+
+
+# ---------------------------------------------------------------- clocks
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.path = Path(tempfile.mkstemp(suffix=".csv")[1])
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={CLOCK_QUERY}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(gpu_index)], stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = [r.split(",") for r in self.path.read_text().strip().splitlines() if r.strip()]
+        self.path.unlink(missing_ok=True)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, name in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- profile summary (traffic)
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        h.update((ROOT / rel).read_bytes())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, or None when the
+    kernel sources changed since that capture."""
+    if not PROFILE.exists():
+        return None
+    text = PROFILE.read_text()
+    m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    m_traffic = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_traffic or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_traffic.group(1))
+
+
+def measured_peak_hbm():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        return float(json.loads(p.read_text())["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl")
+    torch.cuda.set_device(local)
+    from paper_2407_12263_gb300 import build as cuda_build
+    from paper_2407_12263_gb300 import lbm
+    cuda_build.build()
+    lbm.load()
+
+    w = I.WORKLOADS[args.workload]
+    grid = w["grid"]
+    cells = grid[0] * grid[1] * grid[2]
+    phi0 = I.droplet_phi(grid, w["R"], w["xi"])
+    params = dict(tau_f=w["tau_f"], tau_g=w["tau_g"], M=w["M"], xi=w["xi"], sigma=w["sigma"],
+                  rho_ratio=w["rho_ratio"], mu_ratio=w["mu_ratio"], body_force=w["body_force"])
+    stream = torch.cuda.Stream()
+
+    def timed(scheme, steps, warmup, sampler=None):
+        g = lbm.Lattice(grid, w["Q"], scheme=scheme, stream=stream.cuda_stream, **params)
+        g.init_phi(phi0)
+        m0 = g.mass()[0]
+        g.step(warmup)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clocks = sampler() if sampler else None
+        barrier(world)
+        torch.cuda.synchronize()
+        n0 = g.launch_count
+        ev0.record(stream)
+        g.step(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        launches = g.launch_count - n0
+        secs = ev0.elapsed_time(ev1) / 1e3
+        clk = clocks.stop() if clocks else None
+        m1 = g.mass()[0]
+        g.close()
+        return secs, launches, clk, abs(m1 - m0) / m0
+
+    t_df, launches, clk, drift = timed(0, args.steps, args.warmup, sampler=lambda: ClockSampler(local))
+    t_df = max_over_ranks(t_df, world)
+    t_fd, fd_launches, _, fd_drift = timed(1, args.steps, args.warmup)
+    t_fd = max_over_ranks(t_fd, world)
+    value = aggregate_mlups(cells, args.steps, t_df, world)
+    fd_value = aggregate_mlups(cells, args.steps, t_fd, world)
+
+    peak, peak_kind = measured_peak_hbm()
+    launch_s = t_df / args.steps  # one fused kernel per step
+    achieved = BYTES_PER_CELL["df"] * cells / launch_s / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": profiled_traffic(),
+                "peak_kind": peak_kind, "bytes_per_cell": BYTES_PER_CELL["df"],
+                "kernel": "step_kernel<19, difference-free>"}
+
+    e2e = run_e2e(lbm, torch, grid, w, params, phi0, cells, args, world)
+
+    out = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(t_df / args.steps * 1e3, 5), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"{args.workload}: D3Q19 {grid[0]}x{grid[1]}x{grid[2]} periodic static droplet "
+                                  f"R={w['R']:g} xi={w['xi']:g} sigma={w['sigma']:g}, density/viscosity ratio 1, "
+                                  f"tau_f={w['tau_f']}, M={w['M']} (tau_phi=0.06), Courant 0.997",
+                      "lattice": "D3Q19", "scheme": "difference-free", "storage": "fp32",
+                      "l2": "working set 638 MB > 129 MB L2: no flush needed",
+                      "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+           "roofline": roofline, "e2e": e2e, "gpu_launches": launches,
+           "clocks": clk,
+           "fd": {"value": round(fd_value, 1), "unit": "MLUPS", "ms_per_step": round(t_fd / args.steps * 1e3, 5),
+                  "gpu_launches": fd_launches, "bytes_per_cell": BYTES_PER_CELL["fd"],
+                  "hbm_frac": round(BYTES_PER_CELL["fd"] * cells / (t_fd / args.steps) / 1e9 / peak, 4)},
+           "df_vs_fd": round(value / fd_value, 4),
+           "sum_phi_drift": {"df": drift, "fd": fd_drift, "steps": args.warmup + args.steps}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"], out["accuracy"] = run_cpu_baseline(lbm, grid, w, params, phi0, cells, args)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_e2e(lbm, torch, grid, w, params, phi0, cells, args, world):
+    """Through the C ABI with host buffers: pinned phi0 in, the steps, moments and mass out."""
+    shape = phi0.shape
+    pin = lambda n: torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+    phi_h = pin(phi0.size).reshape(shape)
+    phi_h[...] = phi0
+    phi_o, p_o, u_o = pin(phi0.size).reshape(shape), pin(phi0.size).reshape(shape), pin(3 * phi0.size).reshape((3,) + shape)
+    g = lbm.Lattice(grid, w["Q"], **params)
+    g.init_phi(phi_h)                 # warm the handle (staging allocation, module load)
+    g.step(args.warmup)
+    lbm.lbm_moments(g.h, phi_o, p_o, u_o)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.init_phi(phi_h)
+    g.step(args.steps)
+    lbm.lbm_moments(g.h, phi_o, p_o, u_o)
+    s = g.mass()
+    t1 = time.perf_counter()
+    g.close()
+    secs = max_over_ranks(t1 - t0, world)
+    h2d = phi0.size * 8
+    d2h = 5 * phi0.size * 8 + 16
+    return {"value": round(aggregate_mlups(cells, args.steps, secs, world), 1), "unit": "MLUPS",
+            "h2d_bytes_per_step": round(h2d / args.steps, 1), "d2h_bytes_per_step": round(d2h / args.steps, 1),
+            "seconds": round(secs, 4), "sum_phi": s[0]}
+
+
+def run_cpu_baseline(lbm, grid, w, params, phi0, cells, args):
+    """The FP64 oracle on the host cores over full-grid steps of the workload (bounded to about
+    args.cpu_seconds), and the GPU's error against it after the same steps."""
+    import oracle
+    oracle.build()
+    ref = oracle.Oracle(w["Q"], grid, **params)
+    ref.init_phi(phi0)
+    t0 = time.perf_counter()
+    ref.step(1)
+    one = time.perf_counter() - t0
+    k = max(1, min(50, int(args.cpu_seconds / max(one, 1e-3)) - 1))
+    t0 = time.perf_counter()
+    ref.step(k)
+    secs = time.perf_counter() - t0
+    n = k + 1
+    cpu = {"value": round(cells * k / secs / 1e6, 3), "unit": "MLUPS", "cores": oracle.num_threads(),
+           "kind": "oracle", "sample": f"{k} full-grid steps of {WORKLOAD} (FP64 C, OpenMP over rows), "
+                                       f"{secs:.1f} s"}
+    g = lbm.Lattice(grid, w["Q"], **params)
+    g.init_phi(phi0)
+    g.step(n)
+    phi_g, p_g, u_g = g.moments()
+    g.close()
+    phi_o, p_o, u_o = ref.moments()
+    acc = {"steps": n, "max_abs_phi": float(np.abs(phi_g - phi_o).max()),
+           "rel_l2_u": float(np.linalg.norm(u_g - u_o) / np.linalg.norm(u_o)),
+           "max_abs_p": float(np.abs(p_g - p_o).max()),
+           "bounds": {"max_abs_phi": 1e-4, "rel_l2_u": 1e-3, "sum_phi_drift": 1e-7}}
+    return cpu, acc
+
+
+# ---------------------------------------------------------------- reference arm: the oracle
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    w = I.WORKLOADS[args.workload]
+    grid = w["grid"]
+    params = dict(tau_f=w["tau_f"], tau_g=w["tau_g"], M=w["M"], xi=w["xi"], sigma=w["sigma"],
+                  rho_ratio=w["rho_ratio"], mu_ratio=w["mu_ratio"], body_force=w["body_force"])
+    full = I.droplet_phi(grid, w["R"], w["xi"])
+    # each step: one update of a periodic slab cut through the droplet centre, sized so that the
+    # whole --warmup + --steps run takes about args.ref_seconds
+    def slab(nz):
+        z0 = grid[2] // 2 - nz // 2
+        return np.ascontiguousarray(full[z0:z0 + nz])
+
+    probe = oracle.Oracle(w["Q"], (grid[0], grid[1], 3), **params)
+    probe.init_phi(slab(3))
+    t0 = time.perf_counter()
+    probe.step(2)
+    per_cell = (time.perf_counter() - t0) / (2 * grid[0] * grid[1] * 3)
+    budget = args.ref_seconds / max(1, args.steps + args.warmup)
+    nz = int(max(3, min(grid[2], budget / (per_cell * grid[0] * grid[1]))))
+    sub = (grid[0], grid[1], nz)
+    o = oracle.Oracle(w["Q"], sub, **params)
+    o.init_phi(slab(nz))
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    secs = time.perf_counter() - t0
+    cells = sub[0] * sub[1] * sub[2]
+    value = cells * args.steps / secs / 1e6
+    sample = f"each step updates a {sub[0]}x{sub[1]}x{sub[2]} periodic slab cut through the droplet centre"
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "MLUPS", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(secs / args.steps * 1e3, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{args.workload} (oracle sample: {sample})", "lattice": "D3Q19",
+                      "scheme": "difference-free"},
+           "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": oracle.num_threads(),
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(I.WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=90.0)
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.workload != WORKLOAD:
+        ap.error("the benchmark line is defined on droplet3d_128 only")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,150 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) difference-free conservative phase-field
+ * lattice Boltzmann solver (Zhao, Patel & Lee, arXiv:2407.12263).
+ *
+ * One handle owns one periodic lattice (D2Q9 or D3Q19) and its device state: the
+ * post-collision populations f* (one-fluid pressure PDF, Sec. 2.2) and g* (conservative
+ * phase-field PDF, Sec. 2.3), FP32, structure-of-arrays planes [Q][nz][ny][nx] with x
+ * fastest, in two ping-pong copies. Every step is one fused stream-collide kernel launch
+ * (difference-free scheme), or two launches for the finite-difference variant.
+ *
+ * Units are lattice units: dx = 1 and dt = 1 in every collision, moment and forcing
+ * formula; the Courant number only enters the Lax-Wendroff propagation (Sec. 2.2).
+ * Fluid 2 (phi = 0) has density 1 and dynamic viscosity eta2 = tau_f / 3; fluid 1
+ * (phi = 1) has density rho_ratio and viscosity mu_ratio * eta2.
+ *
+ * Host arrays passed to or from the library are FP64, owned by the caller, never
+ * retained, and laid out like the device planes: scalar fields have nx*ny*nz entries with
+ * x fastest; vector fields are 3 such planes (x, y, z components). Population arrays are
+ * Q planes in the velocity order given below.
+ *
+ * Velocity order. D2Q9 follows Sec. 2.2: 0 rest; 1..4 = (1,0), (0,1), (-1,0), (0,-1);
+ * 5..8 = (1,1), (-1,1), (-1,-1), (1,-1). D3Q19: 0 rest; 1..6 = +x, -x, +y, -y, +z, -z;
+ * 7..18 = (1,1,0), (-1,-1,0), (1,-1,0), (-1,1,0), (1,0,1), (-1,0,-1), (1,0,-1), (-1,0,1),
+ * (0,1,1), (0,-1,-1), (0,1,-1), (0,-1,1). Weights follow the speed: 4/9, 1/9, 1/36 (D2Q9)
+ * and 1/3, 1/18, 1/36 (D3Q19).
+ *
+ * Errors: every call returns an lbm_status; nothing throws across the ABI. The message
+ * of the last failure on a handle is available from lbm_last_error(handle) until the next
+ * call on that handle; failures of lbm_create are reported by lbm_last_error(NULL) on the
+ * calling thread. A handle must not be used from two host threads at once. Calls that
+ * return data to the host synchronise the handle's stream; lbm_step does not, so a fault
+ * in an asynchronous launch surfaces at the next synchronising call.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+enum lbm_lattice { LBM_D2Q9 = 9, LBM_D3Q19 = 19 };
+
+enum lbm_status {
+    LBM_OK = 0,
+    LBM_EINVAL = -1,     /* an argument is out of range or inconsistent */
+    LBM_ENOMEM = -2,     /* a device allocation failed */
+    LBM_ECUDA = -3,      /* a CUDA runtime call or kernel launch failed */
+    LBM_ENONFINITE = -4, /* the state holds a NaN or an infinity */
+    LBM_ETIMEOUT = -5,   /* a bounded device-side wait gave up */
+    LBM_ESTATE = -6      /* the call needs lbm_init_phi (or lbm_set_pops) first */
+};
+
+enum lbm_scheme {
+    LBM_SCHEME_DIFFERENCE_FREE = 0, /* grad phi and n from the central moment K1 (Sec. 2.3) */
+    LBM_SCHEME_FINITE_DIFFERENCE = 1 /* isotropic central difference of phi (Sec. 3.4) */
+};
+
+typedef struct {
+    int scheme;     /* enum lbm_scheme; default difference-free */
+    int storage;    /* 0 = FP32 populations (the only storage built) */
+    double courant; /* Lax-Wendroff Courant number c, 0 < c <= 1; default 0.997 (Sec. 2.2) */
+    int walls;      /* 0 = fully periodic (the only boundary built) */
+    void *stream;   /* cudaStream_t the handle launches on; NULL = a stream the handle owns */
+} lbm_opts;
+
+/* Fill *opts with the defaults above. */
+void lbm_default_opts(lbm_opts *opts);
+
+/*
+ * Create a handle and allocate its device state (no kernel runs).
+ *   grid[3]    nx, ny, nz; nx, ny >= 3; D2Q9 needs nz = 1, D3Q19 nz >= 3; nz <= 65535;
+ *              nx*ny*nz < 2^31.
+ *   lattice    LBM_D2Q9 or LBM_D3Q19.
+ *   tau_f      relaxation time tau_rho of fluid 2 (Eq. c-n_m), > 0; nu2 = tau_f / 3.
+ *   tau_g, M   phase-field relaxation time and mobility, related by M = tau_phi cs^2 dt
+ *              (Sec. 2.3). If M > 0 it fixes tau_phi = 3 M; otherwise tau_phi = tau_g > 0.
+ *   xi         interface thickness delta of Eq. cac, >= 2.
+ *   sigma      surface tension of Eq. surface, >= 0.
+ *   rho_ratio  rho1 / rho2 (> 0); mu_ratio eta1 / eta2 (> 0). Local viscosity
+ *              eta(phi) = eta2 + (eta1 - eta2) phi and tau_rho = eta / (rho / 3).
+ *   body_force G of Eq. body (3 components; NULL = 0; the z component must be 0 for D2Q9).
+ *   opts       NULL = defaults.
+ * Returns LBM_OK and *out, or LBM_EINVAL / LBM_ENOMEM / LBM_ECUDA with *out = NULL.
+ */
+int lbm_create(lbm_ctx **out, const int grid[3], int lattice, double tau_f, double tau_g,
+               double M, double xi, double sigma, double rho_ratio, double mu_ratio,
+               const double body_force[3], const lbm_opts *opts);
+
+/*
+ * Initial state from the order parameter (host FP64, nx*ny*nz), an optional velocity
+ * (3 host planes, NULL = rest) and a uniform pressure p0 > 0. Builds the post-collision
+ * populations f* = f^eq(p0, u0, rho(phi0), Pi_s) (Eq. geq_s) and
+ * g* = g^eq(phi0, u0, S0) - t_i (tau_phi - 1/2) e_i . grad phi0 (Eq. geq), with grad phi0
+ * the isotropic central difference of phi0 and n0 = grad phi0 / |grad phi0|. Synchronous.
+ */
+int lbm_init_phi(lbm_ctx *ctx, const double *phi0, const double *u0, double p0);
+
+/* Advance n >= 0 time steps (asynchronous on the handle's stream). */
+int lbm_step(lbm_ctx *ctx, int n);
+
+/*
+ * Macroscopic fields of the current state: phi, p and u computed from the propagated
+ * populations exactly as the next step computes them before colliding (phi = sum g_i,
+ * Eq. momentum, Eq. pressure). Any output may be NULL. Synchronous.
+ */
+int lbm_moments(lbm_ctx *ctx, double *phi, double *p, double *u);
+
+/*
+ * grad phi and the unit normal n of the current state as the scheme computes them:
+ * from K1 (Sec. 2.3, Eq. norm) or from the isotropic central difference (Sec. 3.4).
+ * 3 host planes each; either may be NULL. Synchronous.
+ */
+int lbm_gradients(lbm_ctx *ctx, double *grad_phi, double *normal);
+
+/*
+ * Global sums over the propagated current state: sum phi and sum rho phi (the mass
+ * m = sum rho phi dx^3 of Sec. 3.3), accumulated in FP64 on the device. Also scans every
+ * stored population and returns LBM_ENONFINITE if one is not finite. Synchronous.
+ */
+int lbm_mass(lbm_ctx *ctx, double *sum_phi, double *sum_rho_phi);
+
+/* Copy the post-collision populations f*, g* to / from host FP64 arrays (Q planes each;
+ * either pointer of lbm_get_pops may be NULL). lbm_set_pops also marks the state
+ * initialised. Synchronous. */
+int lbm_get_pops(lbm_ctx *ctx, double *f, double *g);
+int lbm_set_pops(lbm_ctx *ctx, const double *f, const double *g);
+
+/* Kernel launches issued by this handle since creation (one per step for the
+ * difference-free scheme, two for the finite-difference variant, plus auxiliaries). */
+long long lbm_launch_count(const lbm_ctx *ctx);
+
+/* tau_phi the handle resolved from (tau_g, M). */
+double lbm_tau_phi(const lbm_ctx *ctx);
+
+/* The velocity set the CUDA path uses: d, e[Q][3] (row-major) and weights w[Q]; any output
+ * may be NULL. Host-only (needs no GPU). LBM_EINVAL for an unknown lattice. */
+int lbm_lattice_tables(int lattice, int *d, int *e, double *w);
+
+/* Message of the last failure (see the error notes above); never NULL. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* Free the handle and its device memory; NULL is a no-op. Synchronises the stream. */
+void lbm_destroy(lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,271 @@
+// aux_kernels.cu -- initialisation, field output, FP64 mass reduction and population
+// conversion for the difference-free conservative phase-field LBM (arXiv:2407.12263).
+// None of these runs inside the time-step loop.
+#include "cell.cuh"
+
+namespace lbm {
+
+constexpr int kAuxBX = 32, kAuxBY = 4;
+
+// ---------------------------------------------------------------------------------------
+// Initial post-collision populations (FP64 arithmetic, stored FP32):
+//   grad phi0 = 3 sum_{i != 0} t_i e_i phi0(x + e_i)   (isotropic central difference)
+//   n0 = grad phi0 / |grad phi0|, S0 = 4 phi0 (1 - phi0) / delta n0, rho0 = rho2 + drho phi0
+//   f*_i = f^eq_i(p0, u0, rho0, Pi_s0)                                   (Eq. geq_s)
+//   g*_i = g^eq_i(phi0, u0, S0) - t_i (tau_phi - 1/2) e_i . grad phi0     (Eq. geq)
+// The g term is the first-order non-equilibrium part a relaxed state carries after collision,
+// so the first K1 already points along -grad phi for any tau_phi.
+// ---------------------------------------------------------------------------------------
+template <int Q>
+__global__ void init_kernel(const Params P, int z0, const double* __restrict__ phi0s,
+                            const double* __restrict__ u0s, double p0, float* __restrict__ f,
+                            float* __restrict__ g) {
+    const int x = blockIdx.x * kAuxBX + threadIdx.x;
+    const int y = blockIdx.y * kAuxBY + threadIdx.y;
+    const int zl = blockIdx.z;
+    if (x >= P.nx || y >= P.ny) return;
+    const int nzs = gridDim.z;
+    const int ls = (zl + 1) * P.nxy + y * P.nx + x;  // this cell in the staged phi0 slab
+    const double phi = phi0s[ls];
+
+    double gx = 0.0, gy = 0.0, gz = 0.0;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const int xx = (x + Lat<Q>::cx(i) + P.nx) % P.nx;
+        const int yy = (y + Lat<Q>::cy(i) + P.ny) % P.ny;
+        const int ll = (zl + 1 + Lat<Q>::cz(i)) * P.nxy + yy * P.nx + xx;
+        const double v = Lat<Q>::wd(i) * phi0s[ll];
+        gx += Lat<Q>::cx(i) * v;
+        gy += Lat<Q>::cy(i) * v;
+        gz += Lat<Q>::cz(i) * v;
+    }
+    gx *= 3.0;
+    gy *= 3.0;
+    gz *= 3.0;
+    const double g2 = gx * gx + gy * gy + gz * gz;
+    const double gn = sqrt(g2);
+    const double inv = (g2 > 1e-24) ? 1.0 / gn : 0.0;
+    const double n[3] = {gx * inv, gy * inv, gz * inv};
+    const double smag = P.four_over_delta_d * phi * (1.0 - phi);
+    const double S[3] = {smag * n[0], smag * n[1], smag * n[2]};
+    const double rho = P.rho2_d + P.drho_d * phi;
+    const size_t slab = (size_t)nzs * P.nxy;
+    const int lu = zl * P.nxy + y * P.nx + x;
+    const double u[3] = {u0s ? u0s[lu] : 0.0, u0s ? u0s[slab + lu] : 0.0, u0s ? u0s[2 * slab + lu] : 0.0};
+    const double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const double sg = P.sigma_d * gn;
+    const double trc = (double)Lat<Q>::D - (n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+
+    const size_t N = (size_t)P.N;
+    const size_t c = (size_t)(z0 + zl) * P.nxy + (size_t)y * P.nx + x;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const double t = Lat<Q>::wd(i);
+        const double eu = Lat<Q>::cx(i) * u[0] + Lat<Q>::cy(i) * u[1] + Lat<Q>::cz(i) * u[2];
+        const double en = Lat<Q>::cx(i) * n[0] + Lat<Q>::cy(i) * n[1] + Lat<Q>::cz(i) * n[2];
+        const double es = Lat<Q>::cx(i) * S[0] + Lat<Q>::cy(i) * S[1] + Lat<Q>::cz(i) * S[2];
+        const double eg = Lat<Q>::cx(i) * gx + Lat<Q>::cy(i) * gy + Lat<Q>::cz(i) * gz;
+        const double gam = 3.0 * eu + 4.5 * eu * eu - 1.5 * u2;
+        const double pis = sg * ((double)Lat<Q>::e2(i) - en * en - trc / 3.0);
+        const double feq_shifted = t * (3.0 * p0 - P.w0d + rho * gam - 4.5 * pis);
+        const double gstar = t * (phi * (1.0 + gam) + P.tau_phi_d * es) - t * (P.tau_phi_d - 0.5) * eg;
+        f[i * N + c] = (float)feq_shifted;
+        g[i * N + c] = (float)gstar;
+    }
+}
+
+cudaError_t launch_init(const Params& P, int z0, int nzs, const double* phi0s, const double* u0s,
+                        double p0, float* f, float* g, cudaStream_t s) {
+    const dim3 grid((P.nx + kAuxBX - 1) / kAuxBX, (P.ny + kAuxBY - 1) / kAuxBY, nzs), block(kAuxBX, kAuxBY);
+    if (P.Q == 9) init_kernel<9><<<grid, block, 0, s>>>(P, z0, phi0s, u0s, p0, f, g);
+    else init_kernel<19><<<grid, block, 0, s>>>(P, z0, phi0s, u0s, p0, f, g);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Fields of the propagated current state (the values the next step collides with).
+// Output slab layout: 11 FP64 planes of nzs * nxy values: phi, p, u(3), grad phi(3), n(3).
+// ---------------------------------------------------------------------------------------
+template <int Q, int SCHEME, bool GEN>
+__global__ void moments_kernel(const Params P, int z0, const float* __restrict__ f,
+                               const float* __restrict__ g, const float* __restrict__ phi_fd, int mask,
+                               double* __restrict__ out) {
+    const int x = blockIdx.x * kAuxBX + threadIdx.x;
+    const int y = blockIdx.y * kAuxBY + threadIdx.y;
+    const int zl = blockIdx.z;
+    if (x >= P.nx || y >= P.ny) return;
+    const int z = z0 + zl;
+    const Nbr nb = make_nbr(P, x, y, z);
+    const int c = (z * P.ny + y) * P.nx + x;
+    float fb[Q], gb[Q];
+    pull<Q, true>(P, f, g, c, nb, fb, gb);
+    Macro m;
+    macro_flow<Q, GEN>(P, fb, gb, m);
+    if (SCHEME == SCHEME_DF) {
+        macro_interface_df<Q>(P, gb, m);
+    } else {
+        float gx, gy, gz;
+        fd_gradient<Q>(phi_fd, c, nb, gx, gy, gz);
+        macro_interface_fd(P, gx, gy, gz, m);
+    }
+    macro_pressure<Q, GEN>(P, fb, m);
+    const size_t slab = (size_t)gridDim.z * P.nxy;
+    const size_t l = (size_t)zl * P.nxy + (size_t)y * P.nx + x;
+    if (mask & 1) out[l] = (double)m.phi;
+    if (mask & 2) out[slab + l] = (P.w0d + (double)m.P) / 3.0;  // p = cs^2 (w0 + P)
+    for (int a = 0; a < 3; ++a) {
+        if (mask & 4) out[(2 + a) * slab + l] = (double)m.u[a];
+        if (mask & 8) out[(5 + a) * slab + l] = (double)m.gphi[a];
+        if (mask & 16) out[(8 + a) * slab + l] = (double)m.n[a];
+    }
+}
+
+template <int Q, int SCHEME>
+static void moments_q(const Params& P, int z0, int nzs, const float* f, const float* g, const float* phi,
+                      int mask, double* out, cudaStream_t s) {
+    const dim3 grid((P.nx + kAuxBX - 1) / kAuxBX, (P.ny + kAuxBY - 1) / kAuxBY, nzs), block(kAuxBX, kAuxBY);
+    if (P.general) moments_kernel<Q, SCHEME, true><<<grid, block, 0, s>>>(P, z0, f, g, phi, mask, out);
+    else moments_kernel<Q, SCHEME, false><<<grid, block, 0, s>>>(P, z0, f, g, phi, mask, out);
+}
+
+cudaError_t launch_moments(const Params& P, int scheme, int z0, int nzs, const float* f, const float* g,
+                           const float* phi_fd, int mask, double* out, cudaStream_t s) {
+    if (P.Q == 9) {
+        if (scheme == SCHEME_DF) moments_q<9, SCHEME_DF>(P, z0, nzs, f, g, phi_fd, mask, out, s);
+        else moments_q<9, SCHEME_FD>(P, z0, nzs, f, g, phi_fd, mask, out, s);
+    } else {
+        if (scheme == SCHEME_DF) moments_q<19, SCHEME_DF>(P, z0, nzs, f, g, phi_fd, mask, out, s);
+        else moments_q<19, SCHEME_FD>(P, z0, nzs, f, g, phi_fd, mask, out, s);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Mass: sum phi and sum rho phi over the propagated state, FP64 accumulation, plus a count of
+// non-finite stored populations. Grid-stride per thread, warp shuffle, shared memory per block,
+// one partial triple per block; a single block then sums the partials in a fixed order, so the
+// result does not depend on scheduling.
+// ---------------------------------------------------------------------------------------
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void block_sum3(double (&v)[3], double* out) {
+    __shared__ double red[3][kRedThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        v[k] = warp_sum(v[k]);
+        if (lane == 0) red[k][warp] = v[k];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double w = (lane < kRedThreads / 32) ? red[k][lane] : 0.0;
+            w = warp_sum(w);
+            if (lane == 0) out[k] = w;
+        }
+    }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(kRedThreads)
+mass_kernel(const Params P, const float* __restrict__ f, const float* __restrict__ g, double* __restrict__ partials) {
+    double acc[3] = {0.0, 0.0, 0.0};
+    const size_t N = (size_t)P.N;
+    for (long long c = (long long)blockIdx.x * kRedThreads + threadIdx.x; c < P.N;
+         c += (long long)gridDim.x * kRedThreads) {
+        const int z = (int)(c / P.nxy);
+        const int r = (int)(c - (long long)z * P.nxy);
+        const int y = r / P.nx, x = r - y * P.nx;
+        const Nbr nb = make_nbr(P, x, y, z);
+        float fb[Q], gb[Q];
+        pull<Q, false>(P, nullptr, g, (int)c, nb, fb, gb);
+        const double phi = (double)sum_phi<Q>(gb);
+        acc[0] += phi;
+        acc[1] += (P.rho2_d + P.drho_d * phi) * phi;
+        int bad = 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) bad += !isfinite(__ldg(f + i * N + c)) + !isfinite(__ldg(g + i * N + c));
+        acc[2] += (double)bad;
+    }
+    block_sum3(acc, partials + 3 * blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+mass_finish(const double* __restrict__ partials, int n, double* __restrict__ result) {
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < n; b += kRedThreads)
+        for (int k = 0; k < 3; ++k) acc[k] += partials[3 * b + k];
+    block_sum3(acc, result);
+}
+
+int mass_partials_needed(const Params& P) {
+    const long long blocks = (P.N + kRedThreads - 1) / kRedThreads;
+    return (int)(blocks < 1024 ? blocks : 1024);
+}
+
+cudaError_t launch_mass(const Params& P, const float* f, const float* g, double* partials, int n_partials,
+                        double* result, cudaStream_t s) {
+    if (P.Q == 9) mass_kernel<9><<<n_partials, kRedThreads, 0, s>>>(P, f, g, partials);
+    else mass_kernel<19><<<n_partials, kRedThreads, 0, s>>>(P, f, g, partials);
+    mass_finish<<<1, kRedThreads, 0, s>>>(partials, n_partials, result);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Population plane <-> FP64 staging (the f shift t_i w0 is added back on the way out).
+// ---------------------------------------------------------------------------------------
+template <int Q>
+__device__ __forceinline__ double shift_of(int q, double w0) {
+    double t = 0.0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        if (i == q) t = Lat<Q>::wd(i);
+    return t * w0;
+}
+
+template <int Q>
+__global__ void pops_to_f64(const Params P, const float* __restrict__ src, int q, int is_f, int z0, int nzs,
+                            double* __restrict__ dst) {
+    const size_t n = (size_t)nzs * P.nxy, base = (size_t)z0 * P.nxy;
+    const double sh = is_f ? shift_of<Q>(q, P.w0d) : 0.0;
+    for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (size_t)gridDim.x * blockDim.x)
+        dst[l] = (double)src[(size_t)q * P.N + base + l] + sh;
+}
+
+template <int Q>
+__global__ void pops_from_f64(const Params P, const double* __restrict__ src, int q, int is_f, int z0, int nzs,
+                              float* __restrict__ dst) {
+    const size_t n = (size_t)nzs * P.nxy, base = (size_t)z0 * P.nxy;
+    const double sh = is_f ? shift_of<Q>(q, P.w0d) : 0.0;
+    for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (size_t)gridDim.x * blockDim.x)
+        dst[(size_t)q * P.N + base + l] = (float)(src[l] - sh);
+}
+
+static unsigned conv_blocks(const Params& P, int nzs) {
+    const size_t n = (size_t)nzs * P.nxy;
+    const size_t b = (n + 255) / 256;
+    return (unsigned)(b < 4096 ? b : 4096);
+}
+
+cudaError_t launch_pops_to_f64(const Params& P, const float* src, int q, int is_f, int z0, int nzs, double* dst,
+                               cudaStream_t s) {
+    if (P.Q == 9) pops_to_f64<9><<<conv_blocks(P, nzs), 256, 0, s>>>(P, src, q, is_f, z0, nzs, dst);
+    else pops_to_f64<19><<<conv_blocks(P, nzs), 256, 0, s>>>(P, src, q, is_f, z0, nzs, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pops_from_f64(const Params& P, const double* src, int q, int is_f, int z0, int nzs, float* dst,
+                                 cudaStream_t s) {
+    if (P.Q == 9) pops_from_f64<9><<<conv_blocks(P, nzs), 256, 0, s>>>(P, src, q, is_f, z0, nzs, dst);
+    else pops_from_f64<19><<<conv_blocks(P, nzs), 256, 0, s>>>(P, src, q, is_f, z0, nzs, dst);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,0 +1,256 @@
+// cell.cuh -- per-cell device code of the difference-free conservative phase-field LBM
+// (Zhao, Patel & Lee, arXiv:2407.12263): Lax-Wendroff pull, macroscopic stage, collisions.
+//
+// Storage: FP32 planes [Q][N]. f is held as the deviation f_i - t_i w0 from the lattice
+// weights times the reference pressure level w0 = p0 / cs^2; propagation and collision are
+// linear with weights summing to one, so the shift passes through them unchanged and every
+// FP32 value on the f path is a small deviation rather than a number of order t_i. g is held
+// as is. All arithmetic is FP32 with constants folded (1/cs^2 = 3, 1/(2 cs^4) = 4.5).
+#pragma once
+
+#include "lattice.cuh"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+constexpr float kNormalGuard = 1e-24f;  // n = 0 where |K1|^2 (or |grad phi|^2) <= this
+
+// Element offsets from a cell to its six face neighbours on the periodic grid.
+struct Nbr {
+    int xm, xp, ym, yp, zm, zp;
+};
+
+__device__ __forceinline__ Nbr make_nbr(const Params& P, int x, int y, int z) {
+    Nbr n;
+    n.xm = (x == 0) ? P.nx - 1 : -1;
+    n.xp = (x == P.nx - 1) ? -(P.nx - 1) : 1;
+    n.ym = (y == 0) ? (P.ny - 1) * P.nx : -P.nx;
+    n.yp = (y == P.ny - 1) ? -(P.ny - 1) * P.nx : P.nx;
+    n.zm = (z == 0) ? (P.nz - 1) * P.nxy : -P.nxy;
+    n.zp = (z == P.nz - 1) ? -(P.nz - 1) * P.nxy : P.nxy;
+    return n;
+}
+
+// Offset of the cell x + s e_i (s = +1 or -1). Folds to two or three adds once unrolled.
+template <int Q>
+__device__ __forceinline__ int link_offset(const Nbr& n, int i, int s) {
+    const int ex = s * Lat<Q>::cx(i), ey = s * Lat<Q>::cy(i), ez = s * Lat<Q>::cz(i);
+    return (ex > 0 ? n.xp : ex < 0 ? n.xm : 0) + (ey > 0 ? n.yp : ey < 0 ? n.ym : 0) +
+           (ez > 0 ? n.zp : ez < 0 ? n.zm : 0);
+}
+
+// Lax-Wendroff propagation (Sec. 2.2) of both sets into registers:
+// fbar_i(x) = a- f*_i(x - e_i) + a0 f*_i(x) + a+ f*_i(x + e_i), the same for g.
+template <int Q, bool WITH_F>
+__device__ __forceinline__ void pull(const Params& P, const float* __restrict__ f,
+                                     const float* __restrict__ g, int c, const Nbr& nb,
+                                     float (&fb)[Q], float (&gb)[Q]) {
+    const size_t N = (size_t)P.N;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float* gq = g + i * N;
+        if (i == 0) {
+            if (WITH_F) fb[0] = __ldg(f + c);
+            gb[0] = __ldg(gq + c);
+        } else {
+            const int cm = c + link_offset<Q>(nb, i, -1);
+            const int cp = c + link_offset<Q>(nb, i, +1);
+            if (WITH_F) {
+                const float* fq = f + i * N;
+                fb[i] = P.am * __ldg(fq + cm) + P.a0 * __ldg(fq + c) + P.ap * __ldg(fq + cp);
+            }
+            gb[i] = P.am * __ldg(gq + cm) + P.a0 * __ldg(gq + c) + P.ap * __ldg(gq + cp);
+        }
+    }
+}
+
+template <int Q>
+__device__ __forceinline__ float sum_phi(const float (&gb)[Q]) {
+    float phi = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) phi += gb[i];
+    return phi;
+}
+
+struct Macro {
+    float phi, rho, inv_rho;
+    float u[3];
+    float n[3];
+    float S[3];
+    float gphi[3];
+    float P;      // p / cs^2 - w0 = sum (f_i - t_i w0) + u . grad rho / 2
+    float gnorm;  // |grad phi|
+};
+
+// phi, rho, u (Sec. 2.3, Eq. momentum): rho u = sum fbar_i e_i + rho G / 2.
+template <int Q, bool GEN>
+__device__ __forceinline__ void macro_flow(const Params& P, const float (&fb)[Q], const float (&gb)[Q], Macro& m) {
+    m.phi = sum_phi<Q>(gb);
+    float jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        if (Lat<Q>::cx(i) > 0) jx += fb[i];
+        if (Lat<Q>::cx(i) < 0) jx -= fb[i];
+        if (Lat<Q>::cy(i) > 0) jy += fb[i];
+        if (Lat<Q>::cy(i) < 0) jy -= fb[i];
+        if (Lat<Q>::cz(i) > 0) jz += fb[i];
+        if (Lat<Q>::cz(i) < 0) jz -= fb[i];
+    }
+    if (GEN) {
+        m.rho = P.rho2 + P.drho * m.phi;
+        m.inv_rho = 1.0f / m.rho;
+        jx += 0.5f * m.rho * P.G[0];
+        jy += 0.5f * m.rho * P.G[1];
+        jz += 0.5f * m.rho * P.G[2];
+    } else {
+        m.rho = P.rho2;
+        m.inv_rho = 1.0f;  // rho2 = 1 and no density contrast
+    }
+    m.u[0] = jx * m.inv_rho;
+    m.u[1] = jy * m.inv_rho;
+    m.u[2] = jz * m.inv_rho;
+}
+
+// Interface normal, sharpening flux and gradients from the first central moment of g
+// (Sec. 2.3, Eq. norm): K1 = sum g_i e_i - phi u, n = -K1/|K1|, S = 4 phi (1-phi)/delta n,
+// grad phi = (tau_phi cs^2 S - K1) / ((tau_phi + 1/2) cs^2).
+template <int Q>
+__device__ __forceinline__ void macro_interface_df(const Params& P, const float (&gb)[Q], Macro& m) {
+    float kx = 0.f, ky = 0.f, kz = 0.f;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        if (Lat<Q>::cx(i) > 0) kx += gb[i];
+        if (Lat<Q>::cx(i) < 0) kx -= gb[i];
+        if (Lat<Q>::cy(i) > 0) ky += gb[i];
+        if (Lat<Q>::cy(i) < 0) ky -= gb[i];
+        if (Lat<Q>::cz(i) > 0) kz += gb[i];
+        if (Lat<Q>::cz(i) < 0) kz -= gb[i];
+    }
+    kx -= m.phi * m.u[0];
+    ky -= m.phi * m.u[1];
+    kz -= m.phi * m.u[2];
+    const float k2 = kx * kx + ky * ky + kz * kz;
+    const float r = (k2 > kNormalGuard) ? -rsqrtf(k2) : 0.f;
+    m.n[0] = kx * r;
+    m.n[1] = ky * r;
+    m.n[2] = kz * r;
+    const float smag = P.four_over_delta * m.phi * (1.f - m.phi);
+    m.S[0] = smag * m.n[0];
+    m.S[1] = smag * m.n[1];
+    m.S[2] = smag * m.n[2];
+    m.gphi[0] = P.grad_s * m.S[0] - P.grad_k * kx;
+    m.gphi[1] = P.grad_s * m.S[1] - P.grad_k * ky;
+    m.gphi[2] = P.grad_s * m.S[2] - P.grad_k * kz;
+}
+
+// Finite-difference variant (Sec. 3.4): n = grad phi / |grad phi| with grad phi given.
+__device__ __forceinline__ void macro_interface_fd(const Params& P, float gx, float gy, float gz, Macro& m) {
+    m.gphi[0] = gx;
+    m.gphi[1] = gy;
+    m.gphi[2] = gz;
+    const float g2 = gx * gx + gy * gy + gz * gz;
+    const float r = (g2 > kNormalGuard) ? rsqrtf(g2) : 0.f;
+    m.n[0] = gx * r;
+    m.n[1] = gy * r;
+    m.n[2] = gz * r;
+    const float smag = P.four_over_delta * m.phi * (1.f - m.phi);
+    m.S[0] = smag * m.n[0];
+    m.S[1] = smag * m.n[1];
+    m.S[2] = smag * m.n[2];
+}
+
+// Pressure (Eq. pressure): p/cs^2 = sum fbar_i + u . grad rho / 2, held as P = p/cs^2 - w0.
+template <int Q, bool GEN>
+__device__ __forceinline__ void macro_pressure(const Params& P, const float (&fb)[Q], Macro& m) {
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) s += fb[i];
+    if (GEN) s += 0.5f * P.drho * (m.u[0] * m.gphi[0] + m.u[1] * m.gphi[1] + m.u[2] * m.gphi[2]);
+    m.P = s;
+    m.gnorm = sqrtf(m.gphi[0] * m.gphi[0] + m.gphi[1] * m.gphi[1] + m.gphi[2] * m.gphi[2]);
+}
+
+// Isotropic central difference of the propagated phi field (Sec. 3.4):
+// grad phi = sum_{i != 0} t_i e_i [phi(x + e_i) - phi(x - e_i)] / (2 cs^2)
+//          = 3 sum_{i != 0} t_i e_i phi(x + e_i)   (the velocity set is symmetric).
+template <int Q>
+__device__ __forceinline__ void fd_gradient(const float* __restrict__ phi, int c, const Nbr& nb,
+                                            float& gx, float& gy, float& gz) {
+    gx = gy = gz = 0.f;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const float v = Lat<Q>::w(i) * __ldg(phi + c + link_offset<Q>(nb, i, +1));
+        if (Lat<Q>::cx(i) > 0) gx += v;
+        if (Lat<Q>::cx(i) < 0) gx -= v;
+        if (Lat<Q>::cy(i) > 0) gy += v;
+        if (Lat<Q>::cy(i) < 0) gy -= v;
+        if (Lat<Q>::cz(i) > 0) gz += v;
+        if (Lat<Q>::cz(i) < 0) gz -= v;
+    }
+    gx *= 3.f;
+    gy *= 3.f;
+    gz *= 3.f;
+}
+
+template <int Q>
+__device__ __forceinline__ float edot(int i, const float (&v)[3]) {
+    float r = 0.f;
+    if (Lat<Q>::cx(i) > 0) r += v[0];
+    if (Lat<Q>::cx(i) < 0) r -= v[0];
+    if (Lat<Q>::cy(i) > 0) r += v[1];
+    if (Lat<Q>::cy(i) < 0) r -= v[1];
+    if (Lat<Q>::cz(i) > 0) r += v[2];
+    if (Lat<Q>::cz(i) < 0) r -= v[2];
+    return r;
+}
+
+// Collisions, in place on fb / gb.
+//   f^eq_i - t_i w0 = t_i [P + rho gam_i - 4.5 Pi_s:(e_i e_i - cs^2 I)]            (Eq. geq_s,
+//        gam_i = 3 e.u + 4.5 (e.u)^2 - 1.5 u^2, the CSS term entering with a minus sign so that
+//        the second moment is p I + rho u u - Pi_s as App. A requires)
+//   Pi_s:(e e - cs^2 I) = sigma |grad phi| [|e|^2 - (e.n)^2 - cs^2 (D - |n|^2)]        (Eq. surface)
+//   S_i = t_i gam_i (e_i - u) . grad rho                                                 (App. A)
+//   R_i = t_i [3 (e_i - u) + 9 (e_i . u) e_i] . rho G                                    (Eq. body)
+//   f*_i = fbar_i - omega_rho (fbar_i - f^eq_i + F_i/2) + F_i                           (Eq. c-n_m)
+//   g^eq_i = t_i [phi (1 + gam_i) + tau_phi e_i . S]                                     (Eq. geq)
+//   g*_i = g_i - omega_g (g_i - g^eq_i)                                                  (Eq. c-n_c)
+template <int Q, bool GEN>
+__device__ __forceinline__ void collide(const Params& P, const Macro& m, float (&fb)[Q], float (&gb)[Q]) {
+    constexpr int D = Lat<Q>::D;
+    const float u2 = m.u[0] * m.u[0] + m.u[1] * m.u[1] + m.u[2] * m.u[2];
+    const float sg = P.sigma * m.gnorm;
+    const float trc = (float)D - (m.n[0] * m.n[0] + m.n[1] * m.n[1] + m.n[2] * m.n[2]);
+    const float pi0 = -sg * (trc * (1.0f / 3.0f));  // sigma |grad phi| (|e|^2 - cs^2 trc) for |e|^2 = 0
+    const float gr[3] = {P.drho * m.gphi[0], P.drho * m.gphi[1], P.drho * m.gphi[2]};
+    const float rG[3] = {m.rho * P.G[0], m.rho * P.G[1], m.rho * P.G[2]};
+    const float ugr = m.u[0] * gr[0] + m.u[1] * gr[1] + m.u[2] * gr[2];
+    const float urG = m.u[0] * rG[0] + m.u[1] * rG[1] + m.u[2] * rG[2];
+    float omega_f = P.omega_f;
+    if (GEN) {
+        const float tau = P.tau_f * (1.f + P.mu_m1 * m.phi) * m.inv_rho;  // eta(phi) / (rho cs^2)
+        omega_f = 1.0f / (tau + 0.5f);
+    }
+    const float omega_g = P.omega_g;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float t = Lat<Q>::w(i);
+        const float eu = edot<Q>(i, m.u);
+        const float en = edot<Q>(i, m.n);
+        const float es = edot<Q>(i, m.S);
+        const float gam = eu * (3.f + 4.5f * eu) - 1.5f * u2;
+        const float pis = pi0 + sg * ((float)Lat<Q>::e2(i) - en * en);
+        const float feq = t * (m.P + m.rho * gam - 4.5f * pis);
+        if (GEN) {
+            const float egr = edot<Q>(i, gr);
+            const float erG = edot<Q>(i, rG);
+            const float F = t * (gam * (egr - ugr) + 3.f * (erG - urG) + 9.f * eu * erG);
+            fb[i] = fb[i] - omega_f * (fb[i] - feq + 0.5f * F) + F;
+        } else {
+            fb[i] = fb[i] - omega_f * (fb[i] - feq);
+        }
+        const float geq = t * (m.phi * (1.f + gam) + P.tau_phi * es);
+        gb[i] = gb[i] - omega_g * (gb[i] - geq);
+    }
+}
+
+}  // namespace lbm

@@ -1,0 +1,442 @@
+// lbm_api.cu -- the C ABI (include/lbm.h): handle management, argument checks, slab-wise
+// host <-> device transfers and kernel launches on the handle's stream.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/lbm.h"
+#include "lattice.cuh"
+#include "lbm_internal.h"
+
+using lbm::Params;
+
+struct lbm_ctx {
+    Params P;
+    int scheme;
+    double courant;
+    int device;
+    cudaStream_t stream;
+    bool own_stream;
+    float* f[2];
+    float* g[2];
+    int cur;               // index of the buffer pair holding the current state
+    float* phi_fd;         // propagated phi plane of the finite-difference variant
+    double* partials;      // per-block FP64 partial sums of the mass reduction
+    int n_partials;
+    double* result;        // 3 doubles: sum phi, sum rho phi, non-finite count
+    double* staging;       // FP64 staging for host transfers, allocated on first use
+    size_t staging_elems;
+    bool initialised;
+    long long launches;
+    char err[512];
+};
+
+namespace {
+
+constexpr size_t kStagingCap = size_t(32) << 20;  // doubles (256 MB) per staging slab at most
+
+thread_local char g_create_error[512] = "no error";
+
+int set_error(lbm_ctx* ctx, int code, const char* fmt, ...) {
+    char* buf = ctx ? ctx->err : g_create_error;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 512, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define LBM_CUDA(ctx, call)                                                                   \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return set_error((ctx), e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, \
+                             "%s failed: %s", #call, cudaGetErrorString(e_));                 \
+    } while (0)
+
+bool is_fin(double v) { return std::isfinite(v); }
+
+void free_ctx(lbm_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(c->f[k]);
+        cudaFree(c->g[k]);
+    }
+    cudaFree(c->phi_fd);
+    cudaFree(c->partials);
+    cudaFree(c->result);
+    cudaFree(c->staging);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int ensure_staging(lbm_ctx* c, size_t elems) {
+    if (c->staging_elems >= elems) return LBM_OK;
+    cudaFree(c->staging);
+    c->staging = nullptr;
+    c->staging_elems = 0;
+    LBM_CUDA(c, cudaMalloc(&c->staging, elems * sizeof(double)));
+    c->staging_elems = elems;
+    return LBM_OK;
+}
+
+// z-planes per slab so that slab_planes(nzs) * nxy doubles fit the staging cap.
+int slab_depth(const lbm_ctx* c, int planes_per_z, int extra_planes) {
+    const size_t nxy = (size_t)c->P.nxy;
+    long long nzs = (long long)(kStagingCap / nxy) - extra_planes;
+    nzs = planes_per_z > 0 ? nzs / planes_per_z : nzs;
+    if (nzs < 1) nzs = 1;
+    if (nzs > c->P.nz) nzs = c->P.nz;
+    return (int)nzs;
+}
+
+int check_ctx(lbm_ctx* c) {
+    if (!c) return set_error(nullptr, LBM_EINVAL, "null handle");
+    LBM_CUDA(c, cudaSetDevice(c->device));
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_default_opts(lbm_opts* o) {
+    if (!o) return;
+    o->scheme = LBM_SCHEME_DIFFERENCE_FREE;
+    o->storage = 0;
+    o->courant = 0.997;
+    o->walls = 0;
+    o->stream = nullptr;
+}
+
+int lbm_create(lbm_ctx** out, const int grid[3], int lattice, double tau_f, double tau_g, double M, double xi,
+               double sigma, double rho_ratio, double mu_ratio, const double body_force[3], const lbm_opts* opts) {
+    if (!out) return set_error(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!grid) return set_error(nullptr, LBM_EINVAL, "grid is NULL");
+    lbm_opts o;
+    lbm_default_opts(&o);
+    if (opts) o = *opts;
+    const int nx = grid[0], ny = grid[1], nz = grid[2];
+    if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19)
+        return set_error(nullptr, LBM_EINVAL, "lattice must be 9 (D2Q9) or 19 (D3Q19), got %d", lattice);
+    if (nx < 3 || ny < 3) return set_error(nullptr, LBM_EINVAL, "nx and ny must be >= 3 (got %d, %d)", nx, ny);
+    if (lattice == LBM_D2Q9 && nz != 1) return set_error(nullptr, LBM_EINVAL, "D2Q9 needs nz = 1 (got %d)", nz);
+    if (lattice == LBM_D3Q19 && (nz < 3 || nz > 65535))
+        return set_error(nullptr, LBM_EINVAL, "D3Q19 needs 3 <= nz <= 65535 (got %d)", nz);
+    const long long N = (long long)nx * ny * nz;
+    if (N >= (long long)INT_MAX) return set_error(nullptr, LBM_EINVAL, "nx*ny*nz must be < 2^31 (got %lld)", N);
+    if (!(tau_f > 0) || !is_fin(tau_f)) return set_error(nullptr, LBM_EINVAL, "tau_f must be > 0");
+    if (!is_fin(M) || !is_fin(tau_g) || (!(M > 0) && !(tau_g > 0)))
+        return set_error(nullptr, LBM_EINVAL, "need M > 0 or tau_g > 0");
+    if (!(xi >= 2) || !is_fin(xi)) return set_error(nullptr, LBM_EINVAL, "xi must be >= 2 (got %g)", xi);
+    if (!(sigma >= 0) || !is_fin(sigma)) return set_error(nullptr, LBM_EINVAL, "sigma must be >= 0");
+    if (!(rho_ratio > 0) || !is_fin(rho_ratio) || !(mu_ratio > 0) || !is_fin(mu_ratio))
+        return set_error(nullptr, LBM_EINVAL, "rho_ratio and mu_ratio must be > 0");
+    double G[3] = {0, 0, 0};
+    if (body_force)
+        for (int a = 0; a < 3; ++a) G[a] = body_force[a];
+    for (int a = 0; a < 3; ++a)
+        if (!is_fin(G[a])) return set_error(nullptr, LBM_EINVAL, "body_force must be finite");
+    if (lattice == LBM_D2Q9 && G[2] != 0) return set_error(nullptr, LBM_EINVAL, "D2Q9 needs body_force[2] = 0");
+    if (o.scheme != LBM_SCHEME_DIFFERENCE_FREE && o.scheme != LBM_SCHEME_FINITE_DIFFERENCE)
+        return set_error(nullptr, LBM_EINVAL, "unknown scheme %d", o.scheme);
+    if (o.storage != 0) return set_error(nullptr, LBM_EINVAL, "storage %d is not built (0 = FP32)", o.storage);
+    if (o.walls != 0) return set_error(nullptr, LBM_EINVAL, "walls %d are not built (0 = periodic)", o.walls);
+    if (!(o.courant > 0 && o.courant <= 1)) return set_error(nullptr, LBM_EINVAL, "courant must be in (0, 1]");
+
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    if (!c) return set_error(nullptr, LBM_ENOMEM, "host allocation failed");
+    std::memset(c, 0, sizeof(*c));
+    std::snprintf(c->err, sizeof c->err, "no error");
+    c->scheme = o.scheme;
+    c->courant = o.courant;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        delete c;
+        return set_error(nullptr, LBM_ECUDA, "no CUDA device available");
+    }
+
+    // Parameters (Sec. 2.2, Sec. 2.3). tau_phi from M = tau_phi cs^2 dt when M > 0.
+    Params& P = c->P;
+    const double cs2 = 1.0 / 3.0;
+    const double cc = o.courant;
+    const double tau_phi = (M > 0) ? M / cs2 : tau_g;
+    P.Q = lattice;
+    P.nx = nx;
+    P.ny = ny;
+    P.nz = nz;
+    P.nxy = nx * ny;
+    P.N = N;
+    P.am = (float)(0.5 * cc * (1.0 + cc));   // weight of f*(x - e)
+    P.a0 = (float)(1.0 - cc * cc);           // weight of f*(x)
+    P.ap = (float)(-0.5 * cc * (1.0 - cc));  // weight of f*(x + e)
+    P.tau_phi = (float)tau_phi;
+    P.omega_g = (float)(1.0 / (tau_phi + 0.5));
+    P.grad_s = (float)(tau_phi / (tau_phi + 0.5));
+    P.grad_k = (float)(1.0 / ((tau_phi + 0.5) * cs2));
+    P.tau_f = (float)tau_f;
+    P.omega_f = (float)(1.0 / (tau_f + 0.5));
+    P.rho2 = 1.0f;
+    P.drho = (float)(rho_ratio - 1.0);
+    P.mu_m1 = (float)(mu_ratio - 1.0);
+    P.sigma = (float)sigma;
+    P.four_over_delta = (float)(4.0 / xi);
+    for (int a = 0; a < 3; ++a) P.G[a] = (float)G[a];
+    P.w0 = 1.0f;  // p0 = cs^2 until lbm_init_phi sets it
+    P.general = (rho_ratio != 1.0 || mu_ratio != 1.0 || G[0] != 0 || G[1] != 0 || G[2] != 0) ? 1 : 0;
+    P.w0d = 1.0;
+    P.tau_phi_d = tau_phi;
+    P.sigma_d = sigma;
+    P.four_over_delta_d = 4.0 / xi;
+    P.drho_d = rho_ratio - 1.0;
+    P.rho2_d = 1.0;
+
+    int rc = LBM_OK;
+    auto fail = [&](int code) {
+        std::snprintf(g_create_error, sizeof g_create_error, "%s", c->err);
+        free_ctx(c);
+        return code;
+    };
+    if (o.stream) {
+        c->stream = (cudaStream_t)o.stream;
+        c->own_stream = false;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            set_error(c, LBM_ECUDA, "cudaStreamCreate failed: %s", cudaGetErrorString(e));
+            return fail(LBM_ECUDA);
+        }
+        c->own_stream = true;
+    }
+    const size_t pop_bytes = (size_t)lattice * (size_t)N * sizeof(float);
+    for (int k = 0; k < 2 && rc == LBM_OK; ++k) {
+        cudaError_t e1 = cudaMalloc(&c->f[k], pop_bytes);
+        cudaError_t e2 = (e1 == cudaSuccess) ? cudaMalloc(&c->g[k], pop_bytes) : e1;
+        if (e2 != cudaSuccess)
+            rc = set_error(c, e2 == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA,
+                           "allocating %zu bytes of populations failed: %s", 4 * pop_bytes,
+                           cudaGetErrorString(e2));
+    }
+    if (rc == LBM_OK && c->scheme == LBM_SCHEME_FINITE_DIFFERENCE) {
+        cudaError_t e = cudaMalloc(&c->phi_fd, (size_t)N * sizeof(float));
+        if (e != cudaSuccess) rc = set_error(c, LBM_ENOMEM, "allocating the phi plane failed: %s", cudaGetErrorString(e));
+    }
+    if (rc == LBM_OK) {
+        c->n_partials = lbm::mass_partials_needed(P);
+        cudaError_t e = cudaMalloc(&c->partials, (size_t)3 * c->n_partials * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&c->result, 3 * sizeof(double));
+        if (e != cudaSuccess) rc = set_error(c, LBM_ENOMEM, "allocating reduction scratch failed: %s", cudaGetErrorString(e));
+    }
+    if (rc != LBM_OK) return fail(rc);
+    *out = c;
+    return LBM_OK;
+}
+
+int lbm_init_phi(lbm_ctx* c, const double* phi0, const double* u0, double p0) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!phi0) return set_error(c, LBM_EINVAL, "phi0 is NULL");
+    if (!(p0 > 0) || !is_fin(p0)) return set_error(c, LBM_EINVAL, "p0 must be > 0 and finite");
+    Params& P = c->P;
+    P.w0d = p0 * 3.0;  // w0 = p0 / cs^2: the level the f storage is shifted by
+    P.w0 = (float)P.w0d;
+    const size_t nxy = (size_t)P.nxy;
+    const int per_z = 1 + (u0 ? 3 : 0);
+    const int nzs = slab_depth(c, per_z, 2);
+    rc = ensure_staging(c, (size_t)(nzs + 2 + (u0 ? 3 * nzs : 0)) * nxy);
+    if (rc) return rc;
+    double* phis = c->staging;
+    double* us = c->staging + (size_t)(nzs + 2) * nxy;
+    for (int z0 = 0; z0 < P.nz; z0 += nzs) {
+        const int n = (z0 + nzs <= P.nz) ? nzs : P.nz - z0;
+        // phi0 planes z0-1 .. z0+n (periodic images at the ends); D2Q9 has only its one plane
+        const int lo = (P.Q == 9) ? 0 : -1, hi = (P.Q == 9) ? n - 1 : n;
+        for (int l = lo; l <= hi; ++l) {
+            const int z = ((z0 + l) % P.nz + P.nz) % P.nz;
+            LBM_CUDA(c, cudaMemcpyAsync(phis + (size_t)(l + 1) * nxy, phi0 + (size_t)z * nxy, nxy * sizeof(double),
+                                        cudaMemcpyHostToDevice, c->stream));
+        }
+        if (u0)
+            for (int a = 0; a < 3; ++a)
+                LBM_CUDA(c, cudaMemcpyAsync(us + (size_t)a * n * nxy, u0 + (size_t)a * P.N + (size_t)z0 * nxy,
+                                            (size_t)n * nxy * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        LBM_CUDA(c, lbm::launch_init(P, z0, n, phis, u0 ? us : nullptr, p0, c->f[c->cur], c->g[c->cur], c->stream));
+        c->launches += 1;
+    }
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->initialised = true;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_ctx* c, int n) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (n < 0) return set_error(c, LBM_EINVAL, "n must be >= 0 (got %d)", n);
+    if (!c->initialised) return set_error(c, LBM_ESTATE, "lbm_step before lbm_init_phi");
+    for (int k = 0; k < n; ++k) {
+        const int a = c->cur, b = 1 - c->cur;
+        int launches = 0;
+        LBM_CUDA(c, lbm::launch_step(c->P, c->scheme, c->f[a], c->g[a], c->f[b], c->g[b], c->phi_fd, c->stream,
+                                     &launches));
+        c->launches += launches;
+        c->cur = b;
+    }
+    return LBM_OK;
+}
+
+static int fields_out(lbm_ctx* c, int mask, double* const* dst /* 11 planes, NULL = skip */) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!c->initialised) return set_error(c, LBM_ESTATE, "no state: call lbm_init_phi first");
+    Params& P = c->P;
+    const size_t nxy = (size_t)P.nxy;
+    const int nzs = slab_depth(c, 11, 0);
+    rc = ensure_staging(c, (size_t)11 * nzs * nxy);
+    if (rc) return rc;
+    const float* f = c->f[c->cur];
+    const float* g = c->g[c->cur];
+    if (c->scheme == LBM_SCHEME_FINITE_DIFFERENCE) {
+        LBM_CUDA(c, lbm::launch_fd_phi(P, g, c->phi_fd, c->stream));
+        c->launches += 1;
+    }
+    for (int z0 = 0; z0 < P.nz; z0 += nzs) {
+        const int n = (z0 + nzs <= P.nz) ? nzs : P.nz - z0;
+        LBM_CUDA(c, lbm::launch_moments(P, c->scheme, z0, n, f, g, c->phi_fd, mask, c->staging, c->stream));
+        c->launches += 1;
+        const size_t slab = (size_t)n * nxy;
+        for (int j = 0; j < 11; ++j) {
+            if (!dst[j]) continue;
+            LBM_CUDA(c, cudaMemcpyAsync(dst[j] + (size_t)z0 * nxy, c->staging + (size_t)j * slab, slab * sizeof(double),
+                                        cudaMemcpyDeviceToHost, c->stream));
+        }
+        LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return LBM_OK;
+}
+
+int lbm_moments(lbm_ctx* c, double* phi, double* p, double* u) {
+    if (!c) return set_error(nullptr, LBM_EINVAL, "null handle");
+    const size_t N = c ? (size_t)c->P.N : 0;
+    double* dst[11] = {phi, p, u, u ? u + N : nullptr, u ? u + 2 * N : nullptr,
+                       nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    const int mask = (phi ? 1 : 0) | (p ? 2 : 0) | (u ? 4 : 0);
+    if (!mask) return LBM_OK;
+    return fields_out(c, mask, dst);
+}
+
+int lbm_gradients(lbm_ctx* c, double* grad_phi, double* normal) {
+    if (!c) return set_error(nullptr, LBM_EINVAL, "null handle");
+    const size_t N = (size_t)c->P.N;
+    double* dst[11] = {nullptr, nullptr, nullptr, nullptr, nullptr,
+                       grad_phi, grad_phi ? grad_phi + N : nullptr, grad_phi ? grad_phi + 2 * N : nullptr,
+                       normal, normal ? normal + N : nullptr, normal ? normal + 2 * N : nullptr};
+    const int mask = (grad_phi ? 8 : 0) | (normal ? 16 : 0);
+    if (!mask) return LBM_OK;
+    return fields_out(c, mask, dst);
+}
+
+int lbm_mass(lbm_ctx* c, double* sum_phi, double* sum_rho_phi) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!c->initialised) return set_error(c, LBM_ESTATE, "no state: call lbm_init_phi first");
+    LBM_CUDA(c, lbm::launch_mass(c->P, c->f[c->cur], c->g[c->cur], c->partials, c->n_partials, c->result, c->stream));
+    c->launches += 2;
+    double r[3];
+    LBM_CUDA(c, cudaMemcpyAsync(r, c->result, sizeof r, cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (sum_phi) *sum_phi = r[0];
+    if (sum_rho_phi) *sum_rho_phi = r[1];
+    if (r[2] != 0.0) return set_error(c, LBM_ENONFINITE, "%.0f stored populations are not finite", r[2]);
+    return LBM_OK;
+}
+
+static int pops_io(lbm_ctx* c, double* f_out, double* g_out, const double* f_in, const double* g_in) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    Params& P = c->P;
+    const size_t nxy = (size_t)P.nxy;
+    const int nzs = slab_depth(c, 1, 0);
+    rc = ensure_staging(c, (size_t)nzs * nxy);
+    if (rc) return rc;
+    for (int is_f = 1; is_f >= 0; --is_f) {
+        double* host_out = is_f ? f_out : g_out;
+        const double* host_in = is_f ? f_in : g_in;
+        float* dev = is_f ? c->f[c->cur] : c->g[c->cur];
+        if (!host_out && !host_in) continue;
+        for (int q = 0; q < P.Q; ++q)
+            for (int z0 = 0; z0 < P.nz; z0 += nzs) {
+                const int n = (z0 + nzs <= P.nz) ? nzs : P.nz - z0;
+                const size_t off = (size_t)q * P.N + (size_t)z0 * nxy, bytes = (size_t)n * nxy * sizeof(double);
+                if (host_in) {
+                    LBM_CUDA(c, cudaMemcpyAsync(c->staging, host_in + off, bytes, cudaMemcpyHostToDevice, c->stream));
+                    LBM_CUDA(c, lbm::launch_pops_from_f64(P, c->staging, q, is_f, z0, n, dev, c->stream));
+                } else {
+                    LBM_CUDA(c, lbm::launch_pops_to_f64(P, dev, q, is_f, z0, n, c->staging, c->stream));
+                    LBM_CUDA(c, cudaMemcpyAsync(host_out + off, c->staging, bytes, cudaMemcpyDeviceToHost, c->stream));
+                }
+                c->launches += 1;
+                LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+            }
+    }
+    return LBM_OK;
+}
+
+int lbm_get_pops(lbm_ctx* c, double* f, double* g) {
+    if (!c) return set_error(nullptr, LBM_EINVAL, "null handle");
+    if (!c->initialised) return set_error(c, LBM_ESTATE, "no state: call lbm_init_phi first");
+    return pops_io(c, f, g, nullptr, nullptr);
+}
+
+int lbm_set_pops(lbm_ctx* c, const double* f, const double* g) {
+    if (!c) return set_error(nullptr, LBM_EINVAL, "null handle");
+    if (!f || !g) return set_error(c, LBM_EINVAL, "f and g are required");
+    int rc = pops_io(c, nullptr, nullptr, f, g);
+    if (rc == LBM_OK) c->initialised = true;
+    return rc;
+}
+
+long long lbm_launch_count(const lbm_ctx* c) { return c ? c->launches : 0; }
+
+double lbm_tau_phi(const lbm_ctx* c) { return c ? c->P.tau_phi_d : 0.0; }
+
+const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err : g_create_error; }
+
+void lbm_destroy(lbm_ctx* c) { free_ctx(c); }
+
+int lbm_lattice_tables(int lattice, int* d, int* e, double* w) {
+    if (lattice == LBM_D2Q9) {
+        if (d) *d = lbm::Lat<9>::D;
+        for (int i = 0; i < 9; ++i) {
+            if (e) {
+                e[3 * i] = lbm::Lat<9>::cx(i);
+                e[3 * i + 1] = lbm::Lat<9>::cy(i);
+                e[3 * i + 2] = lbm::Lat<9>::cz(i);
+            }
+            if (w) w[i] = lbm::Lat<9>::wd(i);
+        }
+        return LBM_OK;
+    }
+    if (lattice == LBM_D3Q19) {
+        if (d) *d = lbm::Lat<19>::D;
+        for (int i = 0; i < 19; ++i) {
+            if (e) {
+                e[3 * i] = lbm::Lat<19>::cx(i);
+                e[3 * i + 1] = lbm::Lat<19>::cy(i);
+                e[3 * i + 2] = lbm::Lat<19>::cz(i);
+            }
+            if (w) w[i] = lbm::Lat<19>::wd(i);
+        }
+        return LBM_OK;
+    }
+    return LBM_EINVAL;
+}
+
+}  // extern "C"

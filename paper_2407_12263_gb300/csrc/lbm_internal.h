@@ -1,0 +1,63 @@
+// lbm_internal.h -- parameters and kernel launchers shared by the CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// Scalar parameters of one lattice, derived on the host once (lbm_create / lbm_init_phi).
+struct Params {
+    int Q;                 // 9 or 19
+    int nx, ny, nz;
+    int nxy;               // nx * ny
+    long long N;           // nx * ny * nz
+    float am, a0, ap;      // Lax-Wendroff weights of f*(x - e), f*(x), f*(x + e) (Sec. 2.2)
+    float tau_phi;         // phase-field relaxation time
+    float omega_g;         // 1 / (tau_phi + 1/2)           (Eq. c-n_c)
+    float grad_s;          // tau_phi / (tau_phi + 1/2)      grad phi = grad_s S - grad_k K1
+    float grad_k;          // 1 / ((tau_phi + 1/2) cs^2)
+    float tau_f;           // tau_rho of fluid 2
+    float omega_f;         // 1 / (tau_f + 1/2), used where the kinematic viscosity is uniform
+    float rho2, drho;      // rho2 = 1, drho = rho1 - rho2
+    float mu_m1;           // eta1 / eta2 - 1
+    float sigma;           // surface tension
+    float four_over_delta; // 4 / delta
+    float G[3];            // body force
+    float w0;              // storage shift of f: f_i is held as f_i - t_i w0 (w0 = p0 / cs^2)
+    int general;           // 1 if any of drho, G, mu_m1 is non-zero (selects the full collision)
+    // FP64 copies for the initialisation and the conversions to and from FP64 host arrays
+    double w0d, tau_phi_d, sigma_d, four_over_delta_d, drho_d, rho2_d;
+};
+
+enum Scheme { SCHEME_DF = 0, SCHEME_FD = 1 };
+
+// Launchers (return the launch's cudaError_t). Population buffers are [Q][N] FP32 planes.
+cudaError_t launch_step(const Params& P, int scheme, const float* f_in, const float* g_in,
+                        float* f_out, float* g_out, float* phi_fd, cudaStream_t s, int* launches);
+cudaError_t launch_fd_phi(const Params& P, const float* g_in, float* phi_fd, cudaStream_t s);
+
+// Initial populations for z in [z0, z0 + nzs). phi0s holds planes z0-1 .. z0+nzs of phi0
+// (periodic images for the two halo planes; D2Q9 holds the single plane at index 1);
+// u0s (or nullptr) holds 3 x nzs planes of the velocity for the slab.
+cudaError_t launch_init(const Params& P, int z0, int nzs, const double* phi0s, const double* u0s,
+                        double p0, float* f, float* g, cudaStream_t s);
+
+// Macroscopic fields for z in [z0, z0 + nzs) written as FP64 planes of the slab into out:
+// plane k of field j at out + (j * nzs) * nxy ... see the field order in the definition.
+// mask selects the fields: bit 0 phi, 1 p, 2 u (3 planes), 3 grad phi (3), 4 n (3).
+cudaError_t launch_moments(const Params& P, int scheme, int z0, int nzs, const float* f,
+                           const float* g, const float* phi_fd, int mask, double* out, cudaStream_t s);
+
+// sum phi, sum rho phi (FP64) and the count of non-finite stored populations.
+cudaError_t launch_mass(const Params& P, const float* f, const float* g, double* partials,
+                        int n_partials, double* result /* 3 doubles */, cudaStream_t s);
+int mass_partials_needed(const Params& P);
+
+// Population plane q, slab [z0, z0 + nzs): FP32 device <-> FP64 staging.
+cudaError_t launch_pops_to_f64(const Params& P, const float* src, int q, int is_f, int z0, int nzs,
+                               double* dst, cudaStream_t s);
+cudaError_t launch_pops_from_f64(const Params& P, const double* src, int q, int is_f, int z0, int nzs,
+                                 float* dst, cudaStream_t s);
+
+}  // namespace lbm

@@ -1,0 +1,104 @@
+"""The C-ABI library loads, exports every symbol include/lbm.h declares, and checks its
+arguments on the host (no GPU needed for any of these)."""
+import ctypes
+import re
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2407_12263_gb300 import build as cuda_build
+from paper_2407_12263_gb300 import lbm
+
+ROOT = Path(__file__).resolve().parent.parent
+
+
+@pytest.fixture(scope="module")
+def lib():
+    cuda_build.build()
+    return lbm.load()
+
+
+def _declared_functions():
+    names = []
+    for h in (ROOT / "include").glob("*.h"):
+        text = re.sub(r"/\*.*?\*/", "", h.read_text(), flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[a-z_ ]+\**\s*\**(lbm_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(lib, name), name
+    assert {s[0] for s in lbm.SIGNATURES} >= set(names)
+
+
+def test_library_is_built_for_sm_103a():
+    assert "arch=compute_103a,code=sm_103a" in " ".join(cuda_build.ARCH)
+    assert lbm.library_path().exists()
+
+
+@pytest.mark.parametrize("Q", [9, 19])
+def test_lattice_tables_match_documented_order_and_oracle(lib, Q):
+    d, e, w = lbm.lbm_lattice_tables(Q)
+    do, eo, to = O.lattice(Q)
+    assert d == do
+    np.testing.assert_array_equal(e, eo)
+    np.testing.assert_allclose(w, to, rtol=0, atol=1e-16)
+
+
+def _create(**over):
+    args = dict(grid=(8, 8, 8), lattice=19, tau_f=0.8, tau_g=0.8, M=0.02, xi=4.0, sigma=1e-3,
+                rho_ratio=1.0, mu_ratio=1.0, body_force=(0.0, 0.0, 0.0))
+    args.update(over)
+    return lbm.lbm_create(**args)
+
+
+@pytest.mark.parametrize("over", [
+    dict(lattice=7), dict(grid=(2, 8, 8)), dict(grid=(8, 2, 8)), dict(grid=(8, 8, 2)),
+    dict(lattice=9, grid=(8, 8, 2)), dict(grid=(8, 8, 70000)), dict(grid=(2048, 2048, 1024)),
+    dict(tau_f=0.0), dict(tau_f=float("nan")), dict(M=0.0, tau_g=0.0), dict(M=-1.0, tau_g=-1.0),
+    dict(xi=1.5), dict(xi=float("inf")), dict(sigma=-1e-3), dict(rho_ratio=0.0), dict(mu_ratio=-2.0),
+    dict(body_force=(0.0, float("nan"), 0.0)), dict(lattice=9, grid=(8, 8, 1), body_force=(0.0, 0.0, 1e-5)),
+])
+def test_create_rejects_invalid_arguments(lib, over):
+    with pytest.raises(lbm.LBMError) as exc:
+        _create(**over)
+    assert exc.value.status == lbm.LBM_EINVAL
+    assert lbm.lbm_last_error(None) != "no error"
+
+
+@pytest.mark.parametrize("field,value", [("scheme", 5), ("storage", 1), ("walls", 1), ("courant", 0.0),
+                                         ("courant", 1.5)])
+def test_create_rejects_invalid_options(lib, field, value):
+    o = lbm.lbm_default_opts()
+    setattr(o, field, value)
+    with pytest.raises(lbm.LBMError) as exc:
+        _create(opts=o)
+    assert exc.value.status == lbm.LBM_EINVAL
+
+
+def test_default_options(lib):
+    o = lbm.lbm_default_opts()
+    assert (o.scheme, o.storage, o.courant, o.walls) == (0, 0, 0.997, 0)
+    assert o.stream is None
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    assert lib.lbm_step(None, 1) == lbm.LBM_EINVAL
+    assert lib.lbm_mass(None, None, None) == lbm.LBM_EINVAL
+    assert lib.lbm_launch_count(None) == 0
+    lib.lbm_destroy(None)
+    out = ctypes.c_void_p()
+    assert lib.lbm_create(ctypes.byref(out), None, 19, 0.8, 0.8, 0.02, 4.0, 1e-3, 1.0, 1.0, None, None) == lbm.LBM_EINVAL
+    assert lib.lbm_create(None, None, 19, 0.8, 0.8, 0.02, 4.0, 1e-3, 1.0, 1.0, None, None) == lbm.LBM_EINVAL
+
+
+def test_product_path_does_not_import_the_oracle():
+    pkg = ROOT / "paper_2407_12263_gb300"
+    for src in list(pkg.rglob("*.py")) + list(pkg.rglob("*.cu")) + list(pkg.rglob("*.cuh")) + list(pkg.rglob("*.h")):
+        text = src.read_text()
+        assert "import oracle" not in text and "from oracle" not in text and "lbm_oracle" not in text, src

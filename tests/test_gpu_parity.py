@@ -1,0 +1,244 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element.
+
+Tolerances (FP32 arithmetic and storage against FP64): max |phi_gpu - phi_oracle| <= 1e-4,
+||u_gpu - u_oracle||_2 / ||u_oracle||_2 <= 1e-3, relative drift of sum phi <= 1e-7. Pressure
+and populations get absolute bounds derived from FP32 rounding of values of order t_i.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2407_12263_gb300 import build as cuda_build
+from paper_2407_12263_gb300 import inputs as I
+from paper_2407_12263_gb300 import lbm
+
+pytestmark = pytest.mark.gpu
+
+PHI_TOL, U_REL_TOL, MASS_DRIFT_TOL = 1e-4, 1e-3, 1e-7
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    cuda_build.build()
+    lbm.load()
+
+
+def _pair(Q, grid, phi0, u0=None, p0=1.0 / 3.0, scheme=0, courant=0.997, **params):
+    base = dict(tau_f=0.8, tau_g=0.8, M=0.02, xi=4.0, sigma=1e-3, rho_ratio=1.0, mu_ratio=1.0,
+                body_force=(0.0, 0.0, 0.0))
+    base.update(params)
+    gpu = lbm.Lattice(grid, Q, scheme=scheme, courant=courant, **base)
+    ref = O.Oracle(Q, grid, scheme=scheme, courant=courant, **base)
+    gpu.init_phi(phi0, u0, p0)
+    ref.init_phi(phi0, u0, p0)
+    return gpu, ref
+
+
+def _compare(gpu, ref, u_abs=0.0):
+    phi_g, p_g, u_g = gpu.moments()
+    phi_o, p_o, u_o = ref.moments()
+    err_phi = np.abs(phi_g - phi_o).max()
+    nu = np.linalg.norm(u_o)
+    err_u = np.linalg.norm(u_g - u_o) / nu if nu > 0 else np.linalg.norm(u_g)
+    err_p = np.abs(p_g - p_o).max()
+    assert err_phi <= PHI_TOL, err_phi
+    assert err_u <= U_REL_TOL or np.abs(u_g - u_o).max() <= u_abs, err_u
+    assert err_p <= 1e-6, err_p
+    return err_phi, err_u, err_p
+
+
+GENERAL = dict(rho_ratio=3.0, mu_ratio=2.0, body_force=(2e-5, -1e-5, 1.5e-5))
+
+
+# ---------------------------------------------------------------- initial state
+@pytest.mark.parametrize("Q,grid", [(9, (37, 21, 1)), (19, (37, 21, 11))])
+def test_initial_populations_match(Q, grid):
+    phi0 = I.multi_droplet_phi(grid, seed=11, count=3, r_range=(3.0, 6.0), xi=4.0)
+    u0 = I.smooth_velocity(grid, seed=12, amplitude=0.03)
+    if Q == 9:
+        u0[2] = 0
+    gen = dict(GENERAL)
+    if Q == 9:
+        gen["body_force"] = (2e-5, -1e-5, 0.0)
+    gpu, ref = _pair(Q, grid, phi0, u0, 0.3, **gen)
+    fg, gg = gpu.get_pops()
+    fo, go = ref.get_pops()
+    # FP32 storage of values of order t_i (f shifted by t_i w0 on the device, restored exactly)
+    np.testing.assert_allclose(gg, go, rtol=0, atol=4e-8)
+    np.testing.assert_allclose(fg, fo, rtol=0, atol=4e-8)
+
+
+# ---------------------------------------------------------------- stepping
+@pytest.mark.parametrize("scheme", [0, 1])
+@pytest.mark.parametrize("Q,grid,R", [(9, (64, 64, 1), 16.0), (19, (32, 32, 32), 8.0)])
+def test_static_droplet_parity(Q, grid, R, scheme):
+    """The droplet workloads (2D 64^2 R = 16 and a 32^3 copy of the 3D one), 300 steps."""
+    phi0 = I.droplet_phi(grid, R, 4.0)
+    gpu, ref = _pair(Q, grid, phi0, scheme=scheme)
+    s0 = gpu.mass()[0]
+    gpu.step(300)
+    ref.step(300)
+    _compare(gpu, ref, u_abs=1e-9)
+    assert abs(gpu.mass()[0] - s0) / s0 <= MASS_DRIFT_TOL
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+@pytest.mark.parametrize("Q,grid", [(9, (45, 39, 1)), (19, (37, 21, 19))])
+def test_ragged_grid_all_terms_parity(Q, grid, scheme):
+    """Ragged extents (not multiples of the 32 x 4 thread block), density and viscosity ratio,
+    body force and a non-zero initial velocity: every term of the collision is exercised."""
+    phi0 = I.multi_droplet_phi(grid, seed=21, count=3, r_range=(3.0, 7.0), xi=4.0)
+    u0 = I.smooth_velocity(grid, seed=22, amplitude=0.03)
+    gen = dict(GENERAL)
+    if Q == 9:
+        u0[2] = 0
+        gen["body_force"] = (2e-5, -1e-5, 0.0)
+    gpu, ref = _pair(Q, grid, phi0, u0, **gen)
+    gpu.step(150)
+    ref.step(150)
+    _compare(gpu, ref)
+    gg, ng = gpu.gradients()
+    go, no = ref.gradients()
+    phi = ref.moments()[0]
+    band = (phi > 0.05) & (phi < 0.95)
+    assert np.abs(gg - go).max() <= 1e-4
+    assert np.abs(ng[:, band] - no[:, band]).max() <= 1e-3
+
+
+def test_one_step_populations_match():
+    grid = (21, 13, 9)
+    phi0 = I.multi_droplet_phi(grid, seed=31, count=2, r_range=(3.0, 5.0), xi=4.0)
+    u0 = I.smooth_velocity(grid, seed=32, amplitude=0.03)
+    gpu, ref = _pair(19, grid, phi0, u0, **GENERAL)
+    gpu.step(1)
+    ref.step(1)
+    fg, gg = gpu.get_pops()
+    fo, go = ref.get_pops()
+    np.testing.assert_allclose(gg, go, rtol=0, atol=2e-7)
+    np.testing.assert_allclose(fg, fo, rtol=0, atol=2e-7)
+
+
+def test_unit_courant_and_other_relaxation_times():
+    grid = (24, 20, 16)
+    phi0 = I.droplet_phi(grid, 6.0, 4.0)
+    for courant, tau_f, tau_g, M in ((1.0, 0.8, 0.8, 0.02), (0.9, 0.3, 1.5, 0.0), (0.997, 2.0, 0.06, 0.0)):
+        gpu, ref = _pair(19, grid, phi0, courant=courant, tau_f=tau_f, tau_g=tau_g, M=M)
+        assert gpu.tau_phi == pytest.approx(ref.tau_phi, rel=1e-15)
+        gpu.step(100)
+        ref.step(100)
+        _compare(gpu, ref, u_abs=1e-9)
+
+
+# ---------------------------------------------------------------- full size
+def test_full_size_droplet_parity():
+    """The 3D workload at its full size (D3Q19, 128^3, R = 24, xi = 4) in the launch configuration
+    the benchmark times: every cell after 4 steps, plus phi conservation over 200 steps."""
+    w = I.WORKLOADS["droplet3d_128"]
+    phi0 = I.droplet_phi(w["grid"], w["R"], w["xi"])
+    gpu, ref = _pair(19, w["grid"], phi0)
+    s0 = gpu.mass()[0]
+    gpu.step(4)
+    ref.step(4)
+    _compare(gpu, ref, u_abs=1e-9)
+    gpu.step(196)
+    s1 = gpu.mass()[0]
+    assert abs(s1 - s0) / s0 <= MASS_DRIFT_TOL
+
+
+# ---------------------------------------------------------------- edge cases
+@pytest.mark.parametrize("Q,grid", [(9, (3, 3, 1)), (19, (3, 3, 3)), (19, (3, 5, 4)), (9, (3, 200, 1))])
+def test_minimum_grids(Q, grid):
+    phi0 = I.sine_phi(grid, 0.5, 0.3, axis=1)
+    u0 = I.smooth_velocity(grid, seed=41, amplitude=0.02)
+    if Q == 9:
+        u0[2] = 0
+    gpu, ref = _pair(Q, grid, phi0, u0)
+    gpu.step(30)
+    ref.step(30)
+    _compare(gpu, ref)
+
+
+def test_zero_steps_and_state_errors():
+    grid = (8, 8, 8)
+    g = lbm.Lattice(grid, 19, 0.8, 0.8, 0.02, 4.0, 1e-3)
+    with pytest.raises(lbm.LBMError) as e:
+        g.step(1)
+    assert e.value.status == lbm.LBM_ESTATE
+    with pytest.raises(lbm.LBMError) as e:
+        g.mass()
+    assert e.value.status == lbm.LBM_ESTATE
+    g.init_phi(I.droplet_phi(grid, 2.5, 4.0))
+    f0, g0 = g.get_pops()
+    g.step(0)
+    f1, g1 = g.get_pops()
+    np.testing.assert_array_equal(f0, f1)
+    with pytest.raises(lbm.LBMError) as e:
+        g.step(-1)
+    assert e.value.status == lbm.LBM_EINVAL
+    with pytest.raises(lbm.LBMError) as e:
+        g.init_phi(np.zeros(g.shape), None, 0.0)
+    assert e.value.status == lbm.LBM_EINVAL
+
+
+def test_set_get_roundtrip_and_nonfinite_detection():
+    grid = (10, 9, 8)
+    g = lbm.Lattice(grid, 19, 0.8, 0.8, 0.02, 4.0, 1e-3)
+    rng = np.random.default_rng(5)
+    _, _, t = O.lattice(19)
+    f = t[:, None, None, None] * (1 + 0.01 * rng.standard_normal((19,) + g.shape))
+    gg = t[:, None, None, None] * rng.uniform(0, 1, (19,) + g.shape)
+    g.set_pops(f, gg)
+    f1, g1 = g.get_pops()
+    np.testing.assert_allclose(f1, f, rtol=0, atol=1e-8)
+    np.testing.assert_allclose(g1, gg, rtol=0, atol=1e-8)
+    g.mass()
+    f[7, 3, 4, 5] = np.nan            # injected on the host
+    g.set_pops(f, gg)
+    with pytest.raises(lbm.LBMError) as e:
+        g.mass()
+    assert e.value.status == lbm.LBM_ENONFINITE
+
+
+def test_launch_count_is_one_kernel_per_step():
+    grid = (16, 16, 16)
+    for scheme, per_step in ((0, 1), (1, 2)):
+        g = lbm.Lattice(grid, 19, 0.8, 0.8, 0.02, 4.0, 1e-3, scheme=scheme)
+        g.init_phi(I.droplet_phi(grid, 4.0, 4.0))
+        n0 = g.launch_count
+        g.step(10)
+        assert g.launch_count - n0 == 10 * per_step
+
+
+# ---------------------------------------------------------------- physics on the GPU
+def test_laplace_law_3d_full_size():
+    """3D static droplet, 128^3, R = 24, 5000 steps: p_in - p_out = 2 sigma / R_eff within 5%,
+    sum phi drift <= 1e-7, spurious currents small."""
+    w = I.WORKLOADS["droplet3d_128"]
+    grid, R, xi = w["grid"], w["R"], w["xi"]
+    g = lbm.Lattice(grid, 19, w["tau_f"], w["tau_g"], w["M"], xi, w["sigma"])
+    g.init_phi(I.droplet_phi(grid, R, xi))
+    s0 = g.mass()[0]
+    g.step(w["steps"])
+    phi, p, u = g.moments()
+    r = I.periodic_distance(grid, (63.5, 63.5, 63.5))
+    jump = p[r < R - 2 * xi].mean() - p[r > R + 2 * xi].mean()
+    r_eff = ((1 - phi).sum() * 3 / (4 * np.pi)) ** (1 / 3)
+    assert jump == pytest.approx(2 * w["sigma"] / r_eff, rel=0.05)
+    assert abs(g.mass()[0] - s0) / s0 <= MASS_DRIFT_TOL
+    assert np.abs(u).max() < 1e-4
+
+
+def test_difference_free_and_fd_normals_agree_on_gpu():
+    grid, R, xi = (48, 48, 48), 12.0, 4.0
+    out = {}
+    for scheme in (0, 1):
+        g = lbm.Lattice(grid, 19, 0.8, 0.8, 0.02, xi, 1e-3, scheme=scheme)
+        g.init_phi(I.droplet_phi(grid, R, xi))
+        g.step(200)
+        out[scheme] = (g.moments()[0],) + g.gradients()
+    phi = out[0][0]
+    band = (phi > 0.1) & (phi < 0.9)
+    cosang = (out[0][2][:, band] * out[1][2][:, band]).sum(0)
+    assert np.degrees(np.arccos(np.clip(cosang.min(), -1, 1))) < 5.0
+    g0, g1 = out[0][1][:, band], out[1][1][:, band]
+    assert np.linalg.norm(g0 - g1) / np.linalg.norm(g1) < 4 / (3 * xi * xi) + 0.02
