@@ -58,6 +58,7 @@ __global__ void init_kernel(const Params P, int z0, const double* __restrict__ p
 
     const size_t N = (size_t)P.N;
     const size_t c = (size_t)(z0 + zl) * P.nxy + (size_t)y * P.nx + x;
+    double fsum = 0.0, gsum = 0.0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const double t = Lat<Q>::wd(i);
@@ -67,11 +68,17 @@ __global__ void init_kernel(const Params P, int z0, const double* __restrict__ p
         const double eg = Lat<Q>::cx(i) * gx + Lat<Q>::cy(i) * gy + Lat<Q>::cz(i) * gz;
         const double gam = 3.0 * eu + 4.5 * eu * eu - 1.5 * u2;
         const double pis = sg * ((double)Lat<Q>::e2(i) - en * en - trc / 3.0);
-        const double feq_shifted = t * (3.0 * p0 - P.w0d + rho * gam - 4.5 * pis);
+        const double fstar = t * (3.0 * p0 + rho * gam - 4.5 * pis);
         const double gstar = t * (phi * (1.0 + gam) + P.tau_phi_d * es) - t * (P.tau_phi_d - 0.5) * eg;
-        f[i * N + c] = (float)feq_shifted;
-        g[i * N + c] = (float)gstar;
+        fsum += fstar;
+        gsum += gstar;
+        if (i > 0) {
+            f[i * N + c] = (float)(fstar - t * P.w0d);
+            g[i * N + c] = (float)(gstar - t * P.phi_ref_d);
+        }
     }
+    f[c] = (float)(fsum - P.w0d);      // plane 0: zeroth moments of the shifted sets
+    g[c] = (float)(gsum - P.phi_ref_d);
 }
 
 cudaError_t launch_init(const Params& P, int z0, int nzs, const double* phi0s, const double* u0s,
@@ -108,10 +115,10 @@ __global__ void moments_kernel(const Params P, int z0, const float* __restrict__
         fd_gradient<Q>(phi_fd, c, nb, gx, gy, gz);
         macro_interface_fd(P, gx, gy, gz, m);
     }
-    macro_pressure<Q, GEN>(P, fb, m);
+    macro_pressure<GEN>(P, m);
     const size_t slab = (size_t)gridDim.z * P.nxy;
     const size_t l = (size_t)zl * P.nxy + (size_t)y * P.nx + x;
-    if (mask & 1) out[l] = (double)m.phi;
+    if (mask & 1) out[l] = P.phi_ref_d + (double)m.Phi;
     if (mask & 2) out[slab + l] = (P.w0d + (double)m.P) / 3.0;  // p = cs^2 (w0 + P)
     for (int a = 0; a < 3; ++a) {
         if (mask & 4) out[(2 + a) * slab + l] = (double)m.u[a];
@@ -186,7 +193,7 @@ mass_kernel(const Params P, const float* __restrict__ f, const float* __restrict
         const Nbr nb = make_nbr(P, x, y, z);
         float fb[Q], gb[Q];
         pull<Q, false>(P, nullptr, g, (int)c, nb, fb, gb);
-        const double phi = (double)sum_phi<Q>(gb);
+        const double phi = P.phi_ref_d + (double)gb[0];
         acc[0] += phi;
         acc[1] += (P.rho2_d + P.drho_d * phi) * phi;
         int bad = 0;
@@ -219,33 +226,41 @@ cudaError_t launch_mass(const Params& P, const float* f, const float* g, double*
 }
 
 // ---------------------------------------------------------------------------------------
-// Population plane <-> FP64 staging (the f shift t_i w0 is added back on the way out).
+// Device storage <-> plain FP64 populations, all Q planes of a slab (staging [Q][nzs * nxy]).
+// Plane i >= 1: v_i + t_i ref; plane 0: the rest population (ref + v_0) - sum_{i>=1} f_i.
 // ---------------------------------------------------------------------------------------
 template <int Q>
-__device__ __forceinline__ double shift_of(int q, double w0) {
-    double t = 0.0;
-#pragma unroll
-    for (int i = 0; i < Q; ++i)
-        if (i == q) t = Lat<Q>::wd(i);
-    return t * w0;
-}
-
-template <int Q>
-__global__ void pops_to_f64(const Params P, const float* __restrict__ src, int q, int is_f, int z0, int nzs,
+__global__ void pops_to_f64(const Params P, const float* __restrict__ src, int is_f, int z0, int nzs,
                             double* __restrict__ dst) {
-    const size_t n = (size_t)nzs * P.nxy, base = (size_t)z0 * P.nxy;
-    const double sh = is_f ? shift_of<Q>(q, P.w0d) : 0.0;
-    for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (size_t)gridDim.x * blockDim.x)
-        dst[l] = (double)src[(size_t)q * P.N + base + l] + sh;
+    const size_t n = (size_t)nzs * P.nxy, base = (size_t)z0 * P.nxy, N = (size_t)P.N;
+    const double ref = is_f ? P.w0d : P.phi_ref_d;
+    for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (size_t)gridDim.x * blockDim.x) {
+        double rest = ref + (double)src[base + l];
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const double v = (double)src[i * N + base + l] + Lat<Q>::wd(i) * ref;
+            dst[i * n + l] = v;
+            rest -= v;
+        }
+        dst[l] = rest;
+    }
 }
 
 template <int Q>
-__global__ void pops_from_f64(const Params P, const double* __restrict__ src, int q, int is_f, int z0, int nzs,
+__global__ void pops_from_f64(const Params P, const double* __restrict__ src, int is_f, int z0, int nzs,
                               float* __restrict__ dst) {
-    const size_t n = (size_t)nzs * P.nxy, base = (size_t)z0 * P.nxy;
-    const double sh = is_f ? shift_of<Q>(q, P.w0d) : 0.0;
-    for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (size_t)gridDim.x * blockDim.x)
-        dst[(size_t)q * P.N + base + l] = (float)(src[l] - sh);
+    const size_t n = (size_t)nzs * P.nxy, base = (size_t)z0 * P.nxy, N = (size_t)P.N;
+    const double ref = is_f ? P.w0d : P.phi_ref_d;
+    for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (size_t)gridDim.x * blockDim.x) {
+        double sum = src[l];
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const double v = src[i * n + l];
+            sum += v;
+            dst[i * N + base + l] = (float)(v - Lat<Q>::wd(i) * ref);
+        }
+        dst[base + l] = (float)(sum - ref);
+    }
 }
 
 static unsigned conv_blocks(const Params& P, int nzs) {
@@ -254,17 +269,17 @@ static unsigned conv_blocks(const Params& P, int nzs) {
     return (unsigned)(b < 4096 ? b : 4096);
 }
 
-cudaError_t launch_pops_to_f64(const Params& P, const float* src, int q, int is_f, int z0, int nzs, double* dst,
+cudaError_t launch_pops_to_f64(const Params& P, const float* src, int is_f, int z0, int nzs, double* dst,
                                cudaStream_t s) {
-    if (P.Q == 9) pops_to_f64<9><<<conv_blocks(P, nzs), 256, 0, s>>>(P, src, q, is_f, z0, nzs, dst);
-    else pops_to_f64<19><<<conv_blocks(P, nzs), 256, 0, s>>>(P, src, q, is_f, z0, nzs, dst);
+    if (P.Q == 9) pops_to_f64<9><<<conv_blocks(P, nzs), 256, 0, s>>>(P, src, is_f, z0, nzs, dst);
+    else pops_to_f64<19><<<conv_blocks(P, nzs), 256, 0, s>>>(P, src, is_f, z0, nzs, dst);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pops_from_f64(const Params& P, const double* src, int q, int is_f, int z0, int nzs, float* dst,
+cudaError_t launch_pops_from_f64(const Params& P, const double* src, int is_f, int z0, int nzs, float* dst,
                                  cudaStream_t s) {
-    if (P.Q == 9) pops_from_f64<9><<<conv_blocks(P, nzs), 256, 0, s>>>(P, src, q, is_f, z0, nzs, dst);
-    else pops_from_f64<19><<<conv_blocks(P, nzs), 256, 0, s>>>(P, src, q, is_f, z0, nzs, dst);
+    if (P.Q == 9) pops_from_f64<9><<<conv_blocks(P, nzs), 256, 0, s>>>(P, src, is_f, z0, nzs, dst);
+    else pops_from_f64<19><<<conv_blocks(P, nzs), 256, 0, s>>>(P, src, is_f, z0, nzs, dst);
     return cudaGetLastError();
 }
 

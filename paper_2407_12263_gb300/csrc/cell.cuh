@@ -1,11 +1,21 @@
 // cell.cuh -- per-cell device code of the difference-free conservative phase-field LBM
 // (Zhao, Patel & Lee, arXiv:2407.12263): Lax-Wendroff pull, macroscopic stage, collisions.
 //
-// Storage: FP32 planes [Q][N]. f is held as the deviation f_i - t_i w0 from the lattice
-// weights times the reference pressure level w0 = p0 / cs^2; propagation and collision are
-// linear with weights summing to one, so the shift passes through them unchanged and every
-// FP32 value on the f path is a small deviation rather than a number of order t_i. g is held
-// as is. All arithmetic is FP32 with constants folded (1/cs^2 = 3, 1/(2 cs^4) = 4.5).
+// Storage (FP32 planes [Q][N]). Plane i >= 1 holds the population shifted by its lattice
+// weight times a reference level, f_i - t_i w0 (w0 = p0 / cs^2) and g_i - t_i phi_ref
+// (phi_ref = 0 or 1, the bulk phase that fills most of the grid). Plane 0 holds the zeroth
+// moment of the shifted set, sum_i f_i - w0 and phi - phi_ref, in place of the rest
+// population, which it fixes exactly (f_0 = sum_i f_i - sum_{i>=1} f_i). Both choices are
+// exact changes of variables:
+//  * propagation and collision are linear with weights summing to one, so the shift passes
+//    through them, and every FP32 value is a deviation instead of a number of order t_i;
+//  * the rest population does not move and the collision conserves the zeroth moment, so
+//    phi_new(x) = phi*(x) + sum_{i>=1} [LW(g*_i)(x) - g*_i(x)] and the collision leaves it alone.
+//    In FP32 this removes the per-step bias that rounding t_i-weighted sums would add to phi
+//    in every cell, and a uniform region is an exact fixed point of the update.
+// The Lax-Wendroff update is evaluated in difference form for the same reason: it returns a
+// uniform field unchanged bit for bit. All arithmetic is FP32 with constants folded
+// (1/cs^2 = 3, 1/(2 cs^4) = 4.5).
 #pragma once
 
 #include "lattice.cuh"
@@ -39,53 +49,56 @@ __device__ __forceinline__ int link_offset(const Nbr& n, int i, int s) {
            (ez > 0 ? n.zp : ez < 0 ? n.zm : 0);
 }
 
-// Lax-Wendroff propagation (Sec. 2.2) of both sets into registers:
-// fbar_i(x) = a- f*_i(x - e_i) + a0 f*_i(x) + a+ f*_i(x + e_i), the same for g.
+// Lax-Wendroff propagation (Sec. 2.2) into registers:
+//   fbar_i(x) = f*_i(x) - c [f*_i(x) - f*_i(x - e_i)] - c(1-c)/2 [f*_i(x + e_i) - 2 f*_i(x) + f*_i(x - e_i)]
+//             = f*_i(x) + lw_m [f*_i(x - e_i) - f*_i(x)] + lw_p [f*_i(x + e_i) - f*_i(x)],
+// and the zeroth moments fb[0] = sum fbar - w0, gb[0] = phi - phi_ref of the propagated state.
 template <int Q, bool WITH_F>
 __device__ __forceinline__ void pull(const Params& P, const float* __restrict__ f,
                                      const float* __restrict__ g, int c, const Nbr& nb,
                                      float (&fb)[Q], float (&gb)[Q]) {
     const size_t N = (size_t)P.N;
+    float df = 0.f, dg = 0.f;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
+    for (int i = 1; i < Q; ++i) {
+        const int cm = c + link_offset<Q>(nb, i, -1);
+        const int cp = c + link_offset<Q>(nb, i, +1);
         const float* gq = g + i * N;
-        if (i == 0) {
-            if (WITH_F) fb[0] = __ldg(f + c);
-            gb[0] = __ldg(gq + c);
-        } else {
-            const int cm = c + link_offset<Q>(nb, i, -1);
-            const int cp = c + link_offset<Q>(nb, i, +1);
-            if (WITH_F) {
-                const float* fq = f + i * N;
-                fb[i] = P.am * __ldg(fq + cm) + P.a0 * __ldg(fq + c) + P.ap * __ldg(fq + cp);
-            }
-            gb[i] = P.am * __ldg(gq + cm) + P.a0 * __ldg(gq + c) + P.ap * __ldg(gq + cp);
+        const float g0 = __ldg(gq + c);
+        const float d = P.lw_m * (__ldg(gq + cm) - g0) + P.lw_p * (__ldg(gq + cp) - g0);
+        gb[i] = g0 + d;
+        dg += d;
+        if (WITH_F) {
+            const float* fq = f + i * N;
+            const float f0 = __ldg(fq + c);
+            const float e = P.lw_m * (__ldg(fq + cm) - f0) + P.lw_p * (__ldg(fq + cp) - f0);
+            fb[i] = f0 + e;
+            df += e;
         }
     }
-}
-
-template <int Q>
-__device__ __forceinline__ float sum_phi(const float (&gb)[Q]) {
-    float phi = 0.f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) phi += gb[i];
-    return phi;
+    gb[0] = __ldg(g + c) + dg;
+    if (WITH_F) fb[0] = __ldg(f + c) + df;
 }
 
 struct Macro {
-    float phi, rho, inv_rho;
+    float Phi;    // phi - phi_ref
+    float phi, omphi, rho, inv_rho;
     float u[3];
     float n[3];
     float S[3];
     float gphi[3];
-    float P;      // p / cs^2 - w0 = sum (f_i - t_i w0) + u . grad rho / 2
+    float Pbar;   // sum fbar - w0
+    float P;      // p / cs^2 - w0 = sum fbar - w0 + u . grad rho / 2
     float gnorm;  // |grad phi|
 };
 
 // phi, rho, u (Sec. 2.3, Eq. momentum): rho u = sum fbar_i e_i + rho G / 2.
 template <int Q, bool GEN>
 __device__ __forceinline__ void macro_flow(const Params& P, const float (&fb)[Q], const float (&gb)[Q], Macro& m) {
-    m.phi = sum_phi<Q>(gb);
+    m.Phi = gb[0];
+    m.phi = P.phi_ref + m.Phi;
+    m.omphi = (1.f - P.phi_ref) - m.Phi;  // 1 - phi, exact on the phi_ref side
+    m.Pbar = fb[0];
     float jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
@@ -113,7 +126,8 @@ __device__ __forceinline__ void macro_flow(const Params& P, const float (&fb)[Q]
 
 // Interface normal, sharpening flux and gradients from the first central moment of g
 // (Sec. 2.3, Eq. norm): K1 = sum g_i e_i - phi u, n = -K1/|K1|, S = 4 phi (1-phi)/delta n,
-// grad phi = (tau_phi cs^2 S - K1) / ((tau_phi + 1/2) cs^2).
+// grad phi = (tau_phi cs^2 S - K1) / ((tau_phi + 1/2) cs^2). The shift t_i phi_ref has no
+// first moment, so the stored deviations give K1 directly.
 template <int Q>
 __device__ __forceinline__ void macro_interface_df(const Params& P, const float (&gb)[Q], Macro& m) {
     float kx = 0.f, ky = 0.f, kz = 0.f;
@@ -134,7 +148,7 @@ __device__ __forceinline__ void macro_interface_df(const Params& P, const float 
     m.n[0] = kx * r;
     m.n[1] = ky * r;
     m.n[2] = kz * r;
-    const float smag = P.four_over_delta * m.phi * (1.f - m.phi);
+    const float smag = P.four_over_delta * m.phi * m.omphi;
     m.S[0] = smag * m.n[0];
     m.S[1] = smag * m.n[1];
     m.S[2] = smag * m.n[2];
@@ -153,26 +167,24 @@ __device__ __forceinline__ void macro_interface_fd(const Params& P, float gx, fl
     m.n[0] = gx * r;
     m.n[1] = gy * r;
     m.n[2] = gz * r;
-    const float smag = P.four_over_delta * m.phi * (1.f - m.phi);
+    const float smag = P.four_over_delta * m.phi * m.omphi;
     m.S[0] = smag * m.n[0];
     m.S[1] = smag * m.n[1];
     m.S[2] = smag * m.n[2];
 }
 
 // Pressure (Eq. pressure): p/cs^2 = sum fbar_i + u . grad rho / 2, held as P = p/cs^2 - w0.
-template <int Q, bool GEN>
-__device__ __forceinline__ void macro_pressure(const Params& P, const float (&fb)[Q], Macro& m) {
-    float s = 0.f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) s += fb[i];
-    if (GEN) s += 0.5f * P.drho * (m.u[0] * m.gphi[0] + m.u[1] * m.gphi[1] + m.u[2] * m.gphi[2]);
-    m.P = s;
+template <bool GEN>
+__device__ __forceinline__ void macro_pressure(const Params& P, Macro& m) {
+    m.P = m.Pbar;
+    if (GEN) m.P += 0.5f * P.drho * (m.u[0] * m.gphi[0] + m.u[1] * m.gphi[1] + m.u[2] * m.gphi[2]);
     m.gnorm = sqrtf(m.gphi[0] * m.gphi[0] + m.gphi[1] * m.gphi[1] + m.gphi[2] * m.gphi[2]);
 }
 
 // Isotropic central difference of the propagated phi field (Sec. 3.4):
 // grad phi = sum_{i != 0} t_i e_i [phi(x + e_i) - phi(x - e_i)] / (2 cs^2)
 //          = 3 sum_{i != 0} t_i e_i phi(x + e_i)   (the velocity set is symmetric).
+// The plane holds phi - phi_ref; the constant drops out of the difference.
 template <int Q>
 __device__ __forceinline__ void fd_gradient(const float* __restrict__ phi, int c, const Nbr& nb,
                                             float& gx, float& gy, float& gz) {
@@ -204,7 +216,7 @@ __device__ __forceinline__ float edot(int i, const float (&v)[3]) {
     return r;
 }
 
-// Collisions, in place on fb / gb.
+// Collisions, in place on fb / gb (shifted values, i >= 1):
 //   f^eq_i - t_i w0 = t_i [P + rho gam_i - 4.5 Pi_s:(e_i e_i - cs^2 I)]            (Eq. geq_s,
 //        gam_i = 3 e.u + 4.5 (e.u)^2 - 1.5 u^2, the CSS term entering with a minus sign so that
 //        the second moment is p I + rho u u - Pi_s as App. A requires)
@@ -212,8 +224,10 @@ __device__ __forceinline__ float edot(int i, const float (&v)[3]) {
 //   S_i = t_i gam_i (e_i - u) . grad rho                                                 (App. A)
 //   R_i = t_i [3 (e_i - u) + 9 (e_i . u) e_i] . rho G                                    (Eq. body)
 //   f*_i = fbar_i - omega_rho (fbar_i - f^eq_i + F_i/2) + F_i                           (Eq. c-n_m)
-//   g^eq_i = t_i [phi (1 + gam_i) + tau_phi e_i . S]                                     (Eq. geq)
+//   g^eq_i - t_i phi_ref = t_i [(phi - phi_ref) + phi gam_i + tau_phi e_i . S]          (Eq. geq)
 //   g*_i = g_i - omega_g (g_i - g^eq_i)                                                  (Eq. c-n_c)
+// Zeroth moments: the g collision conserves phi; sum_i f*_i = sum_i fbar_i + u . grad rho,
+// because sum_i F_i = u . grad rho and sum_i f^eq_i = p / cs^2.
 template <int Q, bool GEN>
 __device__ __forceinline__ void collide(const Params& P, const Macro& m, float (&fb)[Q], float (&gb)[Q]) {
     constexpr int D = Lat<Q>::D;
@@ -232,7 +246,7 @@ __device__ __forceinline__ void collide(const Params& P, const Macro& m, float (
     }
     const float omega_g = P.omega_g;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
+    for (int i = 1; i < Q; ++i) {
         const float t = Lat<Q>::w(i);
         const float eu = edot<Q>(i, m.u);
         const float en = edot<Q>(i, m.n);
@@ -248,9 +262,11 @@ __device__ __forceinline__ void collide(const Params& P, const Macro& m, float (
         } else {
             fb[i] = fb[i] - omega_f * (fb[i] - feq);
         }
-        const float geq = t * (m.phi * (1.f + gam) + P.tau_phi * es);
+        const float geq = t * (m.Phi + m.phi * gam + P.tau_phi * es);
         gb[i] = gb[i] - omega_g * (gb[i] - geq);
     }
+    gb[0] = m.Phi;
+    fb[0] = GEN ? m.Pbar + ugr : m.Pbar;
 }
 
 }  // namespace lbm

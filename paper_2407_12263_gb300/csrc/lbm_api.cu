@@ -175,9 +175,8 @@ int lbm_create(lbm_ctx** out, const int grid[3], int lattice, double tau_f, doub
     P.nz = nz;
     P.nxy = nx * ny;
     P.N = N;
-    P.am = (float)(0.5 * cc * (1.0 + cc));   // weight of f*(x - e)
-    P.a0 = (float)(1.0 - cc * cc);           // weight of f*(x)
-    P.ap = (float)(-0.5 * cc * (1.0 - cc));  // weight of f*(x + e)
+    P.lw_m = (float)(0.5 * cc * (1.0 + cc));   // c - c(1-c)/2: weight of f*(x - e) - f*(x)
+    P.lw_p = (float)(-0.5 * cc * (1.0 - cc));  // -c(1-c)/2:    weight of f*(x + e) - f*(x)
     P.tau_phi = (float)tau_phi;
     P.omega_g = (float)(1.0 / (tau_phi + 0.5));
     P.grad_s = (float)(tau_phi / (tau_phi + 0.5));
@@ -190,9 +189,11 @@ int lbm_create(lbm_ctx** out, const int grid[3], int lattice, double tau_f, doub
     P.sigma = (float)sigma;
     P.four_over_delta = (float)(4.0 / xi);
     for (int a = 0; a < 3; ++a) P.G[a] = (float)G[a];
-    P.w0 = 1.0f;  // p0 = cs^2 until lbm_init_phi sets it
+    P.w0 = 1.0f;       // p0 = cs^2 until lbm_init_phi sets it
+    P.phi_ref = 1.0f;  // until lbm_init_phi picks the bulk phase of phi0
     P.general = (rho_ratio != 1.0 || mu_ratio != 1.0 || G[0] != 0 || G[1] != 0 || G[2] != 0) ? 1 : 0;
     P.w0d = 1.0;
+    P.phi_ref_d = 1.0;
     P.tau_phi_d = tau_phi;
     P.sigma_d = sigma;
     P.four_over_delta_d = 4.0 / xi;
@@ -248,6 +249,13 @@ int lbm_init_phi(lbm_ctx* c, const double* phi0, const double* u0, double p0) {
     Params& P = c->P;
     P.w0d = p0 * 3.0;  // w0 = p0 / cs^2: the level the f storage is shifted by
     P.w0 = (float)P.w0d;
+    // g is stored as the deviation from the bulk phase (phi = 0 or 1) that covers most cells
+    double mean = 0.0;
+    for (long long k = 0; k < P.N; ++k) mean += phi0[k];
+    mean /= (double)P.N;
+    if (!is_fin(mean)) return set_error(c, LBM_EINVAL, "phi0 is not finite");
+    P.phi_ref_d = (mean >= 0.5) ? 1.0 : 0.0;
+    P.phi_ref = (float)P.phi_ref_d;
     const size_t nxy = (size_t)P.nxy;
     const int per_z = 1 + (u0 ? 3 : 0);
     const int nzs = slab_depth(c, per_z, 2);
@@ -363,28 +371,31 @@ static int pops_io(lbm_ctx* c, double* f_out, double* g_out, const double* f_in,
     if (rc) return rc;
     Params& P = c->P;
     const size_t nxy = (size_t)P.nxy;
-    const int nzs = slab_depth(c, 1, 0);
-    rc = ensure_staging(c, (size_t)nzs * nxy);
+    const int nzs = slab_depth(c, P.Q, 0);
+    rc = ensure_staging(c, (size_t)P.Q * nzs * nxy);
     if (rc) return rc;
     for (int is_f = 1; is_f >= 0; --is_f) {
         double* host_out = is_f ? f_out : g_out;
         const double* host_in = is_f ? f_in : g_in;
         float* dev = is_f ? c->f[c->cur] : c->g[c->cur];
         if (!host_out && !host_in) continue;
-        for (int q = 0; q < P.Q; ++q)
-            for (int z0 = 0; z0 < P.nz; z0 += nzs) {
-                const int n = (z0 + nzs <= P.nz) ? nzs : P.nz - z0;
-                const size_t off = (size_t)q * P.N + (size_t)z0 * nxy, bytes = (size_t)n * nxy * sizeof(double);
-                if (host_in) {
-                    LBM_CUDA(c, cudaMemcpyAsync(c->staging, host_in + off, bytes, cudaMemcpyHostToDevice, c->stream));
-                    LBM_CUDA(c, lbm::launch_pops_from_f64(P, c->staging, q, is_f, z0, n, dev, c->stream));
-                } else {
-                    LBM_CUDA(c, lbm::launch_pops_to_f64(P, dev, q, is_f, z0, n, c->staging, c->stream));
-                    LBM_CUDA(c, cudaMemcpyAsync(host_out + off, c->staging, bytes, cudaMemcpyDeviceToHost, c->stream));
-                }
-                c->launches += 1;
-                LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+        for (int z0 = 0; z0 < P.nz; z0 += nzs) {
+            const int n = (z0 + nzs <= P.nz) ? nzs : P.nz - z0;
+            const size_t slab = (size_t)n * nxy, bytes = slab * sizeof(double);
+            if (host_in) {
+                for (int q = 0; q < P.Q; ++q)
+                    LBM_CUDA(c, cudaMemcpyAsync(c->staging + q * slab, host_in + (size_t)q * P.N + (size_t)z0 * nxy,
+                                                bytes, cudaMemcpyHostToDevice, c->stream));
+                LBM_CUDA(c, lbm::launch_pops_from_f64(P, c->staging, is_f, z0, n, dev, c->stream));
+            } else {
+                LBM_CUDA(c, lbm::launch_pops_to_f64(P, dev, is_f, z0, n, c->staging, c->stream));
+                for (int q = 0; q < P.Q; ++q)
+                    LBM_CUDA(c, cudaMemcpyAsync(host_out + (size_t)q * P.N + (size_t)z0 * nxy, c->staging + q * slab,
+                                                bytes, cudaMemcpyDeviceToHost, c->stream));
             }
+            c->launches += 1;
+            LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+        }
     }
     return LBM_OK;
 }

@@ -12,7 +12,8 @@ struct Params {
     int nx, ny, nz;
     int nxy;               // nx * ny
     long long N;           // nx * ny * nz
-    float am, a0, ap;      // Lax-Wendroff weights of f*(x - e), f*(x), f*(x + e) (Sec. 2.2)
+    float lw_m, lw_p;      // Lax-Wendroff, difference form (Sec. 2.2):
+                           // fbar(x) = f*(x) + lw_m [f*(x - e) - f*(x)] + lw_p [f*(x + e) - f*(x)]
     float tau_phi;         // phase-field relaxation time
     float omega_g;         // 1 / (tau_phi + 1/2)           (Eq. c-n_c)
     float grad_s;          // tau_phi / (tau_phi + 1/2)      grad phi = grad_s S - grad_k K1
@@ -25,14 +26,18 @@ struct Params {
     float four_over_delta; // 4 / delta
     float G[3];            // body force
     float w0;              // storage shift of f: f_i is held as f_i - t_i w0 (w0 = p0 / cs^2)
+    float phi_ref;         // storage shift of g: g_i is held as g_i - t_i phi_ref (phi_ref = 0 or 1)
     int general;           // 1 if any of drho, G, mu_m1 is non-zero (selects the full collision)
     // FP64 copies for the initialisation and the conversions to and from FP64 host arrays
-    double w0d, tau_phi_d, sigma_d, four_over_delta_d, drho_d, rho2_d;
+    double w0d, phi_ref_d, tau_phi_d, sigma_d, four_over_delta_d, drho_d, rho2_d;
 };
 
 enum Scheme { SCHEME_DF = 0, SCHEME_FD = 1 };
 
-// Launchers (return the launch's cudaError_t). Population buffers are [Q][N] FP32 planes.
+// Launchers (return the launch's cudaError_t). Population buffers are [Q][N] FP32 planes:
+// plane i >= 1 holds f_i - t_i w0 (g_i - t_i phi_ref); plane 0 holds the zeroth moment of the
+// shifted set, sum_i f_i - w0 (sum_i g_i - phi_ref = phi - phi_ref), in place of the rest
+// population, which it determines exactly.
 cudaError_t launch_step(const Params& P, int scheme, const float* f_in, const float* g_in,
                         float* f_out, float* g_out, float* phi_fd, cudaStream_t s, int* launches);
 cudaError_t launch_fd_phi(const Params& P, const float* g_in, float* phi_fd, cudaStream_t s);
@@ -54,10 +59,11 @@ cudaError_t launch_mass(const Params& P, const float* f, const float* g, double*
                         int n_partials, double* result /* 3 doubles */, cudaStream_t s);
 int mass_partials_needed(const Params& P);
 
-// Population plane q, slab [z0, z0 + nzs): FP32 device <-> FP64 staging.
-cudaError_t launch_pops_to_f64(const Params& P, const float* src, int q, int is_f, int z0, int nzs,
-                               double* dst, cudaStream_t s);
-cudaError_t launch_pops_from_f64(const Params& P, const double* src, int q, int is_f, int z0, int nzs,
-                                 float* dst, cudaStream_t s);
+// All Q populations of the slab [z0, z0 + nzs) between the device storage and FP64 staging
+// holding plain populations (Q planes of nzs * nxy values).
+cudaError_t launch_pops_to_f64(const Params& P, const float* src, int is_f, int z0, int nzs, double* dst,
+                               cudaStream_t s);
+cudaError_t launch_pops_from_f64(const Params& P, const double* src, int is_f, int z0, int nzs, float* dst,
+                                 cudaStream_t s);
 
 }  // namespace lbm

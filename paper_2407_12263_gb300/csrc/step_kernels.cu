@@ -42,7 +42,7 @@ step_kernel(const Params P, const float* __restrict__ f_in, const float* __restr
         fd_gradient<Q>(phi_fd, c, nb, gx, gy, gz);
         macro_interface_fd(P, gx, gy, gz, m);
     }
-    macro_pressure<Q, GEN>(P, fb, m);
+    macro_pressure<GEN>(P, m);
     collide<Q, GEN>(P, m, fb, gb);
 
     const size_t N = (size_t)P.N;
@@ -53,7 +53,7 @@ step_kernel(const Params P, const float* __restrict__ f_in, const float* __restr
     }
 }
 
-// Finite-difference variant, pass 1: phi = sum_i LW(g*)_i, one FP32 plane.
+// Finite-difference variant, pass 1: the propagated phi (held as phi - phi_ref), one FP32 plane.
 template <int Q>
 __global__ void __launch_bounds__(kStepThreads)
 fd_phi_kernel(const Params P, const float* __restrict__ g_in, float* __restrict__ phi) {
@@ -65,7 +65,7 @@ fd_phi_kernel(const Params P, const float* __restrict__ g_in, float* __restrict_
     const int c = (z * P.ny + y) * P.nx + x;
     float fb[Q], gb[Q];
     pull<Q, false>(P, nullptr, g_in, c, nb, fb, gb);
-    phi[c] = sum_phi<Q>(gb);
+    phi[c] = gb[0];
 }
 
 static dim3 step_grid(const Params& P) {
