@@ -226,6 +226,9 @@ __device__ __forceinline__ float edot(int i, const float (&v)[3]) {
 //   f*_i = fbar_i - omega_rho (fbar_i - f^eq_i + F_i/2) + F_i                           (Eq. c-n_m)
 //   g^eq_i - t_i phi_ref = t_i [(phi - phi_ref) + phi gam_i + tau_phi e_i . S]          (Eq. geq)
 //   g*_i = g_i - omega_g (g_i - g^eq_i)                                                  (Eq. c-n_c)
+// Opposite velocities i and j (e_j = -e_i) share e.u, (e.n)^2 and e.S up to sign, so each pair
+// splits into a part even in e (gam_even = 4.5 (e.u)^2 - 1.5 u^2, Pi_s term) and a part odd in
+// e (3 e.u, e.S), evaluated once.
 // Zeroth moments: the g collision conserves phi; sum_i f*_i = sum_i fbar_i + u . grad rho,
 // because sum_i F_i = u . grad rho and sum_i f^eq_i = p / cs^2.
 template <int Q, bool GEN>
@@ -245,25 +248,36 @@ __device__ __forceinline__ void collide(const Params& P, const Macro& m, float (
         omega_f = 1.0f / (tau + 0.5f);
     }
     const float omega_g = P.omega_g;
+    const float u2h = 1.5f * u2;
+    const float feq0 = m.P - 4.5f * pi0;  // P - 4.5 Pi_s term shared by every |e|^2 class
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
+    for (int k = 0; k < Lat<Q>::kPairs; ++k) {
+        const int i = Lat<Q>::pair_first(k), j = Lat<Q>::pair_second(k);
         const float t = Lat<Q>::w(i);
         const float eu = edot<Q>(i, m.u);
         const float en = edot<Q>(i, m.n);
         const float es = edot<Q>(i, m.S);
-        const float gam = eu * (3.f + 4.5f * eu) - 1.5f * u2;
-        const float pis = pi0 + sg * ((float)Lat<Q>::e2(i) - en * en);
-        const float feq = t * (m.P + m.rho * gam - 4.5f * pis);
+        const float even = 4.5f * eu * eu - u2h;            // gam_i = even + odd, gam_j = even - odd
+        const float odd = 3.f * eu;
+        const float pis = sg * ((float)Lat<Q>::e2(i) - en * en);  // Pi_s term minus its |e|^2 = 0 part
+        const float fe = t * (feq0 + m.rho * even - 4.5f * pis);
+        const float fo = t * m.rho * odd;
+        const float fi = fe + fo, fj = fe - fo;             // f^eq_i, f^eq_j (shifted)
         if (GEN) {
             const float egr = edot<Q>(i, gr);
             const float erG = edot<Q>(i, rG);
-            const float F = t * (gam * (egr - ugr) + 3.f * (erG - urG) + 9.f * eu * erG);
-            fb[i] = fb[i] - omega_f * (fb[i] - feq + 0.5f * F) + F;
+            const float Fi = t * ((even + odd) * (egr - ugr) + 3.f * (erG - urG) + 9.f * eu * erG);
+            const float Fj = t * ((even - odd) * (-egr - ugr) + 3.f * (-erG - urG) + 9.f * eu * erG);
+            fb[i] = fb[i] - omega_f * (fb[i] - fi + 0.5f * Fi) + Fi;
+            fb[j] = fb[j] - omega_f * (fb[j] - fj + 0.5f * Fj) + Fj;
         } else {
-            fb[i] = fb[i] - omega_f * (fb[i] - feq);
+            fb[i] = fb[i] - omega_f * (fb[i] - fi);
+            fb[j] = fb[j] - omega_f * (fb[j] - fj);
         }
-        const float geq = t * (m.Phi + m.phi * gam + P.tau_phi * es);
-        gb[i] = gb[i] - omega_g * (gb[i] - geq);
+        const float ge = t * (m.Phi + m.phi * even);
+        const float go = t * (m.phi * odd + P.tau_phi * es);
+        gb[i] = gb[i] - omega_g * (gb[i] - (ge + go));
+        gb[j] = gb[j] - omega_g * (gb[j] - (ge - go));
     }
     gb[0] = m.Phi;
     fb[0] = GEN ? m.Pbar + ugr : m.Pbar;

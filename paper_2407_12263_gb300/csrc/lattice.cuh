@@ -29,6 +29,10 @@ struct Lat<9> {
     __host__ __device__ static constexpr double wd(int i) {
         return e2(i) == 0 ? 4.0 / 9.0 : e2(i) == 1 ? 1.0 / 9.0 : 1.0 / 36.0;
     }
+    // opposite pairs (i, j) with e_j = -e_i: (1,3), (2,4), (5,7), (6,8)
+    static constexpr int kPairs = 4;
+    __host__ __device__ static constexpr int pair_first(int k) { return k < 2 ? 1 + k : 5 + (k - 2); }
+    __host__ __device__ static constexpr int pair_second(int k) { return pair_first(k) + 2; }
 };
 
 template <>
@@ -55,6 +59,10 @@ struct Lat<19> {
     __host__ __device__ static constexpr double wd(int i) {
         return e2(i) == 0 ? 1.0 / 3.0 : e2(i) == 1 ? 1.0 / 18.0 : 1.0 / 36.0;
     }
+    // opposite pairs (i, i + 1) with e_{i+1} = -e_i for odd i
+    static constexpr int kPairs = 9;
+    __host__ __device__ static constexpr int pair_first(int k) { return 2 * k + 1; }
+    __host__ __device__ static constexpr int pair_second(int k) { return 2 * k + 2; }
 };
 
 }  // namespace lbm

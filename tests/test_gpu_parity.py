@@ -127,14 +127,16 @@ def test_one_step_populations_match():
 
 
 def test_unit_courant_and_other_relaxation_times():
+    """Other Courant numbers and relaxation times, on a droplet carried by a smooth flow."""
     grid = (24, 20, 16)
     phi0 = I.droplet_phi(grid, 6.0, 4.0)
+    u0 = I.smooth_velocity(grid, seed=51, amplitude=0.02)
     for courant, tau_f, tau_g, M in ((1.0, 0.8, 0.8, 0.02), (0.9, 0.3, 1.5, 0.0), (0.997, 2.0, 0.06, 0.0)):
-        gpu, ref = _pair(19, grid, phi0, courant=courant, tau_f=tau_f, tau_g=tau_g, M=M)
+        gpu, ref = _pair(19, grid, phi0, u0, courant=courant, tau_f=tau_f, tau_g=tau_g, M=M)
         assert gpu.tau_phi == pytest.approx(ref.tau_phi, rel=1e-15)
         gpu.step(100)
         ref.step(100)
-        _compare(gpu, ref, u_abs=1e-9)
+        _compare(gpu, ref)
 
 
 def test_long_horizon_within_fp64_sensitivity():
@@ -185,7 +187,9 @@ def test_minimum_grids(Q, grid):
     gpu, ref = _pair(Q, grid, phi0, u0)
     gpu.step(30)
     ref.step(30)
-    _compare(gpu, ref)
+    # on a 3-cell extent the short-wave flow decays to ~1e-7 within these steps: the velocity
+    # bound is taken relative to the initial amplitude 0.02 there
+    _compare(gpu, ref, u_abs=1e-3 * 0.02 * 1e-3)
 
 
 def test_zero_steps_and_state_errors():
@@ -219,8 +223,12 @@ def test_set_get_roundtrip_and_nonfinite_detection():
     gg = t[:, None, None, None] * rng.uniform(0, 1, (19,) + g.shape)
     g.set_pops(f, gg)
     f1, g1 = g.get_pops()
-    np.testing.assert_allclose(f1, f, rtol=0, atol=1e-8)
-    np.testing.assert_allclose(g1, gg, rtol=0, atol=1e-8)
+    # planes i >= 1 round-trip through FP32 deviations; the rest population is rebuilt from the
+    # FP32 zeroth moment (|sum g - 1| ~ 0.5 here), so it carries up to half an FP32 ulp of that
+    np.testing.assert_allclose(f1[1:], f[1:], rtol=0, atol=1e-8)
+    np.testing.assert_allclose(g1[1:], gg[1:], rtol=0, atol=1e-8)
+    np.testing.assert_allclose(f1[0], f[0], rtol=0, atol=6e-8)
+    np.testing.assert_allclose(g1[0], gg[0], rtol=0, atol=6e-8)
     g.mass()
     f[7, 3, 4, 5] = np.nan            # injected on the host
     g.set_pops(f, gg)
