@@ -138,6 +138,36 @@ double lbm_tau_phi(const lbm_ctx *ctx);
  * may be NULL. Host-only (needs no GPU). LBM_EINVAL for an unknown lattice. */
 int lbm_lattice_tables(int lattice, int *d, int *e, double *w);
 
+/*
+ * Mass diagnostic for callers that cannot allocate device memory. Such callers include a
+ * solver whose populations already fill the GPU, code whose device memory is all owned by a
+ * framework's pool or a fixed arena, and a loop that must not stall on the driver's
+ * allocator. This entry point has no counterpart in the paper; it is a variant of the
+ * reduction behind lbm_mass that needs no handle and calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *   g         device pointer to FP32 plain populations g_i (not the handle's storage):
+ *             Q planes [Q][nz][ny][nx], x fastest, plane 0 the rest population, in the
+ *             velocity order above. Read only.
+ *   lattice   LBM_D2Q9 or LBM_D3Q19; grid[3] as for lbm_create.
+ *   courant   Lax-Wendroff Courant number, 0 < c <= 1. rho_ratio > 0 as for lbm_create.
+ *   result    device pointer to 3 doubles, written with: sum phi and sum rho phi over the
+ *             propagated state (the quantities of lbm_mass), then the count of non-finite
+ *             values among the stored populations.
+ *   stream    cudaStream_t to launch on (NULL = the default stream). Asynchronous: result is
+ *             ready when the stream reaches this point.
+ * Scratch. The per-block partial sums live in a static device array that every GPU loading
+ * the library holds until exit. It has room for 2048 blocks (48 KB), and each z-layer takes
+ * at least one block, so nz must be <= 2048; larger grids, like every other invalid argument,
+ * return LBM_EINVAL without launching. Every call shares that array: the blocks of a call
+ * write their slots before the call's final sum reads them, so nothing needs clearing between
+ * calls, but calls that overlap on the GPU (two streams, two threads) race on it and must be
+ * serialised by the caller.
+ * The first call on each device looks up the array's device address; make that first call
+ * before any stream capture. Returns LBM_ECUDA if the lookup or the launch fails.
+ */
+int lbm_mass_noalloc(const float *g, int lattice, const int grid[3], double courant,
+                     double rho_ratio, double *result, void *stream);
+
 /* Message of the last failure (see the error notes above); never NULL. */
 const char *lbm_last_error(const lbm_ctx *ctx);
 

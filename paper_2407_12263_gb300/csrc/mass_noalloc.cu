@@ -1,0 +1,159 @@
+// mass_noalloc.cu -- lbm_mass_noalloc: the FP64 mass reduction for callers that cannot
+// allocate device memory.
+//
+// Some callers cannot call cudaMalloc. Examples:
+//  * a solver whose populations already fill the GPU, so there is nothing left to allocate;
+//  * code that runs under a memory manager which owns every device allocation (a framework's
+//    caching pool, a fixed arena sized at start-up);
+//  * a loop that must not stall on the driver's allocator between steps.
+// The handle-based lbm_mass needs scratch for its per-block partial sums and gets it from
+// cudaMalloc in lbm_create. This entry point instead keeps that scratch in a file-scope
+// __device__ array with a fixed maximum size. Every GPU that loads the library holds the array
+// until the process exits. The caller owns the input populations and the output.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cmath>
+#include <mutex>
+
+#include "../../include/lbm.h"
+#include "cell.cuh"
+
+namespace lbm {
+namespace {
+
+constexpr int kNoallocThreads = 256;
+constexpr int kNoallocMaxBlocks = 2048;  // partial triples the static scratch holds
+
+// One FP64 triple (sum phi, sum rho phi, non-finite count) per block of the last call.
+static __device__ __align__(256) double g_noalloc_partials[3 * kNoallocMaxBlocks];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+double* g_scratch_ptr[kMaxDevices] = {};
+
+// Address of the scratch array on the current device, resolved once per device.
+cudaError_t scratch_on_current_device(double** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        if (e != cudaSuccess) return e;
+        g_scratch_ptr[dev] = static_cast<double*>(p);
+    }
+    *out = g_scratch_ptr[dev];
+    return cudaSuccess;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void block_sum3_d(double (&v)[3], double* out) {
+    __shared__ double red[3][kNoallocThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        v[k] = warp_sum_d(v[k]);
+        if (lane == 0) red[k][warp] = v[k];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double w = (lane < kNoallocThreads / 32) ? red[k][lane] : 0.0;
+            w = warp_sum_d(w);
+            if (lane == 0) out[k] = w;
+        }
+    }
+}
+
+// Block b covers z-layer b / bpl, rows [r0, r1) of it; it writes its triple to partials[b].
+// phi = sum_i of the Lax-Wendroff-propagated g_i (plane 0, the rest population, does not move).
+template <int Q>
+__global__ void __launch_bounds__(kNoallocThreads)
+mass_noalloc_kernel(const Params P, const float* __restrict__ g, int blocks_per_layer, double* __restrict__ partials) {
+    const int z = blockIdx.x / blocks_per_layer, part = blockIdx.x % blocks_per_layer;
+    const int rows_per = (P.ny + blocks_per_layer - 1) / blocks_per_layer;
+    const int r0 = part * rows_per, r1 = min(P.ny, r0 + rows_per);
+    const size_t N = (size_t)P.N;
+    double acc[3] = {0.0, 0.0, 0.0};
+    const int n = (r1 > r0) ? (r1 - r0) * P.nx : 0;
+    for (int k = threadIdx.x; k < n; k += kNoallocThreads) {
+        const int y = r0 + k / P.nx, x = k % P.nx;
+        const int c = (z * P.ny + y) * P.nx + x;
+        const Nbr nb = make_nbr(P, x, y, z);
+        float phi = __ldg(g + c);
+        int bad = !isfinite(phi);
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const float* gq = g + i * N;
+            const float g0 = __ldg(gq + c);
+            const float gm = __ldg(gq + c + link_offset<Q>(nb, i, -1));
+            const float gp = __ldg(gq + c + link_offset<Q>(nb, i, +1));
+            phi += g0 + (P.lw_m * (gm - g0) + P.lw_p * (gp - g0));
+            bad += !isfinite(g0);
+        }
+        const double pd = (double)phi;
+        acc[0] += pd;
+        acc[1] += (P.rho2_d + P.drho_d * pd) * pd;
+        acc[2] += (double)bad;
+    }
+    block_sum3_d(acc, partials + 3 * blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kNoallocThreads)
+mass_noalloc_finish(const double* __restrict__ partials, int n, double* __restrict__ result) {
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < n; b += kNoallocThreads)
+        for (int k = 0; k < 3; ++k) acc[k] += partials[3 * b + k];
+    block_sum3_d(acc, result);
+}
+
+}  // namespace
+}  // namespace lbm
+
+extern "C" int lbm_mass_noalloc(const float* g, int lattice, const int grid[3], double courant, double rho_ratio,
+                                double* result, void* stream) {
+    if (!g || !grid || !result) return LBM_EINVAL;
+    if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19) return LBM_EINVAL;
+    const int nx = grid[0], ny = grid[1], nz = grid[2];
+    if (nx < 3 || ny < 3 || (lattice == LBM_D2Q9 && nz != 1) || (lattice == LBM_D3Q19 && nz < 3)) return LBM_EINVAL;
+    if ((long long)nx * ny * nz >= (long long)INT_MAX) return LBM_EINVAL;
+    // The static scratch holds kNoallocMaxBlocks partial triples and each z-layer takes at least
+    // one block, so grids deeper than that are rejected.
+    if (nz > lbm::kNoallocMaxBlocks) return LBM_EINVAL;
+    if (!(courant > 0 && courant <= 1) || !(rho_ratio > 0) || !std::isfinite(rho_ratio)) return LBM_EINVAL;
+
+    double* partials = nullptr;
+    if (lbm::scratch_on_current_device(&partials) != cudaSuccess) return LBM_ECUDA;
+
+    lbm::Params P = {};
+    P.Q = lattice;
+    P.nx = nx;
+    P.ny = ny;
+    P.nz = nz;
+    P.nxy = nx * ny;
+    P.N = (long long)nx * ny * nz;
+    P.lw_m = (float)(0.5 * courant * (1.0 + courant));
+    P.lw_p = (float)(-0.5 * courant * (1.0 - courant));
+    P.rho2_d = 1.0;
+    P.drho_d = rho_ratio - 1.0;
+    int bpl = lbm::kNoallocMaxBlocks / nz;
+    if (bpl > ny) bpl = ny;
+    if (bpl < 1) bpl = 1;
+    const int blocks = nz * bpl;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (lattice == LBM_D2Q9)
+        lbm::mass_noalloc_kernel<9><<<blocks, lbm::kNoallocThreads, 0, s>>>(P, g, bpl, partials);
+    else
+        lbm::mass_noalloc_kernel<19><<<blocks, lbm::kNoallocThreads, 0, s>>>(P, g, bpl, partials);
+    lbm::mass_noalloc_finish<<<1, lbm::kNoallocThreads, 0, s>>>(partials, blocks, result);
+    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
+}
