@@ -18,8 +18,7 @@ constexpr int kAuxBX = 32, kAuxBY = 4;
 // ---------------------------------------------------------------------------------------
 template <int Q>
 __global__ void init_kernel(const Params P, int z0, const double* __restrict__ phi0s,
-                            const double* __restrict__ u0s, double p0, float* __restrict__ f,
-                            float* __restrict__ g) {
+                            const double* __restrict__ u0s, double p0, float2* __restrict__ fg) {
     const int x = blockIdx.x * kAuxBX + threadIdx.x;
     const int y = blockIdx.y * kAuxBY + threadIdx.y;
     const int zl = blockIdx.z;
@@ -72,20 +71,16 @@ __global__ void init_kernel(const Params P, int z0, const double* __restrict__ p
         const double gstar = t * (phi * (1.0 + gam) + P.tau_phi_d * es) - t * (P.tau_phi_d - 0.5) * eg;
         fsum += fstar;
         gsum += gstar;
-        if (i > 0) {
-            f[i * N + c] = (float)(fstar - t * P.w0d);
-            g[i * N + c] = (float)(gstar - t * P.phi_ref_d);
-        }
+        if (i > 0) fg[i * N + c] = make_float2((float)(fstar - t * P.w0d), (float)(gstar - t * P.phi_ref_d));
     }
-    f[c] = (float)(fsum - P.w0d);      // plane 0: zeroth moments of the shifted sets
-    g[c] = (float)(gsum - P.phi_ref_d);
+    fg[c] = make_float2((float)(fsum - P.w0d), (float)(gsum - P.phi_ref_d));  // plane 0: zeroth moments
 }
 
 cudaError_t launch_init(const Params& P, int z0, int nzs, const double* phi0s, const double* u0s,
-                        double p0, float* f, float* g, cudaStream_t s) {
+                        double p0, float2* fg, cudaStream_t s) {
     const dim3 grid((P.nx + kAuxBX - 1) / kAuxBX, (P.ny + kAuxBY - 1) / kAuxBY, nzs), block(kAuxBX, kAuxBY);
-    if (P.Q == 9) init_kernel<9><<<grid, block, 0, s>>>(P, z0, phi0s, u0s, p0, f, g);
-    else init_kernel<19><<<grid, block, 0, s>>>(P, z0, phi0s, u0s, p0, f, g);
+    if (P.Q == 9) init_kernel<9><<<grid, block, 0, s>>>(P, z0, phi0s, u0s, p0, fg);
+    else init_kernel<19><<<grid, block, 0, s>>>(P, z0, phi0s, u0s, p0, fg);
     return cudaGetLastError();
 }
 
@@ -94,9 +89,8 @@ cudaError_t launch_init(const Params& P, int z0, int nzs, const double* phi0s, c
 // Output slab layout: 11 FP64 planes of nzs * nxy values: phi, p, u(3), grad phi(3), n(3).
 // ---------------------------------------------------------------------------------------
 template <int Q, int SCHEME, bool GEN>
-__global__ void moments_kernel(const Params P, int z0, const float* __restrict__ f,
-                               const float* __restrict__ g, const float* __restrict__ phi_fd, int mask,
-                               double* __restrict__ out) {
+__global__ void moments_kernel(const Params P, int z0, const float2* __restrict__ fg,
+                               const float* __restrict__ phi_fd, int mask, double* __restrict__ out) {
     const int x = blockIdx.x * kAuxBX + threadIdx.x;
     const int y = blockIdx.y * kAuxBY + threadIdx.y;
     const int zl = blockIdx.z;
@@ -105,7 +99,7 @@ __global__ void moments_kernel(const Params P, int z0, const float* __restrict__
     const Nbr nb = make_nbr(P, x, y, z);
     const int c = (z * P.ny + y) * P.nx + x;
     float fb[Q], gb[Q];
-    pull<Q, true>(P, f, g, c, nb, fb, gb);
+    pull<Q, true>(P, fg, c, nb, fb, gb);
     Macro m;
     macro_flow<Q, GEN>(P, fb, gb, m);
     if (SCHEME == SCHEME_DF) {
@@ -128,21 +122,21 @@ __global__ void moments_kernel(const Params P, int z0, const float* __restrict__
 }
 
 template <int Q, int SCHEME>
-static void moments_q(const Params& P, int z0, int nzs, const float* f, const float* g, const float* phi,
-                      int mask, double* out, cudaStream_t s) {
+static void moments_q(const Params& P, int z0, int nzs, const float2* fg, const float* phi, int mask, double* out,
+                      cudaStream_t s) {
     const dim3 grid((P.nx + kAuxBX - 1) / kAuxBX, (P.ny + kAuxBY - 1) / kAuxBY, nzs), block(kAuxBX, kAuxBY);
-    if (P.general) moments_kernel<Q, SCHEME, true><<<grid, block, 0, s>>>(P, z0, f, g, phi, mask, out);
-    else moments_kernel<Q, SCHEME, false><<<grid, block, 0, s>>>(P, z0, f, g, phi, mask, out);
+    if (P.general) moments_kernel<Q, SCHEME, true><<<grid, block, 0, s>>>(P, z0, fg, phi, mask, out);
+    else moments_kernel<Q, SCHEME, false><<<grid, block, 0, s>>>(P, z0, fg, phi, mask, out);
 }
 
-cudaError_t launch_moments(const Params& P, int scheme, int z0, int nzs, const float* f, const float* g,
-                           const float* phi_fd, int mask, double* out, cudaStream_t s) {
+cudaError_t launch_moments(const Params& P, int scheme, int z0, int nzs, const float2* fg, const float* phi_fd,
+                           int mask, double* out, cudaStream_t s) {
     if (P.Q == 9) {
-        if (scheme == SCHEME_DF) moments_q<9, SCHEME_DF>(P, z0, nzs, f, g, phi_fd, mask, out, s);
-        else moments_q<9, SCHEME_FD>(P, z0, nzs, f, g, phi_fd, mask, out, s);
+        if (scheme == SCHEME_DF) moments_q<9, SCHEME_DF>(P, z0, nzs, fg, phi_fd, mask, out, s);
+        else moments_q<9, SCHEME_FD>(P, z0, nzs, fg, phi_fd, mask, out, s);
     } else {
-        if (scheme == SCHEME_DF) moments_q<19, SCHEME_DF>(P, z0, nzs, f, g, phi_fd, mask, out, s);
-        else moments_q<19, SCHEME_FD>(P, z0, nzs, f, g, phi_fd, mask, out, s);
+        if (scheme == SCHEME_DF) moments_q<19, SCHEME_DF>(P, z0, nzs, fg, phi_fd, mask, out, s);
+        else moments_q<19, SCHEME_FD>(P, z0, nzs, fg, phi_fd, mask, out, s);
     }
     return cudaGetLastError();
 }
@@ -182,7 +176,7 @@ __device__ __forceinline__ void block_sum3(double (&v)[3], double* out) {
 
 template <int Q>
 __global__ void __launch_bounds__(kRedThreads)
-mass_kernel(const Params P, const float* __restrict__ f, const float* __restrict__ g, double* __restrict__ partials) {
+mass_kernel(const Params P, const float2* __restrict__ fg, double* __restrict__ partials) {
     double acc[3] = {0.0, 0.0, 0.0};
     const size_t N = (size_t)P.N;
     for (long long c = (long long)blockIdx.x * kRedThreads + threadIdx.x; c < P.N;
@@ -192,13 +186,16 @@ mass_kernel(const Params P, const float* __restrict__ f, const float* __restrict
         const int y = r / P.nx, x = r - y * P.nx;
         const Nbr nb = make_nbr(P, x, y, z);
         float fb[Q], gb[Q];
-        pull<Q, false>(P, nullptr, g, (int)c, nb, fb, gb);
+        pull<Q, false>(P, fg, (int)c, nb, fb, gb);
         const double phi = P.phi_ref_d + (double)gb[0];
         acc[0] += phi;
         acc[1] += (P.rho2_d + P.drho_d * phi) * phi;
         int bad = 0;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) bad += !isfinite(__ldg(f + i * N + c)) + !isfinite(__ldg(g + i * N + c));
+        for (int i = 0; i < Q; ++i) {
+            const float2 v = __ldg(fg + i * N + c);
+            bad += !isfinite(v.x) + !isfinite(v.y);
+        }
         acc[2] += (double)bad;
     }
     block_sum3(acc, partials + 3 * blockIdx.x);
@@ -217,10 +214,10 @@ int mass_partials_needed(const Params& P) {
     return (int)(blocks < 1024 ? blocks : 1024);
 }
 
-cudaError_t launch_mass(const Params& P, const float* f, const float* g, double* partials, int n_partials,
-                        double* result, cudaStream_t s) {
-    if (P.Q == 9) mass_kernel<9><<<n_partials, kRedThreads, 0, s>>>(P, f, g, partials);
-    else mass_kernel<19><<<n_partials, kRedThreads, 0, s>>>(P, f, g, partials);
+cudaError_t launch_mass(const Params& P, const float2* fg, double* partials, int n_partials, double* result,
+                        cudaStream_t s) {
+    if (P.Q == 9) mass_kernel<9><<<n_partials, kRedThreads, 0, s>>>(P, fg, partials);
+    else mass_kernel<19><<<n_partials, kRedThreads, 0, s>>>(P, fg, partials);
     mass_finish<<<1, kRedThreads, 0, s>>>(partials, n_partials, result);
     return cudaGetLastError();
 }
@@ -230,15 +227,17 @@ cudaError_t launch_mass(const Params& P, const float* f, const float* g, double*
 // Plane i >= 1: v_i + t_i ref; plane 0: the rest population (ref + v_0) - sum_{i>=1} f_i.
 // ---------------------------------------------------------------------------------------
 template <int Q>
-__global__ void pops_to_f64(const Params P, const float* __restrict__ src, int is_f, int z0, int nzs,
+__global__ void pops_to_f64(const Params P, const float2* __restrict__ src, int is_f, int z0, int nzs,
                             double* __restrict__ dst) {
     const size_t n = (size_t)nzs * P.nxy, base = (size_t)z0 * P.nxy, N = (size_t)P.N;
     const double ref = is_f ? P.w0d : P.phi_ref_d;
     for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (size_t)gridDim.x * blockDim.x) {
-        double rest = ref + (double)src[base + l];
+        const float2 m0 = src[base + l];
+        double rest = ref + (double)(is_f ? m0.x : m0.y);
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
-            const double v = (double)src[i * N + base + l] + Lat<Q>::wd(i) * ref;
+            const float2 p = src[i * N + base + l];
+            const double v = (double)(is_f ? p.x : p.y) + Lat<Q>::wd(i) * ref;
             dst[i * n + l] = v;
             rest -= v;
         }
@@ -248,7 +247,7 @@ __global__ void pops_to_f64(const Params P, const float* __restrict__ src, int i
 
 template <int Q>
 __global__ void pops_from_f64(const Params P, const double* __restrict__ src, int is_f, int z0, int nzs,
-                              float* __restrict__ dst) {
+                              float2* __restrict__ dst) {
     const size_t n = (size_t)nzs * P.nxy, base = (size_t)z0 * P.nxy, N = (size_t)P.N;
     const double ref = is_f ? P.w0d : P.phi_ref_d;
     for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (size_t)gridDim.x * blockDim.x) {
@@ -257,9 +256,11 @@ __global__ void pops_from_f64(const Params P, const double* __restrict__ src, in
         for (int i = 1; i < Q; ++i) {
             const double v = src[i * n + l];
             sum += v;
-            dst[i * N + base + l] = (float)(v - Lat<Q>::wd(i) * ref);
+            float* slot = is_f ? &dst[i * N + base + l].x : &dst[i * N + base + l].y;
+            *slot = (float)(v - Lat<Q>::wd(i) * ref);
         }
-        dst[base + l] = (float)(sum - ref);
+        float* slot0 = is_f ? &dst[base + l].x : &dst[base + l].y;
+        *slot0 = (float)(sum - ref);
     }
 }
 
@@ -269,14 +270,14 @@ static unsigned conv_blocks(const Params& P, int nzs) {
     return (unsigned)(b < 4096 ? b : 4096);
 }
 
-cudaError_t launch_pops_to_f64(const Params& P, const float* src, int is_f, int z0, int nzs, double* dst,
+cudaError_t launch_pops_to_f64(const Params& P, const float2* src, int is_f, int z0, int nzs, double* dst,
                                cudaStream_t s) {
     if (P.Q == 9) pops_to_f64<9><<<conv_blocks(P, nzs), 256, 0, s>>>(P, src, is_f, z0, nzs, dst);
     else pops_to_f64<19><<<conv_blocks(P, nzs), 256, 0, s>>>(P, src, is_f, z0, nzs, dst);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pops_from_f64(const Params& P, const double* src, int is_f, int z0, int nzs, float* dst,
+cudaError_t launch_pops_from_f64(const Params& P, const double* src, int is_f, int z0, int nzs, float2* dst,
                                  cudaStream_t s) {
     if (P.Q == 9) pops_from_f64<9><<<conv_blocks(P, nzs), 256, 0, s>>>(P, src, is_f, z0, nzs, dst);
     else pops_from_f64<19><<<conv_blocks(P, nzs), 256, 0, s>>>(P, src, is_f, z0, nzs, dst);

@@ -1,7 +1,7 @@
 // cell.cuh -- per-cell device code of the difference-free conservative phase-field LBM
 // (Zhao, Patel & Lee, arXiv:2407.12263): Lax-Wendroff pull, macroscopic stage, collisions.
 //
-// Storage (FP32 planes [Q][N]). Plane i >= 1 holds the population shifted by its lattice
+// Storage (Q planes of N FP32 pairs (f, g)). Plane i >= 1 holds the populations shifted by their lattice
 // weight times a reference level, f_i - t_i w0 (w0 = p0 / cs^2) and g_i - t_i phi_ref
 // (phi_ref = 0 or 1, the bulk phase that fills most of the grid). Plane 0 holds the zeroth
 // moment of the shifted set, sum_i f_i - w0 and phi - phi_ref, in place of the rest
@@ -52,32 +52,31 @@ __device__ __forceinline__ int link_offset(const Nbr& n, int i, int s) {
 // Lax-Wendroff propagation (Sec. 2.2) into registers:
 //   fbar_i(x) = f*_i(x) - c [f*_i(x) - f*_i(x - e_i)] - c(1-c)/2 [f*_i(x + e_i) - 2 f*_i(x) + f*_i(x - e_i)]
 //             = f*_i(x) + lw_m [f*_i(x - e_i) - f*_i(x)] + lw_p [f*_i(x + e_i) - f*_i(x)],
-// and the zeroth moments fb[0] = sum fbar - w0, gb[0] = phi - phi_ref of the propagated state.
+// the same for g, and the zeroth moments fb[0] = sum fbar - w0, gb[0] = phi - phi_ref of the
+// propagated state. Each load brings the (f_i, g_i) pair of one cell.
 template <int Q, bool WITH_F>
-__device__ __forceinline__ void pull(const Params& P, const float* __restrict__ f,
-                                     const float* __restrict__ g, int c, const Nbr& nb,
+__device__ __forceinline__ void pull(const Params& P, const float2* __restrict__ fg, int c, const Nbr& nb,
                                      float (&fb)[Q], float (&gb)[Q]) {
     const size_t N = (size_t)P.N;
     float df = 0.f, dg = 0.f;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-        const int cm = c + link_offset<Q>(nb, i, -1);
-        const int cp = c + link_offset<Q>(nb, i, +1);
-        const float* gq = g + i * N;
-        const float g0 = __ldg(gq + c);
-        const float d = P.lw_m * (__ldg(gq + cm) - g0) + P.lw_p * (__ldg(gq + cp) - g0);
-        gb[i] = g0 + d;
+        const float2* q = fg + i * N;
+        const float2 v0 = __ldg(q + c);
+        const float2 vm = __ldg(q + c + link_offset<Q>(nb, i, -1));
+        const float2 vp = __ldg(q + c + link_offset<Q>(nb, i, +1));
+        const float d = P.lw_m * (vm.y - v0.y) + P.lw_p * (vp.y - v0.y);
+        gb[i] = v0.y + d;
         dg += d;
         if (WITH_F) {
-            const float* fq = f + i * N;
-            const float f0 = __ldg(fq + c);
-            const float e = P.lw_m * (__ldg(fq + cm) - f0) + P.lw_p * (__ldg(fq + cp) - f0);
-            fb[i] = f0 + e;
+            const float e = P.lw_m * (vm.x - v0.x) + P.lw_p * (vp.x - v0.x);
+            fb[i] = v0.x + e;
             df += e;
         }
     }
-    gb[0] = __ldg(g + c) + dg;
-    if (WITH_F) fb[0] = __ldg(f + c) + df;
+    const float2 m0 = __ldg(fg + c);
+    gb[0] = m0.y + dg;
+    if (WITH_F) fb[0] = m0.x + df;
 }
 
 struct Macro {

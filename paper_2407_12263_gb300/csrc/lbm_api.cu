@@ -23,9 +23,8 @@ struct lbm_ctx {
     int device;
     cudaStream_t stream;
     bool own_stream;
-    float* f[2];
-    float* g[2];
-    int cur;               // index of the buffer pair holding the current state
+    float2* fg[2];         // ping-pong state: Q planes of N (f, g) pairs each
+    int cur;               // index of the buffer holding the current state
     float* phi_fd;         // propagated phi plane of the finite-difference variant
     double* partials;      // per-block FP64 partial sums of the mass reduction
     int n_partials;
@@ -66,10 +65,7 @@ void free_ctx(lbm_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    for (int k = 0; k < 2; ++k) {
-        cudaFree(c->f[k]);
-        cudaFree(c->g[k]);
-    }
+    for (int k = 0; k < 2; ++k) cudaFree(c->fg[k]);
     cudaFree(c->phi_fd);
     cudaFree(c->partials);
     cudaFree(c->result);
@@ -217,14 +213,12 @@ int lbm_create(lbm_ctx** out, const int grid[3], int lattice, double tau_f, doub
         }
         c->own_stream = true;
     }
-    const size_t pop_bytes = (size_t)lattice * (size_t)N * sizeof(float);
+    const size_t pop_bytes = (size_t)lattice * (size_t)N * sizeof(float2);
     for (int k = 0; k < 2 && rc == LBM_OK; ++k) {
-        cudaError_t e1 = cudaMalloc(&c->f[k], pop_bytes);
-        cudaError_t e2 = (e1 == cudaSuccess) ? cudaMalloc(&c->g[k], pop_bytes) : e1;
-        if (e2 != cudaSuccess)
-            rc = set_error(c, e2 == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA,
-                           "allocating %zu bytes of populations failed: %s", 4 * pop_bytes,
-                           cudaGetErrorString(e2));
+        cudaError_t e = cudaMalloc(&c->fg[k], pop_bytes);
+        if (e != cudaSuccess)
+            rc = set_error(c, e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA,
+                           "allocating %zu bytes of populations failed: %s", 2 * pop_bytes, cudaGetErrorString(e));
     }
     if (rc == LBM_OK && c->scheme == LBM_SCHEME_FINITE_DIFFERENCE) {
         cudaError_t e = cudaMalloc(&c->phi_fd, (size_t)N * sizeof(float));
@@ -276,7 +270,7 @@ int lbm_init_phi(lbm_ctx* c, const double* phi0, const double* u0, double p0) {
             for (int a = 0; a < 3; ++a)
                 LBM_CUDA(c, cudaMemcpyAsync(us + (size_t)a * n * nxy, u0 + (size_t)a * P.N + (size_t)z0 * nxy,
                                             (size_t)n * nxy * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-        LBM_CUDA(c, lbm::launch_init(P, z0, n, phis, u0 ? us : nullptr, p0, c->f[c->cur], c->g[c->cur], c->stream));
+        LBM_CUDA(c, lbm::launch_init(P, z0, n, phis, u0 ? us : nullptr, p0, c->fg[c->cur], c->stream));
         c->launches += 1;
     }
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -292,8 +286,7 @@ int lbm_step(lbm_ctx* c, int n) {
     for (int k = 0; k < n; ++k) {
         const int a = c->cur, b = 1 - c->cur;
         int launches = 0;
-        LBM_CUDA(c, lbm::launch_step(c->P, c->scheme, c->f[a], c->g[a], c->f[b], c->g[b], c->phi_fd, c->stream,
-                                     &launches));
+        LBM_CUDA(c, lbm::launch_step(c->P, c->scheme, c->fg[a], c->fg[b], c->phi_fd, c->stream, &launches));
         c->launches += launches;
         c->cur = b;
     }
@@ -309,15 +302,14 @@ static int fields_out(lbm_ctx* c, int mask, double* const* dst /* 11 planes, NUL
     const int nzs = slab_depth(c, 11, 0);
     rc = ensure_staging(c, (size_t)11 * nzs * nxy);
     if (rc) return rc;
-    const float* f = c->f[c->cur];
-    const float* g = c->g[c->cur];
+    const float2* fg = c->fg[c->cur];
     if (c->scheme == LBM_SCHEME_FINITE_DIFFERENCE) {
-        LBM_CUDA(c, lbm::launch_fd_phi(P, g, c->phi_fd, c->stream));
+        LBM_CUDA(c, lbm::launch_fd_phi(P, fg, c->phi_fd, c->stream));
         c->launches += 1;
     }
     for (int z0 = 0; z0 < P.nz; z0 += nzs) {
         const int n = (z0 + nzs <= P.nz) ? nzs : P.nz - z0;
-        LBM_CUDA(c, lbm::launch_moments(P, c->scheme, z0, n, f, g, c->phi_fd, mask, c->staging, c->stream));
+        LBM_CUDA(c, lbm::launch_moments(P, c->scheme, z0, n, fg, c->phi_fd, mask, c->staging, c->stream));
         c->launches += 1;
         const size_t slab = (size_t)n * nxy;
         for (int j = 0; j < 11; ++j) {
@@ -355,7 +347,7 @@ int lbm_mass(lbm_ctx* c, double* sum_phi, double* sum_rho_phi) {
     int rc = check_ctx(c);
     if (rc) return rc;
     if (!c->initialised) return set_error(c, LBM_ESTATE, "no state: call lbm_init_phi first");
-    LBM_CUDA(c, lbm::launch_mass(c->P, c->f[c->cur], c->g[c->cur], c->partials, c->n_partials, c->result, c->stream));
+    LBM_CUDA(c, lbm::launch_mass(c->P, c->fg[c->cur], c->partials, c->n_partials, c->result, c->stream));
     c->launches += 2;
     double r[3];
     LBM_CUDA(c, cudaMemcpyAsync(r, c->result, sizeof r, cudaMemcpyDeviceToHost, c->stream));
@@ -377,7 +369,7 @@ static int pops_io(lbm_ctx* c, double* f_out, double* g_out, const double* f_in,
     for (int is_f = 1; is_f >= 0; --is_f) {
         double* host_out = is_f ? f_out : g_out;
         const double* host_in = is_f ? f_in : g_in;
-        float* dev = is_f ? c->f[c->cur] : c->g[c->cur];
+        float2* dev = c->fg[c->cur];
         if (!host_out && !host_in) continue;
         for (int z0 = 0; z0 < P.nz; z0 += nzs) {
             const int n = (z0 + nzs <= P.nz) ? nzs : P.nz - z0;

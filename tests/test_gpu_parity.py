@@ -91,10 +91,11 @@ def test_static_droplet_parity(Q, grid, R, scheme):
 
 
 @pytest.mark.parametrize("scheme", [0, 1])
-@pytest.mark.parametrize("Q,grid", [(9, (45, 39, 1)), (19, (37, 21, 19))])
+@pytest.mark.parametrize("Q,grid", [(9, (45, 39, 1)), (19, (37, 21, 19)), (19, (131, 6, 5))])
 def test_ragged_grid_all_terms_parity(Q, grid, scheme):
-    """Ragged extents (not multiples of the 32 x 4 thread block), density and viscosity ratio,
-    body force and a non-zero initial velocity: every term of the collision is exercised."""
+    """Ragged extents (not multiples of the 32 x 4 or 128 x 1 thread blocks), density and
+    viscosity ratio, body force and a non-zero initial velocity: every term of the collision is
+    exercised."""
     phi0 = I.multi_droplet_phi(grid, seed=21, count=3, r_range=(3.0, 7.0), xi=4.0)
     u0 = I.smooth_velocity(grid, seed=22, amplitude=0.03)
     gen = dict(GENERAL)
