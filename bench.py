@@ -42,7 +42,11 @@ from paper_2407_12263_gb300 import inputs as I  # noqa: E402
 
 METRIC = "MLUPS and % of HBM roofline, 1 GB300, vs same-GPU FD variant & FP32 at stated error"
 WORKLOAD = "droplet3d_128"
-BYTES_PER_CELL = {"df": 2 * 2 * 19 * 4, "fd": 2 * 2 * 19 * 4 + 19 * 4 + 4 + 4}
+# bytes per cell and step: the difference-free step reads and writes 19 (f, g) pairs; the
+# finite-difference step adds a phi pass that reads the 19 pairs (f and g are interleaved, so g
+# alone cannot be read for less) and writes phi, and reads phi in the step
+BYTES_PER_CELL = {"df": 2 * 2 * 19 * 4, "fd": 2 * 2 * 19 * 4 + 2 * 19 * 4 + 4 + 4}
+FD_METHOD_BYTES = 2 * 2 * 19 * 4 + 19 * 4 + 4 + 4  # the FD method's minimum with g readable alone
 PROFILE = ROOT / "profiles" / "step_kernel_droplet3d_128.md"
 KERNEL_SOURCES = ["paper_2407_12263_gb300/csrc/cell.cuh", "paper_2407_12263_gb300/csrc/lattice.cuh",
                   "paper_2407_12263_gb300/csrc/step_kernels.cu", "paper_2407_12263_gb300/csrc/lbm_internal.h"]
@@ -217,6 +221,7 @@ def run_ours(args):
            "clocks": clk,
            "fd": {"value": round(fd_value, 1), "unit": "MLUPS", "ms_per_step": round(t_fd / args.steps * 1e3, 5),
                   "gpu_launches": fd_launches, "bytes_per_cell": BYTES_PER_CELL["fd"],
+                  "method_bytes_per_cell": FD_METHOD_BYTES,
                   "hbm_frac": round(BYTES_PER_CELL["fd"] * cells / (t_fd / args.steps) / 1e9 / peak, 4)},
            "df_vs_fd": round(value / fd_value, 4),
            "sum_phi_drift": {"df": drift, "fd": fd_drift, "steps": args.warmup + args.steps}}
