@@ -4,9 +4,10 @@
  *
  * One handle owns one periodic lattice (D2Q9 or D3Q19) and its device state: the
  * post-collision populations f* (one-fluid pressure PDF, Sec. 2.2) and g* (conservative
- * phase-field PDF, Sec. 2.3), FP32, structure-of-arrays planes [Q][nz][ny][nx] with x
- * fastest, in two ping-pong copies. Every step is one fused stream-collide kernel launch
- * (difference-free scheme), or two launches for the finite-difference variant.
+ * phase-field PDF, Sec. 2.3), held as (f_i, g_i) pairs in planes [Q][nz][ny][nx] with x
+ * fastest, in two ping-pong copies; the moving pairs are FP32, FP16 or BF16 (lbm_storage), all
+ * arithmetic is FP32. Every step is one fused stream-collide kernel launch (difference-free
+ * scheme), or two launches for the finite-difference variant.
  *
  * Units are lattice units: dx = 1 and dt = 1 in every collision, moment and forcing
  * formula; the Courant number only enters the Lax-Wendroff propagation (Sec. 2.2).
@@ -52,6 +53,13 @@ enum lbm_status {
     LBM_ESTATE = -6      /* the call needs lbm_init_phi (or lbm_set_pops) first */
 };
 
+enum lbm_storage {
+    LBM_STORAGE_FP32 = 0, /* (f_i, g_i) pairs as 2 x FP32: 304 B per D3Q19 cell and step */
+    LBM_STORAGE_FP16 = 1, /* moving pairs as 2 x FP16 (deviations scaled by 2^12 and 2^10), the
+                             zeroth-moment plane in FP32: 160 B per D3Q19 cell and step */
+    LBM_STORAGE_BF16 = 2  /* moving pairs as 2 x BF16, zeroth-moment plane in FP32: 160 B */
+};
+
 enum lbm_scheme {
     LBM_SCHEME_DIFFERENCE_FREE = 0, /* grad phi and n from the central moment K1 (Sec. 2.3) */
     LBM_SCHEME_FINITE_DIFFERENCE = 1 /* isotropic central difference of phi (Sec. 3.4) */
@@ -59,7 +67,7 @@ enum lbm_scheme {
 
 typedef struct {
     int scheme;     /* enum lbm_scheme; default difference-free */
-    int storage;    /* 0 = FP32 populations (the only storage built) */
+    int storage;    /* enum lbm_storage; default FP32. Arithmetic is FP32 in every case */
     double courant; /* Lax-Wendroff Courant number c, 0 < c <= 1; default 0.997 (Sec. 2.2) */
     int walls;      /* 0 = fully periodic (the only boundary built) */
     void *stream;   /* cudaStream_t the handle launches on; NULL = a stream the handle owns */

@@ -16,9 +16,9 @@ constexpr int kAuxBX = 32, kAuxBY = 4;
 // The g term is the first-order non-equilibrium part a relaxed state carries after collision,
 // so the first K1 already points along -grad phi for any tau_phi.
 // ---------------------------------------------------------------------------------------
-template <int Q>
+template <int Q, int S>
 __global__ void init_kernel(const Params P, int z0, const double* __restrict__ phi0s,
-                            const double* __restrict__ u0s, double p0, float2* __restrict__ fg) {
+                            const double* __restrict__ u0s, double p0, void* __restrict__ fg) {
     const int x = blockIdx.x * kAuxBX + threadIdx.x;
     const int y = blockIdx.y * kAuxBY + threadIdx.y;
     const int zl = blockIdx.z;
@@ -46,7 +46,7 @@ __global__ void init_kernel(const Params P, int z0, const double* __restrict__ p
     const double inv = (g2 > 1e-24) ? 1.0 / gn : 0.0;
     const double n[3] = {gx * inv, gy * inv, gz * inv};
     const double smag = P.four_over_delta_d * phi * (1.0 - phi);
-    const double S[3] = {smag * n[0], smag * n[1], smag * n[2]};
+    const double Sv[3] = {smag * n[0], smag * n[1], smag * n[2]};
     const double rho = P.rho2_d + P.drho_d * phi;
     const size_t slab = (size_t)nzs * P.nxy;
     const int lu = zl * P.nxy + y * P.nx + x;
@@ -55,7 +55,6 @@ __global__ void init_kernel(const Params P, int z0, const double* __restrict__ p
     const double sg = P.sigma_d * gn;
     const double trc = (double)Lat<Q>::D - (n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
 
-    const size_t N = (size_t)P.N;
     const size_t c = (size_t)(z0 + zl) * P.nxy + (size_t)y * P.nx + x;
     double fsum = 0.0, gsum = 0.0;
 #pragma unroll
@@ -63,7 +62,7 @@ __global__ void init_kernel(const Params P, int z0, const double* __restrict__ p
         const double t = Lat<Q>::wd(i);
         const double eu = Lat<Q>::cx(i) * u[0] + Lat<Q>::cy(i) * u[1] + Lat<Q>::cz(i) * u[2];
         const double en = Lat<Q>::cx(i) * n[0] + Lat<Q>::cy(i) * n[1] + Lat<Q>::cz(i) * n[2];
-        const double es = Lat<Q>::cx(i) * S[0] + Lat<Q>::cy(i) * S[1] + Lat<Q>::cz(i) * S[2];
+        const double es = Lat<Q>::cx(i) * Sv[0] + Lat<Q>::cy(i) * Sv[1] + Lat<Q>::cz(i) * Sv[2];
         const double eg = Lat<Q>::cx(i) * gx + Lat<Q>::cy(i) * gy + Lat<Q>::cz(i) * gz;
         const double gam = 3.0 * eu + 4.5 * eu * eu - 1.5 * u2;
         const double pis = sg * ((double)Lat<Q>::e2(i) - en * en - trc / 3.0);
@@ -71,16 +70,26 @@ __global__ void init_kernel(const Params P, int z0, const double* __restrict__ p
         const double gstar = t * (phi * (1.0 + gam) + P.tau_phi_d * es) - t * (P.tau_phi_d - 0.5) * eg;
         fsum += fstar;
         gsum += gstar;
-        if (i > 0) fg[i * N + c] = make_float2((float)(fstar - t * P.w0d), (float)(gstar - t * P.phi_ref_d));
+        if (i > 0)
+            Store<S>::store(moving_plane<S>(fg, P.N, i) + c, (float)(fstar - t * P.w0d), (float)(gstar - t * P.phi_ref_d), P);
     }
-    fg[c] = make_float2((float)(fsum - P.w0d), (float)(gsum - P.phi_ref_d));  // plane 0: zeroth moments
+    moment_plane(fg)[c] = make_float2((float)(fsum - P.w0d), (float)(gsum - P.phi_ref_d));  // plane 0: zeroth moments
 }
 
 cudaError_t launch_init(const Params& P, int z0, int nzs, const double* phi0s, const double* u0s,
-                        double p0, float2* fg, cudaStream_t s) {
+                        double p0, void* fg, cudaStream_t s) {
     const dim3 grid((P.nx + kAuxBX - 1) / kAuxBX, (P.ny + kAuxBY - 1) / kAuxBY, nzs), block(kAuxBX, kAuxBY);
-    if (P.Q == 9) init_kernel<9><<<grid, block, 0, s>>>(P, z0, phi0s, u0s, p0, fg);
-    else init_kernel<19><<<grid, block, 0, s>>>(P, z0, phi0s, u0s, p0, fg);
+#define LBM_INIT(Q, S) init_kernel<Q, S><<<grid, block, 0, s>>>(P, z0, phi0s, u0s, p0, fg)
+    if (P.Q == 9) {
+        if (P.storage == STORE_F16) LBM_INIT(9, STORE_F16);
+        else if (P.storage == STORE_BF16) LBM_INIT(9, STORE_BF16);
+        else LBM_INIT(9, STORE_F32);
+    } else {
+        if (P.storage == STORE_F16) LBM_INIT(19, STORE_F16);
+        else if (P.storage == STORE_BF16) LBM_INIT(19, STORE_BF16);
+        else LBM_INIT(19, STORE_F32);
+    }
+#undef LBM_INIT
     return cudaGetLastError();
 }
 
@@ -88,8 +97,8 @@ cudaError_t launch_init(const Params& P, int z0, int nzs, const double* phi0s, c
 // Fields of the propagated current state (the values the next step collides with).
 // Output slab layout: 11 FP64 planes of nzs * nxy values: phi, p, u(3), grad phi(3), n(3).
 // ---------------------------------------------------------------------------------------
-template <int Q, int SCHEME, bool GEN>
-__global__ void moments_kernel(const Params P, int z0, const float2* __restrict__ fg,
+template <int Q, int SCHEME, bool GEN, int S>
+__global__ void moments_kernel(const Params P, int z0, const void* __restrict__ fg,
                                const float* __restrict__ phi_fd, int mask, double* __restrict__ out) {
     const int x = blockIdx.x * kAuxBX + threadIdx.x;
     const int y = blockIdx.y * kAuxBY + threadIdx.y;
@@ -99,7 +108,7 @@ __global__ void moments_kernel(const Params P, int z0, const float2* __restrict_
     const Nbr nb = make_nbr(P, x, y, z);
     const int c = (z * P.ny + y) * P.nx + x;
     float fb[Q], gb[Q];
-    pull<Q, true>(P, fg, c, nb, fb, gb);
+    pull<Q, true, S>(P, fg, c, nb, fb, gb);
     Macro m;
     macro_flow<Q, GEN>(P, fb, gb, m);
     if (SCHEME == SCHEME_DF) {
@@ -121,15 +130,23 @@ __global__ void moments_kernel(const Params P, int z0, const float2* __restrict_
     }
 }
 
-template <int Q, int SCHEME>
-static void moments_q(const Params& P, int z0, int nzs, const float2* fg, const float* phi, int mask, double* out,
-                      cudaStream_t s) {
+template <int Q, int SCHEME, int S>
+static void moments_qs(const Params& P, int z0, int nzs, const void* fg, const float* phi, int mask, double* out,
+                       cudaStream_t s) {
     const dim3 grid((P.nx + kAuxBX - 1) / kAuxBX, (P.ny + kAuxBY - 1) / kAuxBY, nzs), block(kAuxBX, kAuxBY);
-    if (P.general) moments_kernel<Q, SCHEME, true><<<grid, block, 0, s>>>(P, z0, fg, phi, mask, out);
-    else moments_kernel<Q, SCHEME, false><<<grid, block, 0, s>>>(P, z0, fg, phi, mask, out);
+    if (P.general) moments_kernel<Q, SCHEME, true, S><<<grid, block, 0, s>>>(P, z0, fg, phi, mask, out);
+    else moments_kernel<Q, SCHEME, false, S><<<grid, block, 0, s>>>(P, z0, fg, phi, mask, out);
 }
 
-cudaError_t launch_moments(const Params& P, int scheme, int z0, int nzs, const float2* fg, const float* phi_fd,
+template <int Q, int SCHEME>
+static void moments_q(const Params& P, int z0, int nzs, const void* fg, const float* phi, int mask, double* out,
+                      cudaStream_t s) {
+    if (P.storage == STORE_F16) moments_qs<Q, SCHEME, STORE_F16>(P, z0, nzs, fg, phi, mask, out, s);
+    else if (P.storage == STORE_BF16) moments_qs<Q, SCHEME, STORE_BF16>(P, z0, nzs, fg, phi, mask, out, s);
+    else moments_qs<Q, SCHEME, STORE_F32>(P, z0, nzs, fg, phi, mask, out, s);
+}
+
+cudaError_t launch_moments(const Params& P, int scheme, int z0, int nzs, const void* fg, const float* phi_fd,
                            int mask, double* out, cudaStream_t s) {
     if (P.Q == 9) {
         if (scheme == SCHEME_DF) moments_q<9, SCHEME_DF>(P, z0, nzs, fg, phi_fd, mask, out, s);
@@ -174,11 +191,10 @@ __device__ __forceinline__ void block_sum3(double (&v)[3], double* out) {
     }
 }
 
-template <int Q>
+template <int Q, int S>
 __global__ void __launch_bounds__(kRedThreads)
-mass_kernel(const Params P, const float2* __restrict__ fg, double* __restrict__ partials) {
+mass_kernel(const Params P, const void* __restrict__ fg, double* __restrict__ partials) {
     double acc[3] = {0.0, 0.0, 0.0};
-    const size_t N = (size_t)P.N;
     for (long long c = (long long)blockIdx.x * kRedThreads + threadIdx.x; c < P.N;
          c += (long long)gridDim.x * kRedThreads) {
         const int z = (int)(c / P.nxy);
@@ -186,14 +202,14 @@ mass_kernel(const Params P, const float2* __restrict__ fg, double* __restrict__ 
         const int y = r / P.nx, x = r - y * P.nx;
         const Nbr nb = make_nbr(P, x, y, z);
         float fb[Q], gb[Q];
-        pull<Q, false>(P, fg, (int)c, nb, fb, gb);
+        pull<Q, false, S>(P, fg, (int)c, nb, fb, gb);
         const double phi = P.phi_ref_d + (double)gb[0];
         acc[0] += phi;
         acc[1] += (P.rho2_d + P.drho_d * phi) * phi;
         int bad = 0;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const float2 v = __ldg(fg + i * N + c);
+            const float2 v = (i == 0) ? __ldg(moment_plane(fg) + c) : Store<S>::load(moving_plane<S>(fg, P.N, i) + c, P);
             bad += !isfinite(v.x) + !isfinite(v.y);
         }
         acc[2] += (double)bad;
@@ -214,10 +230,19 @@ int mass_partials_needed(const Params& P) {
     return (int)(blocks < 1024 ? blocks : 1024);
 }
 
-cudaError_t launch_mass(const Params& P, const float2* fg, double* partials, int n_partials, double* result,
+cudaError_t launch_mass(const Params& P, const void* fg, double* partials, int n_partials, double* result,
                         cudaStream_t s) {
-    if (P.Q == 9) mass_kernel<9><<<n_partials, kRedThreads, 0, s>>>(P, fg, partials);
-    else mass_kernel<19><<<n_partials, kRedThreads, 0, s>>>(P, fg, partials);
+#define LBM_MASS(Q, S) mass_kernel<Q, S><<<n_partials, kRedThreads, 0, s>>>(P, fg, partials)
+    if (P.Q == 9) {
+        if (P.storage == STORE_F16) LBM_MASS(9, STORE_F16);
+        else if (P.storage == STORE_BF16) LBM_MASS(9, STORE_BF16);
+        else LBM_MASS(9, STORE_F32);
+    } else {
+        if (P.storage == STORE_F16) LBM_MASS(19, STORE_F16);
+        else if (P.storage == STORE_BF16) LBM_MASS(19, STORE_BF16);
+        else LBM_MASS(19, STORE_F32);
+    }
+#undef LBM_MASS
     mass_finish<<<1, kRedThreads, 0, s>>>(partials, n_partials, result);
     return cudaGetLastError();
 }
@@ -225,18 +250,20 @@ cudaError_t launch_mass(const Params& P, const float2* fg, double* partials, int
 // ---------------------------------------------------------------------------------------
 // Device storage <-> plain FP64 populations, all Q planes of a slab (staging [Q][nzs * nxy]).
 // Plane i >= 1: v_i + t_i ref; plane 0: the rest population (ref + v_0) - sum_{i>=1} f_i.
+// Writing one set (f or g) re-encodes the other member of each stored pair unchanged: decoding
+// and re-encoding a stored FP32, scaled FP16 or BF16 value returns the same bits.
 // ---------------------------------------------------------------------------------------
-template <int Q>
-__global__ void pops_to_f64(const Params P, const float2* __restrict__ src, int is_f, int z0, int nzs,
+template <int Q, int S>
+__global__ void pops_to_f64(const Params P, const void* __restrict__ src, int is_f, int z0, int nzs,
                             double* __restrict__ dst) {
-    const size_t n = (size_t)nzs * P.nxy, base = (size_t)z0 * P.nxy, N = (size_t)P.N;
+    const size_t n = (size_t)nzs * P.nxy, base = (size_t)z0 * P.nxy;
     const double ref = is_f ? P.w0d : P.phi_ref_d;
     for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (size_t)gridDim.x * blockDim.x) {
-        const float2 m0 = src[base + l];
+        const float2 m0 = moment_plane(src)[base + l];
         double rest = ref + (double)(is_f ? m0.x : m0.y);
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
-            const float2 p = src[i * N + base + l];
+            const float2 p = Store<S>::load(moving_plane<S>(src, P.N, i) + base + l, P);
             const double v = (double)(is_f ? p.x : p.y) + Lat<Q>::wd(i) * ref;
             dst[i * n + l] = v;
             rest -= v;
@@ -245,10 +272,10 @@ __global__ void pops_to_f64(const Params P, const float2* __restrict__ src, int 
     }
 }
 
-template <int Q>
+template <int Q, int S>
 __global__ void pops_from_f64(const Params P, const double* __restrict__ src, int is_f, int z0, int nzs,
-                              float2* __restrict__ dst) {
-    const size_t n = (size_t)nzs * P.nxy, base = (size_t)z0 * P.nxy, N = (size_t)P.N;
+                              void* __restrict__ dst) {
+    const size_t n = (size_t)nzs * P.nxy, base = (size_t)z0 * P.nxy;
     const double ref = is_f ? P.w0d : P.phi_ref_d;
     for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (size_t)gridDim.x * blockDim.x) {
         double sum = src[l];
@@ -256,11 +283,16 @@ __global__ void pops_from_f64(const Params P, const double* __restrict__ src, in
         for (int i = 1; i < Q; ++i) {
             const double v = src[i * n + l];
             sum += v;
-            float* slot = is_f ? &dst[i * N + base + l].x : &dst[i * N + base + l].y;
-            *slot = (float)(v - Lat<Q>::wd(i) * ref);
+            typename Store<S>::T* slot = moving_plane<S>(dst, P.N, i) + base + l;
+            float2 p = Store<S>::load(slot, P);
+            const float w = (float)(v - Lat<Q>::wd(i) * ref);
+            if (is_f) p.x = w;
+            else p.y = w;
+            Store<S>::store(slot, p.x, p.y, P);
         }
-        float* slot0 = is_f ? &dst[base + l].x : &dst[base + l].y;
-        *slot0 = (float)(sum - ref);
+        float2* m0 = moment_plane(dst) + base + l;
+        if (is_f) m0->x = (float)(sum - ref);
+        else m0->y = (float)(sum - ref);
     }
 }
 
@@ -270,18 +302,31 @@ static unsigned conv_blocks(const Params& P, int nzs) {
     return (unsigned)(b < 4096 ? b : 4096);
 }
 
-cudaError_t launch_pops_to_f64(const Params& P, const float2* src, int is_f, int z0, int nzs, double* dst,
+#define LBM_DISPATCH_QS(KERNEL, ...)                                                       \
+    do {                                                                                   \
+        const unsigned nb_ = conv_blocks(P, nzs);                                          \
+        if (P.Q == 9) {                                                                    \
+            if (P.storage == STORE_F16) KERNEL<9, STORE_F16><<<nb_, 256, 0, s>>>(__VA_ARGS__);   \
+            else if (P.storage == STORE_BF16) KERNEL<9, STORE_BF16><<<nb_, 256, 0, s>>>(__VA_ARGS__); \
+            else KERNEL<9, STORE_F32><<<nb_, 256, 0, s>>>(__VA_ARGS__);                    \
+        } else {                                                                           \
+            if (P.storage == STORE_F16) KERNEL<19, STORE_F16><<<nb_, 256, 0, s>>>(__VA_ARGS__);  \
+            else if (P.storage == STORE_BF16) KERNEL<19, STORE_BF16><<<nb_, 256, 0, s>>>(__VA_ARGS__); \
+            else KERNEL<19, STORE_F32><<<nb_, 256, 0, s>>>(__VA_ARGS__);                   \
+        }                                                                                  \
+    } while (0)
+
+cudaError_t launch_pops_to_f64(const Params& P, const void* src, int is_f, int z0, int nzs, double* dst,
                                cudaStream_t s) {
-    if (P.Q == 9) pops_to_f64<9><<<conv_blocks(P, nzs), 256, 0, s>>>(P, src, is_f, z0, nzs, dst);
-    else pops_to_f64<19><<<conv_blocks(P, nzs), 256, 0, s>>>(P, src, is_f, z0, nzs, dst);
+    LBM_DISPATCH_QS(pops_to_f64, P, src, is_f, z0, nzs, dst);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pops_from_f64(const Params& P, const double* src, int is_f, int z0, int nzs, float2* dst,
+cudaError_t launch_pops_from_f64(const Params& P, const double* src, int is_f, int z0, int nzs, void* dst,
                                  cudaStream_t s) {
-    if (P.Q == 9) pops_from_f64<9><<<conv_blocks(P, nzs), 256, 0, s>>>(P, src, is_f, z0, nzs, dst);
-    else pops_from_f64<19><<<conv_blocks(P, nzs), 256, 0, s>>>(P, src, is_f, z0, nzs, dst);
+    LBM_DISPATCH_QS(pops_from_f64, P, src, is_f, z0, nzs, dst);
     return cudaGetLastError();
 }
+#undef LBM_DISPATCH_QS
 
 }  // namespace lbm

@@ -20,6 +20,7 @@
 
 #include "lattice.cuh"
 #include "lbm_internal.h"
+#include "storage.cuh"
 
 namespace lbm {
 
@@ -54,29 +55,28 @@ __device__ __forceinline__ int link_offset(const Nbr& n, int i, int s) {
 //             = f*_i(x) + lw_m [f*_i(x - e_i) - f*_i(x)] + lw_p [f*_i(x + e_i) - f*_i(x)],
 // the same for g, and the zeroth moments fb[0] = sum fbar - w0, gb[0] = phi - phi_ref of the
 // propagated state. Each load brings the (f_i, g_i) pair of one cell.
-template <int Q, bool WITH_F>
-__device__ __forceinline__ void pull(const Params& P, const float2* __restrict__ fg, int c, const Nbr& nb,
+template <int Q, bool WITH_F, int S>
+__device__ __forceinline__ void pull(const Params& P, const void* __restrict__ state, int c, const Nbr& nb,
                                      float (&fb)[Q], float (&gb)[Q]) {
-    const size_t N = (size_t)P.N;
-    float df = 0.f, dg = 0.f;
+    float df = 0.f, dg = 0.f;  // increments in storage units
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-        const float2* q = fg + i * N;
-        const float2 v0 = __ldg(q + c);
-        const float2 vm = __ldg(q + c + link_offset<Q>(nb, i, -1));
-        const float2 vp = __ldg(q + c + link_offset<Q>(nb, i, +1));
+        const typename Store<S>::T* q = moving_plane<S>(state, P.N, i);
+        const float2 v0 = Store<S>::load_raw(q + c);
+        const float2 vm = Store<S>::load_raw(q + c + link_offset<Q>(nb, i, -1));
+        const float2 vp = Store<S>::load_raw(q + c + link_offset<Q>(nb, i, +1));
         const float d = P.lw_m * (vm.y - v0.y) + P.lw_p * (vp.y - v0.y);
-        gb[i] = v0.y + d;
+        gb[i] = (v0.y + d) * Store<S>::kInvG;
         dg += d;
         if (WITH_F) {
             const float e = P.lw_m * (vm.x - v0.x) + P.lw_p * (vp.x - v0.x);
-            fb[i] = v0.x + e;
+            fb[i] = (v0.x + e) * Store<S>::kInvF;
             df += e;
         }
     }
-    const float2 m0 = __ldg(fg + c);
-    gb[0] = m0.y + dg;
-    if (WITH_F) fb[0] = m0.x + df;
+    const float2 m0 = __ldg(moment_plane(state) + c);
+    gb[0] = m0.y + dg * Store<S>::kInvG;
+    if (WITH_F) fb[0] = m0.x + df * Store<S>::kInvF;
 }
 
 struct Macro {

@@ -13,6 +13,7 @@
 #include "../../include/lbm.h"
 #include "lattice.cuh"
 #include "lbm_internal.h"
+#include "storage.cuh"
 
 using lbm::Params;
 
@@ -23,7 +24,7 @@ struct lbm_ctx {
     int device;
     cudaStream_t stream;
     bool own_stream;
-    float2* fg[2];         // ping-pong state: Q planes of N (f, g) pairs each
+    void* fg[2];           // ping-pong state: Q planes of N (f, g) pairs each (storage.cuh)
     int cur;               // index of the buffer holding the current state
     float* phi_fd;         // propagated phi plane of the finite-difference variant
     double* partials;      // per-block FP64 partial sums of the mass reduction
@@ -145,7 +146,8 @@ int lbm_create(lbm_ctx** out, const int grid[3], int lattice, double tau_f, doub
     if (lattice == LBM_D2Q9 && G[2] != 0) return set_error(nullptr, LBM_EINVAL, "D2Q9 needs body_force[2] = 0");
     if (o.scheme != LBM_SCHEME_DIFFERENCE_FREE && o.scheme != LBM_SCHEME_FINITE_DIFFERENCE)
         return set_error(nullptr, LBM_EINVAL, "unknown scheme %d", o.scheme);
-    if (o.storage != 0) return set_error(nullptr, LBM_EINVAL, "storage %d is not built (0 = FP32)", o.storage);
+    if (o.storage < 0 || o.storage > 2)
+        return set_error(nullptr, LBM_EINVAL, "storage must be 0 (FP32), 1 (FP16) or 2 (BF16), got %d", o.storage);
     if (o.walls != 0) return set_error(nullptr, LBM_EINVAL, "walls %d are not built (0 = periodic)", o.walls);
     if (!(o.courant > 0 && o.courant <= 1)) return set_error(nullptr, LBM_EINVAL, "courant must be in (0, 1]");
 
@@ -188,6 +190,13 @@ int lbm_create(lbm_ctx** out, const int grid[3], int lattice, double tau_f, doub
     P.w0 = 1.0f;       // p0 = cs^2 until lbm_init_phi sets it
     P.phi_ref = 1.0f;  // until lbm_init_phi picks the bulk phase of phi0
     P.general = (rho_ratio != 1.0 || mu_ratio != 1.0 || G[0] != 0 || G[1] != 0 || G[2] != 0) ? 1 : 0;
+    P.storage = o.storage;
+    // FP16 storage: f deviations scaled by 2^12 and g deviations by 2^10 (exact power-of-two
+    // scaling) so that they sit in the normal FP16 range; 1 for FP32 and BF16
+    P.scale_f = (o.storage == lbm::STORE_F16) ? 4096.0f : 1.0f;
+    P.scale_g = (o.storage == lbm::STORE_F16) ? 1024.0f : 1.0f;
+    P.inv_scale_f = 1.0f / P.scale_f;
+    P.inv_scale_g = 1.0f / P.scale_g;
     P.w0d = 1.0;
     P.phi_ref_d = 1.0;
     P.tau_phi_d = tau_phi;
@@ -213,7 +222,7 @@ int lbm_create(lbm_ctx** out, const int grid[3], int lattice, double tau_f, doub
         }
         c->own_stream = true;
     }
-    const size_t pop_bytes = (size_t)lattice * (size_t)N * sizeof(float2);
+    const size_t pop_bytes = lbm::state_bytes(lattice, N, o.storage);
     for (int k = 0; k < 2 && rc == LBM_OK; ++k) {
         cudaError_t e = cudaMalloc(&c->fg[k], pop_bytes);
         if (e != cudaSuccess)
@@ -302,7 +311,7 @@ static int fields_out(lbm_ctx* c, int mask, double* const* dst /* 11 planes, NUL
     const int nzs = slab_depth(c, 11, 0);
     rc = ensure_staging(c, (size_t)11 * nzs * nxy);
     if (rc) return rc;
-    const float2* fg = c->fg[c->cur];
+    const void* fg = c->fg[c->cur];
     if (c->scheme == LBM_SCHEME_FINITE_DIFFERENCE) {
         LBM_CUDA(c, lbm::launch_fd_phi(P, fg, c->phi_fd, c->stream));
         c->launches += 1;
@@ -369,7 +378,7 @@ static int pops_io(lbm_ctx* c, double* f_out, double* g_out, const double* f_in,
     for (int is_f = 1; is_f >= 0; --is_f) {
         double* host_out = is_f ? f_out : g_out;
         const double* host_in = is_f ? f_in : g_in;
-        float2* dev = c->fg[c->cur];
+        void* dev = c->fg[c->cur];
         if (!host_out && !host_in) continue;
         for (int z0 = 0; z0 < P.nz; z0 += nzs) {
             const int n = (z0 + nzs <= P.nz) ? nzs : P.nz - z0;

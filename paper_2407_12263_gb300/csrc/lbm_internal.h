@@ -28,43 +28,47 @@ struct Params {
     float w0;              // storage shift of f: f_i is held as f_i - t_i w0 (w0 = p0 / cs^2)
     float phi_ref;         // storage shift of g: g_i is held as g_i - t_i phi_ref (phi_ref = 0 or 1)
     int general;           // 1 if any of drho, G, mu_m1 is non-zero (selects the full collision)
+    int storage;           // enum StorageKind of the moving planes
+    float scale_f, scale_g, inv_scale_f, inv_scale_g;  // FP16 storage scaling (powers of two)
     // FP64 copies for the initialisation and the conversions to and from FP64 host arrays
     double w0d, phi_ref_d, tau_phi_d, sigma_d, four_over_delta_d, drho_d, rho2_d;
 };
 
 enum Scheme { SCHEME_DF = 0, SCHEME_FD = 1 };
+enum StorageKind { STORE_F32 = 0, STORE_F16 = 1, STORE_BF16 = 2 };
 
-// Launchers (return the launch's cudaError_t). The state is one buffer of Q planes of N float2
-// pairs (f, g): plane i >= 1 holds (f_i - t_i w0, g_i - t_i phi_ref); plane 0 holds the zeroth
-// moments of the shifted sets, (sum_i f_i - w0, sum_i g_i - phi_ref = phi - phi_ref), in place
-// of the rest populations, which they determine exactly. f_i and g_i share their propagation
-// stencil, so one 8-byte load serves both.
-cudaError_t launch_step(const Params& P, int scheme, const float2* fg_in, float2* fg_out, float* phi_fd,
+// Launchers (return the launch's cudaError_t). The state is one buffer of Q planes of N (f, g)
+// pairs: plane i >= 1 holds (f_i - t_i w0, g_i - t_i phi_ref) in the storage type (FP32, FP16
+// or BF16, see storage.cuh); plane 0 holds the zeroth moments of the shifted sets in FP32,
+// (sum_i f_i - w0, sum_i g_i - phi_ref = phi - phi_ref), in place of the rest populations,
+// which they determine exactly. f_i and g_i share their propagation stencil, so one load
+// serves both.
+cudaError_t launch_step(const Params& P, int scheme, const void* fg_in, void* fg_out, float* phi_fd,
                         cudaStream_t s, int* launches);
-cudaError_t launch_fd_phi(const Params& P, const float2* fg_in, float* phi_fd, cudaStream_t s);
+cudaError_t launch_fd_phi(const Params& P, const void* fg_in, float* phi_fd, cudaStream_t s);
 
 // Initial populations for z in [z0, z0 + nzs). phi0s holds planes z0-1 .. z0+nzs of phi0
 // (periodic images for the two halo planes; D2Q9 holds the single plane at index 1);
 // u0s (or nullptr) holds 3 x nzs planes of the velocity for the slab.
 cudaError_t launch_init(const Params& P, int z0, int nzs, const double* phi0s, const double* u0s,
-                        double p0, float2* fg, cudaStream_t s);
+                        double p0, void* fg, cudaStream_t s);
 
 // Macroscopic fields for z in [z0, z0 + nzs) written as FP64 planes of the slab into out:
 // plane k of field j at out + (j * nzs) * nxy ... see the field order in the definition.
 // mask selects the fields: bit 0 phi, 1 p, 2 u (3 planes), 3 grad phi (3), 4 n (3).
-cudaError_t launch_moments(const Params& P, int scheme, int z0, int nzs, const float2* fg,
+cudaError_t launch_moments(const Params& P, int scheme, int z0, int nzs, const void* fg,
                            const float* phi_fd, int mask, double* out, cudaStream_t s);
 
 // sum phi, sum rho phi (FP64) and the count of non-finite stored populations.
-cudaError_t launch_mass(const Params& P, const float2* fg, double* partials, int n_partials,
+cudaError_t launch_mass(const Params& P, const void* fg, double* partials, int n_partials,
                         double* result /* 3 doubles */, cudaStream_t s);
 int mass_partials_needed(const Params& P);
 
 // All Q populations of the slab [z0, z0 + nzs) between the device storage and FP64 staging
 // holding plain populations (Q planes of nzs * nxy values).
-cudaError_t launch_pops_to_f64(const Params& P, const float2* src, int is_f, int z0, int nzs, double* dst,
+cudaError_t launch_pops_to_f64(const Params& P, const void* src, int is_f, int z0, int nzs, double* dst,
                                cudaStream_t s);
-cudaError_t launch_pops_from_f64(const Params& P, const double* src, int is_f, int z0, int nzs, float2* dst,
+cudaError_t launch_pops_from_f64(const Params& P, const double* src, int is_f, int z0, int nzs, void* dst,
                                  cudaStream_t s);
 
 }  // namespace lbm

@@ -27,9 +27,9 @@ namespace lbm {
 #endif
 constexpr int kStepThreads = 128;
 
-template <int Q, int SCHEME, bool GEN>
+template <int Q, int SCHEME, bool GEN, int S>
 __global__ void __launch_bounds__(kStepThreads, LBM_STEP_MINB)
-step_kernel(const Params P, const float2* __restrict__ fg_in, float2* __restrict__ fg_out,
+step_kernel(const Params P, const void* __restrict__ fg_in, void* __restrict__ fg_out,
             const float* __restrict__ phi_fd) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -39,7 +39,7 @@ step_kernel(const Params P, const float2* __restrict__ fg_in, float2* __restrict
     const int c = (z * P.ny + y) * P.nx + x;
 
     float fb[Q], gb[Q];
-    pull<Q, true>(P, fg_in, c, nb, fb, gb);
+    pull<Q, true, S>(P, fg_in, c, nb, fb, gb);
 
     Macro m;
     macro_flow<Q, GEN>(P, fb, gb, m);
@@ -53,16 +53,16 @@ step_kernel(const Params P, const float2* __restrict__ fg_in, float2* __restrict
     macro_pressure<GEN>(P, m);
     collide<Q, GEN>(P, m, fb, gb);
 
-    const size_t N = (size_t)P.N;
+    // streaming stores: the output is not re-read this step
+    __stcs(moment_plane(fg_out) + c, make_float2(fb[0], gb[0]));
 #pragma unroll
-    for (int i = 0; i < Q; ++i)  // streaming stores: the output is not re-read this step
-        __stcs(fg_out + i * N + c, make_float2(fb[i], gb[i]));
+    for (int i = 1; i < Q; ++i) Store<S>::store(moving_plane<S>(fg_out, P.N, i) + c, fb[i], gb[i], P);
 }
 
 // Finite-difference variant, pass 1: the propagated phi (held as phi - phi_ref), one FP32 plane.
-template <int Q>
+template <int Q, int S>
 __global__ void __launch_bounds__(kStepThreads, LBM_STEP_MINB)
-fd_phi_kernel(const Params P, const float2* __restrict__ fg_in, float* __restrict__ phi) {
+fd_phi_kernel(const Params P, const void* __restrict__ fg_in, float* __restrict__ phi) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
@@ -70,7 +70,7 @@ fd_phi_kernel(const Params P, const float2* __restrict__ fg_in, float* __restric
     const Nbr nb = make_nbr(P, x, y, z);
     const int c = (z * P.ny + y) * P.nx + x;
     float fb[Q], gb[Q];
-    pull<Q, false>(P, fg_in, c, nb, fb, gb);
+    pull<Q, false, S>(P, fg_in, c, nb, fb, gb);
     phi[c] = gb[0];
 }
 
@@ -81,33 +81,52 @@ static dim3 step_grid(const Params& P) {
     return dim3((P.nx + b.x - 1) / b.x, (P.ny + b.y - 1) / b.y, P.nz);
 }
 
-template <int Q>
-static cudaError_t step_q(const Params& P, int scheme, const float2* in, float2* out, float* phi, cudaStream_t s,
-                          int* launches) {
+template <int Q, int S>
+static cudaError_t step_qs(const Params& P, int scheme, const void* in, void* out, float* phi, cudaStream_t s,
+                           int* launches) {
     const dim3 grid = step_grid(P), block = step_block(P);
     if (scheme == SCHEME_DF) {
-        if (P.general) step_kernel<Q, SCHEME_DF, true><<<grid, block, 0, s>>>(P, in, out, nullptr);
-        else step_kernel<Q, SCHEME_DF, false><<<grid, block, 0, s>>>(P, in, out, nullptr);
+        if (P.general) step_kernel<Q, SCHEME_DF, true, S><<<grid, block, 0, s>>>(P, in, out, nullptr);
+        else step_kernel<Q, SCHEME_DF, false, S><<<grid, block, 0, s>>>(P, in, out, nullptr);
         *launches += 1;
     } else {
-        fd_phi_kernel<Q><<<grid, block, 0, s>>>(P, in, phi);
-        if (P.general) step_kernel<Q, SCHEME_FD, true><<<grid, block, 0, s>>>(P, in, out, phi);
-        else step_kernel<Q, SCHEME_FD, false><<<grid, block, 0, s>>>(P, in, out, phi);
+        fd_phi_kernel<Q, S><<<grid, block, 0, s>>>(P, in, phi);
+        if (P.general) step_kernel<Q, SCHEME_FD, true, S><<<grid, block, 0, s>>>(P, in, out, phi);
+        else step_kernel<Q, SCHEME_FD, false, S><<<grid, block, 0, s>>>(P, in, out, phi);
         *launches += 2;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_step(const Params& P, int scheme, const float2* fg_in, float2* fg_out, float* phi_fd,
-                        cudaStream_t s, int* launches) {
+template <int Q>
+static cudaError_t step_q(const Params& P, int scheme, const void* in, void* out, float* phi, cudaStream_t s,
+                          int* launches) {
+    if (P.storage == STORE_F16) return step_qs<Q, STORE_F16>(P, scheme, in, out, phi, s, launches);
+    if (P.storage == STORE_BF16) return step_qs<Q, STORE_BF16>(P, scheme, in, out, phi, s, launches);
+    return step_qs<Q, STORE_F32>(P, scheme, in, out, phi, s, launches);
+}
+
+cudaError_t launch_step(const Params& P, int scheme, const void* fg_in, void* fg_out, float* phi_fd, cudaStream_t s,
+                        int* launches) {
     if (P.Q == 9) return step_q<9>(P, scheme, fg_in, fg_out, phi_fd, s, launches);
     return step_q<19>(P, scheme, fg_in, fg_out, phi_fd, s, launches);
 }
 
-cudaError_t launch_fd_phi(const Params& P, const float2* fg_in, float* phi_fd, cudaStream_t s) {
-    const dim3 grid = step_grid(P), block = step_block(P);
-    if (P.Q == 9) fd_phi_kernel<9><<<grid, block, 0, s>>>(P, fg_in, phi_fd);
-    else fd_phi_kernel<19><<<grid, block, 0, s>>>(P, fg_in, phi_fd);
+template <int Q, int S>
+static void fd_phi_qs(const Params& P, const void* in, float* phi, cudaStream_t s) {
+    fd_phi_kernel<Q, S><<<step_grid(P), step_block(P), 0, s>>>(P, in, phi);
+}
+
+cudaError_t launch_fd_phi(const Params& P, const void* fg_in, float* phi_fd, cudaStream_t s) {
+    if (P.Q == 9) {
+        if (P.storage == STORE_F16) fd_phi_qs<9, STORE_F16>(P, fg_in, phi_fd, s);
+        else if (P.storage == STORE_BF16) fd_phi_qs<9, STORE_BF16>(P, fg_in, phi_fd, s);
+        else fd_phi_qs<9, STORE_F32>(P, fg_in, phi_fd, s);
+    } else {
+        if (P.storage == STORE_F16) fd_phi_qs<19, STORE_F16>(P, fg_in, phi_fd, s);
+        else if (P.storage == STORE_BF16) fd_phi_qs<19, STORE_BF16>(P, fg_in, phi_fd, s);
+        else fd_phi_qs<19, STORE_F32>(P, fg_in, phi_fd, s);
+    }
     return cudaGetLastError();
 }
 

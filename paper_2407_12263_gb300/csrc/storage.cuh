@@ -1,0 +1,88 @@
+// storage.cuh -- how the (f_i, g_i) pairs are held in device memory.
+//
+// The state buffer holds plane 0 (the zeroth moments of the shifted sets) as FP32 pairs,
+// followed by planes 1..Q-1 (the shifted moving populations) in the storage type:
+//   STORE_F32   float2 (8 bytes per pair)
+//   STORE_F16   __half2 (4 bytes), f scaled by 2^12 and g by 2^10 before rounding, so the
+//               deviations sit in the normal FP16 range (|f - t w0| < 16, |g - t phi_ref| < 64)
+//   STORE_BF16  __nv_bfloat162 (4 bytes), no scaling (BF16 has the FP32 exponent range)
+// All arithmetic is FP32 in every case. Keeping plane 0 in FP32 keeps phi (and sum f)
+// at FP32 precision and sum phi conserved to FP32 round-off: the Lax-Wendroff increments that
+// update plane 0 telescope over the grid whatever precision the moving populations carry.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+template <int S>
+struct Store;
+
+// load_raw returns the stored pair in storage units (scaled for FP16); kInvF / kInvG turn
+// storage units into population units. load() applies them. The Lax-Wendroff update is linear,
+// so it runs on raw values and the scale is applied once per population afterwards.
+template <>
+struct Store<STORE_F32> {
+    using T = float2;
+    static constexpr float kScaleF = 1.0f, kScaleG = 1.0f, kInvF = 1.0f, kInvG = 1.0f;
+    __device__ __forceinline__ static float2 load_raw(const T* p) { return __ldg(p); }
+    __device__ __forceinline__ static float2 load(const T* p, const Params&) { return __ldg(p); }
+    __device__ __forceinline__ static void store(T* p, float f, float g, const Params&) {
+        __stcs(p, make_float2(f, g));
+    }
+};
+
+template <>
+struct Store<STORE_F16> {
+    using T = __half2;
+    static constexpr float kScaleF = 4096.0f, kScaleG = 1024.0f, kInvF = 1.0f / 4096.0f, kInvG = 1.0f / 1024.0f;
+    __device__ __forceinline__ static float2 load_raw(const T* p) { return __half22float2(__ldg(p)); }
+    __device__ __forceinline__ static float2 load(const T* p, const Params&) {
+        const float2 v = __half22float2(__ldg(p));
+        return make_float2(v.x * kInvF, v.y * kInvG);
+    }
+    __device__ __forceinline__ static void store(T* p, float f, float g, const Params&) {
+        const __half2 h = __floats2half2_rn(f * kScaleF, g * kScaleG);
+        __stcs(reinterpret_cast<unsigned int*>(p), *reinterpret_cast<const unsigned int*>(&h));
+    }
+};
+
+template <>
+struct Store<STORE_BF16> {
+    using T = __nv_bfloat162;
+    static constexpr float kScaleF = 1.0f, kScaleG = 1.0f, kInvF = 1.0f, kInvG = 1.0f;
+    __device__ __forceinline__ static float2 load_raw(const T* p) { return __bfloat1622float2(__ldg(p)); }
+    __device__ __forceinline__ static float2 load(const T* p, const Params&) { return __bfloat1622float2(__ldg(p)); }
+    __device__ __forceinline__ static void store(T* p, float f, float g, const Params&) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(f, g);
+        __stcs(reinterpret_cast<unsigned int*>(p), *reinterpret_cast<const unsigned int*>(&h));
+    }
+};
+
+// Plane 0 (FP32 pairs) and the moving planes of a state buffer.
+__host__ __device__ __forceinline__ const float2* moment_plane(const void* state) {
+    return static_cast<const float2*>(state);
+}
+__host__ __device__ __forceinline__ float2* moment_plane(void* state) { return static_cast<float2*>(state); }
+
+template <int S>
+__host__ __device__ __forceinline__ const typename Store<S>::T* moving_plane(const void* state, long long N, int i) {
+    return reinterpret_cast<const typename Store<S>::T*>(static_cast<const char*>(state) + (size_t)N * sizeof(float2)) +
+           (size_t)(i - 1) * (size_t)N;
+}
+template <int S>
+__host__ __device__ __forceinline__ typename Store<S>::T* moving_plane(void* state, long long N, int i) {
+    return reinterpret_cast<typename Store<S>::T*>(static_cast<char*>(state) + (size_t)N * sizeof(float2)) +
+           (size_t)(i - 1) * (size_t)N;
+}
+
+// Bytes of one state buffer.
+inline size_t state_bytes(int Q, long long N, int storage) {
+    const size_t pair = (storage == STORE_F32) ? sizeof(float2) : 4;
+    return (size_t)N * sizeof(float2) + (size_t)(Q - 1) * (size_t)N * pair;
+}
+
+}  // namespace lbm

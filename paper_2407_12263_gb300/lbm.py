@@ -18,6 +18,7 @@ import numpy as np
 LBM_D2Q9, LBM_D3Q19 = 9, 19
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENONFINITE, LBM_ETIMEOUT, LBM_ESTATE = 0, -1, -2, -3, -4, -5, -6
 LBM_SCHEME_DIFFERENCE_FREE, LBM_SCHEME_FINITE_DIFFERENCE = 0, 1
+LBM_STORAGE_FP32, LBM_STORAGE_FP16, LBM_STORAGE_BF16 = 0, 1, 2
 
 _LIB_PATH = Path(__file__).resolve().parent / "_build" / "liblbm_gb300.so"
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -182,9 +183,10 @@ class Lattice:
     """One handle; arrays shaped (nz, ny, nx). Same parameters as lbm_create."""
 
     def __init__(self, grid, lattice, tau_f, tau_g, M, xi, sigma, rho_ratio=1.0, mu_ratio=1.0,
-                 body_force=(0.0, 0.0, 0.0), scheme=LBM_SCHEME_DIFFERENCE_FREE, courant=0.997, stream=None):
+                 body_force=(0.0, 0.0, 0.0), scheme=LBM_SCHEME_DIFFERENCE_FREE, courant=0.997, stream=None,
+                 storage=LBM_STORAGE_FP32):
         o = lbm_default_opts()
-        o.scheme, o.courant = scheme, courant
+        o.scheme, o.courant, o.storage = scheme, courant, storage
         o.stream = stream
         self.h = lbm_create(grid, lattice, tau_f, tau_g, M, xi, sigma, rho_ratio, mu_ratio, body_force, o)
         nx, ny, nz = grid

@@ -71,7 +71,7 @@ def test_create_rejects_invalid_arguments(lib, over):
     assert lbm.lbm_last_error(None) != "no error"
 
 
-@pytest.mark.parametrize("field,value", [("scheme", 5), ("storage", 1), ("walls", 1), ("courant", 0.0),
+@pytest.mark.parametrize("field,value", [("scheme", 5), ("storage", 3), ("storage", -1), ("walls", 1), ("courant", 0.0),
                                          ("courant", 1.5)])
 def test_create_rejects_invalid_options(lib, field, value):
     o = lbm.lbm_default_opts()
