@@ -218,6 +218,7 @@ def run_ours(args):
                 "kernel": "step_kernel<19, difference-free>"}
 
     e2e = run_e2e(lbm, torch, grid, w, params, phi0, cells, args, world)
+    small = run_small_2d(lbm, torch, stream, args, world)
 
     out = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(t_df / args.steps * 1e3, 5), "higher_is_better": True,
@@ -236,6 +237,7 @@ def run_ours(args):
                   "hbm_frac": round(BYTES_PER_CELL["fd"] * cells / (t_fd / args.steps) / 1e9 / peak, 4)},
            "df_vs_fd": round(value / fd_value, 4),
            "storage16": sixteen,
+           "droplet2d_64": small,
            "sum_phi_drift": {"df": drift, "fd": fd_drift, "steps": args.warmup + args.steps}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"], out["accuracy"] = run_cpu_baseline(lbm, grid, w, params, phi0, cells, args)
@@ -244,6 +246,32 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_small_2d(lbm, torch, stream, args, world):
+    """The 2D droplet (D2Q9, 64^2, 4096 cells): 0.6 MB of state that stays in L2, so each step is
+    a few microseconds of launch overhead and kernel; timed with CUDA graph replay (the default,
+    32 steps per graph) and with one launch per step."""
+    w = I.WORKLOADS["droplet2d_64"]
+    phi0 = I.droplet_phi(w["grid"], w["R"], w["xi"])
+    params = dict(tau_f=w["tau_f"], tau_g=w["tau_g"], M=w["M"], xi=w["xi"], sigma=w["sigma"])
+    cells = w["grid"][0] * w["grid"][1]
+    out = {"unit": "MLUPS", "steps": args.steps, "note": "L2-resident and launch-bound: no roofline claim"}
+    for name, gsteps in (("graphs", 32), ("direct", 0)):
+        g = lbm.Lattice(w["grid"], w["Q"], stream=stream.cuda_stream, graph_steps=gsteps, **params)
+        g.init_phi(phi0)
+        g.step(max(args.warmup, 64))
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        g.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        secs = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, world)
+        out[name] = round(aggregate_mlups(cells, args.steps, secs, world), 1)
+        out[name + "_us_per_step"] = round(secs / args.steps * 1e6, 3)
+        g.close()
+    return out
 
 
 def run_e2e(lbm, torch, grid, w, params, phi0, cells, args, world):

@@ -71,6 +71,9 @@ typedef struct {
     double courant; /* Lax-Wendroff Courant number c, 0 < c <= 1; default 0.997 (Sec. 2.2) */
     int walls;      /* 0 = fully periodic (the only boundary built) */
     void *stream;   /* cudaStream_t the handle launches on; NULL = a stream the handle owns */
+    int graph_steps; /* lbm_step replays CUDA graphs of this many steps (even, >= 2; default 32);
+                        0 launches every step directly. Steps run inside a caller's own stream
+                        capture are always launched directly, so they land in that graph */
 } lbm_opts;
 
 /* Fill *opts with the defaults above. */
@@ -105,7 +108,9 @@ int lbm_create(lbm_ctx **out, const int grid[3], int lattice, double tau_f, doub
  */
 int lbm_init_phi(lbm_ctx *ctx, const double *phi0, const double *u0, double p0);
 
-/* Advance n >= 0 time steps (asynchronous on the handle's stream). */
+/* Advance n >= 0 time steps (asynchronous on the handle's stream). Whole multiples of
+ * opts.graph_steps are replayed from CUDA graphs the handle captures on first use; the rest
+ * are launched directly. Both give bit-identical results. */
 int lbm_step(lbm_ctx *ctx, int n);
 
 /*

@@ -34,6 +34,8 @@ struct lbm_ctx {
     size_t staging_elems;
     bool initialised;
     long long launches;
+    int graph_steps;                  // steps per replayed CUDA graph (0 = none)
+    cudaGraphExec_t graph_exec[2];    // graph of graph_steps steps starting from buffer 0 / 1
     char err[512];
 };
 
@@ -71,6 +73,8 @@ void free_ctx(lbm_ctx* c) {
     cudaFree(c->partials);
     cudaFree(c->result);
     cudaFree(c->staging);
+    for (int k = 0; k < 2; ++k)
+        if (c->graph_exec[k]) cudaGraphExecDestroy(c->graph_exec[k]);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -95,6 +99,35 @@ int slab_depth(const lbm_ctx* c, int planes_per_z, int extra_planes) {
     return (int)nzs;
 }
 
+void drop_graphs(lbm_ctx* c) {
+    for (int k = 0; k < 2; ++k)
+        if (c->graph_exec[k]) {
+            cudaGraphExecDestroy(c->graph_exec[k]);
+            c->graph_exec[k] = nullptr;
+        }
+}
+
+// Captures graph_steps steps starting from buffer `start` (an even count returns to it).
+int capture_graph(lbm_ctx* c, int start) {
+    cudaGraph_t graph = nullptr;
+    LBM_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    int launches = 0, cur = start;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < c->graph_steps && e == cudaSuccess; ++k) {
+        e = lbm::launch_step(c->P, c->scheme, c->fg[cur], c->fg[1 - cur], c->phi_fd, c->stream, &launches);
+        cur = 1 - cur;
+    }
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph_exec[start], graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        c->graph_exec[start] = nullptr;
+        return set_error(c, LBM_ECUDA, "capturing the step graph failed: %s", cudaGetErrorString(e));
+    }
+    return LBM_OK;
+}
+
 int check_ctx(lbm_ctx* c) {
     if (!c) return set_error(nullptr, LBM_EINVAL, "null handle");
     LBM_CUDA(c, cudaSetDevice(c->device));
@@ -112,6 +145,7 @@ void lbm_default_opts(lbm_opts* o) {
     o->courant = 0.997;
     o->walls = 0;
     o->stream = nullptr;
+    o->graph_steps = 32;
 }
 
 int lbm_create(lbm_ctx** out, const int grid[3], int lattice, double tau_f, double tau_g, double M, double xi,
@@ -150,6 +184,8 @@ int lbm_create(lbm_ctx** out, const int grid[3], int lattice, double tau_f, doub
         return set_error(nullptr, LBM_EINVAL, "storage must be 0 (FP32), 1 (FP16) or 2 (BF16), got %d", o.storage);
     if (o.walls != 0) return set_error(nullptr, LBM_EINVAL, "walls %d are not built (0 = periodic)", o.walls);
     if (!(o.courant > 0 && o.courant <= 1)) return set_error(nullptr, LBM_EINVAL, "courant must be in (0, 1]");
+    if (o.graph_steps < 0 || o.graph_steps == 1 || (o.graph_steps & 1))
+        return set_error(nullptr, LBM_EINVAL, "graph_steps must be 0 or an even count >= 2 (got %d)", o.graph_steps);
 
     lbm_ctx* c = new (std::nothrow) lbm_ctx();
     if (!c) return set_error(nullptr, LBM_ENOMEM, "host allocation failed");
@@ -157,6 +193,7 @@ int lbm_create(lbm_ctx** out, const int grid[3], int lattice, double tau_f, doub
     std::snprintf(c->err, sizeof c->err, "no error");
     c->scheme = o.scheme;
     c->courant = o.courant;
+    c->graph_steps = o.graph_steps;
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         delete c;
         return set_error(nullptr, LBM_ECUDA, "no CUDA device available");
@@ -259,6 +296,7 @@ int lbm_init_phi(lbm_ctx* c, const double* phi0, const double* u0, double p0) {
     if (!is_fin(mean)) return set_error(c, LBM_EINVAL, "phi0 is not finite");
     P.phi_ref_d = (mean >= 0.5) ? 1.0 : 0.0;
     P.phi_ref = (float)P.phi_ref_d;
+    drop_graphs(c);  // captured steps carry the old parameters
     const size_t nxy = (size_t)P.nxy;
     const int per_z = 1 + (u0 ? 3 : 0);
     const int nzs = slab_depth(c, per_z, 2);
@@ -292,6 +330,20 @@ int lbm_step(lbm_ctx* c, int n) {
     if (rc) return rc;
     if (n < 0) return set_error(c, LBM_EINVAL, "n must be >= 0 (got %d)", n);
     if (!c->initialised) return set_error(c, LBM_ESTATE, "lbm_step before lbm_init_phi");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    LBM_CUDA(c, cudaStreamIsCapturing(c->stream, &cap));
+    if (c->graph_steps > 0 && cap == cudaStreamCaptureStatusNone) {
+        const int per_step = (c->scheme == LBM_SCHEME_FINITE_DIFFERENCE) ? 2 : 1;
+        while (n >= c->graph_steps) {
+            if (!c->graph_exec[c->cur]) {
+                rc = capture_graph(c, c->cur);
+                if (rc) return rc;
+            }
+            LBM_CUDA(c, cudaGraphLaunch(c->graph_exec[c->cur], c->stream));
+            c->launches += (long long)per_step * c->graph_steps;
+            n -= c->graph_steps;  // an even number of steps leaves the current buffer unchanged
+        }
+    }
     for (int k = 0; k < n; ++k) {
         const int a = c->cur, b = 1 - c->cur;
         int launches = 0;

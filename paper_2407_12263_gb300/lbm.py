@@ -27,7 +27,7 @@ _ip = ctypes.POINTER(ctypes.c_int)
 
 class lbm_opts(ctypes.Structure):
     _fields_ = [("scheme", ctypes.c_int), ("storage", ctypes.c_int), ("courant", ctypes.c_double),
-                ("walls", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("walls", ctypes.c_int), ("stream", ctypes.c_void_p), ("graph_steps", ctypes.c_int)]
 
 
 class LBMError(RuntimeError):
@@ -184,9 +184,11 @@ class Lattice:
 
     def __init__(self, grid, lattice, tau_f, tau_g, M, xi, sigma, rho_ratio=1.0, mu_ratio=1.0,
                  body_force=(0.0, 0.0, 0.0), scheme=LBM_SCHEME_DIFFERENCE_FREE, courant=0.997, stream=None,
-                 storage=LBM_STORAGE_FP32):
+                 storage=LBM_STORAGE_FP32, graph_steps=None):
         o = lbm_default_opts()
         o.scheme, o.courant, o.storage = scheme, courant, storage
+        if graph_steps is not None:
+            o.graph_steps = graph_steps
         o.stream = stream
         self.h = lbm_create(grid, lattice, tau_f, tau_g, M, xi, sigma, rho_ratio, mu_ratio, body_force, o)
         nx, ny, nz = grid

@@ -72,7 +72,8 @@ def test_create_rejects_invalid_arguments(lib, over):
 
 
 @pytest.mark.parametrize("field,value", [("scheme", 5), ("storage", 3), ("storage", -1), ("walls", 1), ("courant", 0.0),
-                                         ("courant", 1.5)])
+                                         ("courant", 1.5), ("graph_steps", 1), ("graph_steps", 3),
+                                         ("graph_steps", -2)])
 def test_create_rejects_invalid_options(lib, field, value):
     o = lbm.lbm_default_opts()
     setattr(o, field, value)
@@ -83,7 +84,7 @@ def test_create_rejects_invalid_options(lib, field, value):
 
 def test_default_options(lib):
     o = lbm.lbm_default_opts()
-    assert (o.scheme, o.storage, o.courant, o.walls) == (0, 0, 0.997, 0)
+    assert (o.scheme, o.storage, o.courant, o.walls, o.graph_steps) == (0, 0, 0.997, 0, 32)
     assert o.stream is None
 
 
