@@ -64,6 +64,7 @@ def _load():
                                   + [ctypes.c_int] * 4)
     lib.oracle_create.restype = ctypes.c_void_p
     lib.oracle_destroy.argtypes = [ctypes.c_void_p]
+    lib.oracle_set_walls.argtypes = [ctypes.c_void_p, ctypes.c_int]
     lib.oracle_tau_phi.argtypes = [ctypes.c_void_p]
     lib.oracle_tau_phi.restype = ctypes.c_double
     lib.oracle_macroscopic_cell.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp]
@@ -153,7 +154,7 @@ class Oracle:
 
     def __init__(self, Q, grid, tau_f, tau_g, M, xi, sigma, rho_ratio=1.0, mu_ratio=1.0,
                  body_force=(0.0, 0.0, 0.0), courant=0.997, scheme=0, pis_sign=-1,
-                 half_force_sign=1, geq_source_tau=1):
+                 half_force_sign=1, geq_source_tau=1, walls=0):
         nx, ny, nz = grid
         self.Q, self.grid = Q, (nx, ny, nz)
         self.shape = (nz, ny, nx)
@@ -164,6 +165,8 @@ class Oracle:
                                     half_force_sign, geq_source_tau)
         if not self._h:
             raise ValueError("oracle_create rejected the arguments")
+        if lib.oracle_set_walls(self._h, int(walls)) != 0:
+            raise ValueError(f"invalid wall mask {walls}")
         self.tau_phi = float(lib.oracle_tau_phi(self._h))
 
     def close(self):

@@ -38,6 +38,13 @@
  *     g* = g^eq(phi0, u0, S0) - t_i (tau_phi - 1/2) e_i . grad phi0, with grad phi0 the
  *     isotropic central difference of phi0.
  *   - No clamping of phi anywhere.
+ *   - Walls (the paper gives no wall treatment; its Rayleigh-Taylor and rising-bubble runs have
+ *     walls): a wall lies half-way between the last cell and the next. Where the Lax-Wendroff
+ *     stencil of population i reaches across a wall, the value there is the opposite population
+ *     of the same cell, f_ibar(x) (half-way bounce-back written for the three-point stencil; at
+ *     c = 1 it is the usual bounce-back). The wall-face fluxes of i and ibar then cancel, so
+ *     sum phi is conserved. Gradients of phi (initialisation, finite-difference variant) read
+ *     the mirror image of the cell across the wall (zero normal gradient).
  */
 #include "lbm_oracle.h"
 
@@ -190,9 +197,38 @@ void oracle_forcing(int Q, double rho, const double *u, const double *grad_rho, 
 
 static long wrap(long a, long n) { return ((a % n) + n) % n; }
 
+static int opposite(const lattice *L, int i)
+{
+    int j;
+    for (j = 0; j < L->Q; ++j)
+        if (L->e[j][0] == -L->e[i][0] && L->e[j][1] == -L->e[i][1] && L->e[j][2] == -L->e[i][2]) return j;
+    return -1;
+}
+
+/* 1 if coordinate a (before wrapping) lies beyond a wall of its axis */
+static int beyond(int walls, int axis, long a, long n) { return ((walls >> axis) & 1) && (a < 0 || a >= n); }
+
+/* coordinate of the cell a step `a` lands on: periodic wrap, or the mirror image across a wall */
+static long land(int walls, int axis, long a, long n)
+{
+    if ((walls >> axis) & 1) {
+        if (a < 0) return -1 - a;
+        if (a >= n) return 2 * n - 1 - a;
+        return a;
+    }
+    return wrap(a, n);
+}
+
 /* grad phi(x) = sum_{i != 0} t_i e_i [phi(x + e_i) - phi(x - e_i)] / (2 cs^2): the isotropic
  * central difference of the finite-difference method the paper compares against (Sec. 3.4). */
+static void isotropic_gradient_walls(int Q, int nx, int ny, int nz, int walls, const double *field, double *grad);
+
 void oracle_isotropic_gradient(int Q, int nx, int ny, int nz, const double *field, double *grad)
+{
+    isotropic_gradient_walls(Q, nx, ny, nz, 0, field, grad);
+}
+
+static void isotropic_gradient_walls(int Q, int nx, int ny, int nz, int walls, const double *field, double *grad)
 {
     lattice L;
     long N = (long)nx * ny * nz;
@@ -206,8 +242,10 @@ void oracle_isotropic_gradient(int Q, int nx, int ny, int nz, const double *fiel
                 long c = (z * ny + y) * nx + x;
                 for (a = 0; a < 3; ++a) grad[a * N + c] = 0.0;
                 for (i = 1; i < L.Q; ++i) {
-                    long xp = wrap(x + L.e[i][0], nx), yp = wrap(y + L.e[i][1], ny), zp = wrap(z + L.e[i][2], nz);
-                    long xm = wrap(x - L.e[i][0], nx), ym = wrap(y - L.e[i][1], ny), zm = wrap(z - L.e[i][2], nz);
+                    long xp = land(walls, 0, x + L.e[i][0], nx), yp = land(walls, 1, y + L.e[i][1], ny);
+                    long zp = land(walls, 2, z + L.e[i][2], nz);
+                    long xm = land(walls, 0, x - L.e[i][0], nx), ym = land(walls, 1, y - L.e[i][1], ny);
+                    long zm = land(walls, 2, z - L.e[i][2], nz);
                     double diff = field[(zp * ny + yp) * nx + xp] - field[(zm * ny + ym) * nx + xm];
                     for (a = 0; a < 3; ++a) grad[a * N + c] += L.t[i] * L.e[i][a] * diff / (2.0 * CS2);
                 }
@@ -228,6 +266,7 @@ struct oracle {
     double c;
     int scheme;
     int pis_sign, half_force_sign, geq_source_tau;
+    int walls; /* bit 0: walls at x = -1/2 and nx - 1/2; bit 1: the same in y; bit 2: in z */
     int initialised;
     double *f, *g;   /* post-collision state f*, g*: [Q][N] */
     double *fn, *gn; /* next state */
@@ -289,6 +328,13 @@ void oracle_destroy(oracle *o)
 }
 
 double oracle_tau_phi(const oracle *o) { return o->tau_phi; }
+
+int oracle_set_walls(oracle *o, int walls)
+{
+    if (walls < 0 || walls > 7 || (o->L.Q == 9 && (walls & 4))) return -1;
+    o->walls = walls;
+    return 0;
+}
 
 void oracle_macroscopic_cell(const oracle *o, const double *fbar, const double *g,
                              const double *fd_grad, double *m)
@@ -386,12 +432,20 @@ static void propagate_cell(const oracle *o, const double *fs, const double *gs, 
     long c = (z * o->ny + y) * o->nx + x;
     int i;
     for (i = 0; i < L->Q; ++i) {
-        long xm = wrap(x - L->e[i][0], o->nx), ym = wrap(y - L->e[i][1], o->ny), zm = wrap(z - L->e[i][2], o->nz);
-        long xp = wrap(x + L->e[i][0], o->nx), yp = wrap(y + L->e[i][1], o->ny), zp = wrap(z + L->e[i][2], o->nz);
-        long cm = (zm * o->ny + ym) * o->nx + xm, cp = (zp * o->ny + yp) * o->nx + xp;
+        long xm = x - L->e[i][0], ym = y - L->e[i][1], zm = z - L->e[i][2];
+        long xp = x + L->e[i][0], yp = y + L->e[i][1], zp = z + L->e[i][2];
+        int wall_m = beyond(o->walls, 0, xm, o->nx) || beyond(o->walls, 1, ym, o->ny) || beyond(o->walls, 2, zm, o->nz);
+        int wall_p = beyond(o->walls, 0, xp, o->nx) || beyond(o->walls, 1, yp, o->ny) || beyond(o->walls, 2, zp, o->nz);
+        long cm = (wrap(zm, o->nz) * o->ny + wrap(ym, o->ny)) * o->nx + wrap(xm, o->nx);
+        long cp = (wrap(zp, o->nz) * o->ny + wrap(yp, o->ny)) * o->nx + wrap(xp, o->nx);
         const double *F = fs + (long)i * o->N, *G = gs + (long)i * o->N;
-        fbar[i] = oracle_lax_wendroff(o->c, F[cm], F[c], F[cp]);
-        g[i] = oracle_lax_wendroff(o->c, G[cm], G[c], G[cp]);
+        int ib = opposite(L, i);
+        const double *Fb = fs + (long)ib * o->N, *Gb = gs + (long)ib * o->N;
+        /* across a wall the stencil reads the opposite population of this cell */
+        double fm = wall_m ? Fb[c] : F[cm], fp = wall_p ? Fb[c] : F[cp];
+        double gm = wall_m ? Gb[c] : G[cm], gp = wall_p ? Gb[c] : G[cp];
+        fbar[i] = oracle_lax_wendroff(o->c, fm, F[c], fp);
+        g[i] = oracle_lax_wendroff(o->c, gm, G[c], gp);
     }
 }
 
@@ -411,7 +465,7 @@ static void fd_phi_pass(oracle *o)
                 o->phi[(z * o->ny + y) * o->nx + x] = phi;
             }
     }
-    oracle_isotropic_gradient(o->L.Q, o->nx, o->ny, o->nz, o->phi, o->grad);
+    isotropic_gradient_walls(o->L.Q, o->nx, o->ny, o->nz, o->walls, o->phi, o->grad);
 }
 
 int oracle_init_phi(oracle *o, const double *phi0, const double *u0, double p0)
@@ -419,7 +473,7 @@ int oracle_init_phi(oracle *o, const double *phi0, const double *u0, double p0)
     const lattice *L = &o->L;
     long c;
     double *grad = o->grad;
-    oracle_isotropic_gradient(L->Q, o->nx, o->ny, o->nz, phi0, grad);
+    isotropic_gradient_walls(L->Q, o->nx, o->ny, o->nz, o->walls, phi0, grad);
 #pragma omp parallel for schedule(static)
     for (c = 0; c < o->N; ++c) {
         double gphi[3], n[3], S[3], u[3], pis[9], feq[19], geq[19];

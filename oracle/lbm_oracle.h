@@ -61,6 +61,11 @@ oracle *oracle_create(int Q, int nx, int ny, int nz, double tau_f, double tau_g,
 void oracle_destroy(oracle *o);
 double oracle_tau_phi(const oracle *o);
 
+/* Walls (bit 0: x, bit 1: y, bit 2: z), half-way between the last cell and the next:
+ * bounce-back in the Lax-Wendroff stencil, mirror image for gradients of phi. Returns -1 for
+ * an invalid mask. Default 0 (fully periodic). */
+int oracle_set_walls(oracle *o, int walls);
+
 /* Macroscopic stage of one cell from its propagated populations fbar, g.
  * fd_grad = NULL selects the moment-based gradient. out receives, packed:
  * phi, rho, u[3], K1[3], n[3], S[3], grad_phi[3], grad_rho[3], p  (21 doubles). */

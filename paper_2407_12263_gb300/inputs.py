@@ -25,6 +25,19 @@ WORKLOADS = {
 }
 
 
+def _rayleigh_taylor(grid, Re=256.0, At=0.5, U=0.04, Ca=1.0, xi=4.0, M=0.02, steps=3600):
+    """Single-mode Rayleigh-Taylor box (heavy fluid 1 on top, walls in z): lattice parameters
+    from the dimensionless groups. Width W = nx, U = sqrt(g W), Re = rho1 U W / eta1,
+    At = (rho1 - rho2)/(rho1 + rho2), Ca = eta1 U / sigma, viscosity ratio 1."""
+    W = grid[0]
+    rho1 = (1.0 + At) / (1.0 - At)          # rho2 = 1
+    g = U * U / W
+    eta1 = rho1 * U * W / Re
+    return dict(Q=19, grid=grid, xi=xi, sigma=eta1 * U / Ca, tau_f=eta1 / (1.0 / 3.0), tau_g=0.8, M=M,
+                rho_ratio=rho1, mu_ratio=1.0, body_force=(0.0, 0.0, -g), walls=4, amplitude=0.05 * W,
+                steps=steps, time_scale=W / U)
+
+
 def cell_coords(grid):
     """Integer cell-centre coordinates (x, y, z) broadcast to (nz, ny, nx)."""
     nx, ny, nz = grid
@@ -65,6 +78,31 @@ def slab_phi(grid, half_width, xi, axis=0, centre=None):
     d = np.abs(coords - centre)
     d = np.minimum(d, n - d)
     return 0.5 * (1.0 + np.tanh(2.0 * (d - half_width) / xi))
+
+
+# Rayleigh-Taylor: 128 x 128 x 512 with walls in z, At = 0.5 (density ratio 3), Re = 256,
+# U = sqrt(g W) = 0.04, cosine perturbation of amplitude 0.05 W; Ca = 1 (the workload gives none:
+# at Ca = 0.1 surface tension makes the single mode stable at this Re), and a 32 x 32 x 128 copy
+# with the same dimensionless groups.
+WORKLOADS["rayleigh_taylor_128x128x512"] = _rayleigh_taylor((128, 128, 512))
+WORKLOADS["rayleigh_taylor_32x32x128"] = _rayleigh_taylor((32, 32, 128))
+
+
+def rayleigh_taylor_phi(grid, amplitude, xi):
+    """Heavy fluid (phi = 1) above the plane z = (nz - 1)/2 + A cos(2 pi (x + 1/2)/nx) cos(2 pi (y + 1/2)/ny)."""
+    nx, ny, nz = grid
+    x, y, z = cell_coords(grid)
+    zi = (nz - 1) / 2.0 + amplitude * np.cos(2 * np.pi * (x + 0.5) / nx) * np.cos(2 * np.pi * (y + 0.5) / ny)
+    return 0.5 * (1.0 + np.tanh(2.0 * (z - zi) / xi))
+
+
+def interface_height(phi_column):
+    """Height where a column of phi (bottom to top, rising from 0 to 1) crosses 1/2."""
+    c = np.asarray(phi_column, dtype=np.float64)
+    k = int(np.argmax(c >= 0.5))
+    if k == 0:
+        return float("nan")
+    return (k - 1) + (0.5 - c[k - 1]) / (c[k] - c[k - 1])
 
 
 def droplet_workload_phi(name):
