@@ -69,7 +69,11 @@ typedef struct {
     int scheme;     /* enum lbm_scheme; default difference-free */
     int storage;    /* enum lbm_storage; default FP32. Arithmetic is FP32 in every case */
     double courant; /* Lax-Wendroff Courant number c, 0 < c <= 1; default 0.997 (Sec. 2.2) */
-    int walls;      /* 0 = fully periodic (the only boundary built) */
+    int walls;      /* mask of walled axes: 1 = x, 2 = y, 4 = z (D3Q19 only); 0 = fully periodic.
+                       A wall lies half-way beyond the first and last cell of its axis:
+                       half-way bounce-back in the Lax-Wendroff stencil (sum phi conserved),
+                       zero normal gradient of phi for the initial and finite-difference
+                       gradients */
     void *stream;   /* cudaStream_t the handle launches on; NULL = a stream the handle owns */
     int graph_steps; /* lbm_step replays CUDA graphs of this many steps (even, >= 2; default 32);
                         0 launches every step directly. Steps run inside a caller's own stream
@@ -104,7 +108,9 @@ int lbm_create(lbm_ctx **out, const int grid[3], int lattice, double tau_f, doub
  * (3 host planes, NULL = rest) and a uniform pressure p0 > 0. Builds the post-collision
  * populations f* = f^eq(p0, u0, rho(phi0), Pi_s) (Eq. geq_s) and
  * g* = g^eq(phi0, u0, S0) - t_i (tau_phi - 1/2) e_i . grad phi0 (Eq. geq), with grad phi0
- * the isotropic central difference of phi0 and n0 = grad phi0 / |grad phi0|. Synchronous.
+ * the isotropic central difference of phi0 and n0 = grad phi0 / |grad phi0|. Every phi0 value
+ * must lie in [-1, 1.5] (LBM_EINVAL otherwise): the handle holds phi as a fixed-point number
+ * with range [-2, 2) and resolution 2^-30. Synchronous.
  */
 int lbm_init_phi(lbm_ctx *ctx, const double *phi0, const double *u0, double p0);
 
@@ -129,14 +135,17 @@ int lbm_gradients(lbm_ctx *ctx, double *grad_phi, double *normal);
 
 /*
  * Global sums over the propagated current state: sum phi and sum rho phi (the mass
- * m = sum rho phi dx^3 of Sec. 3.3), accumulated in FP64 on the device. Also scans every
- * stored population and returns LBM_ENONFINITE if one is not finite. Synchronous.
+ * m = sum rho phi dx^3 of Sec. 3.3). sum phi is the exact sum of the fixed-point phi values
+ * (a 64-bit integer sum; the time step conserves it bit for bit, walls included); sum rho phi
+ * accumulates in FP64. Also scans every stored population and returns LBM_ENONFINITE if one
+ * is not finite. Synchronous.
  */
 int lbm_mass(lbm_ctx *ctx, double *sum_phi, double *sum_rho_phi);
 
 /* Copy the post-collision populations f*, g* to / from host FP64 arrays (Q planes each;
  * either pointer of lbm_get_pops may be NULL). lbm_set_pops also marks the state
- * initialised. Synchronous. */
+ * initialised; sum_i g_i must lie in [-1, 1.5] in every cell (LBM_EINVAL otherwise), and is
+ * rounded to the fixed-point grid of phi (2^-30). Synchronous. */
 int lbm_get_pops(lbm_ctx *ctx, double *f, double *g);
 int lbm_set_pops(lbm_ctx *ctx, const double *f, const double *g);
 

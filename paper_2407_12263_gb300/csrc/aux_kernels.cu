@@ -30,8 +30,10 @@ __global__ void init_kernel(const Params P, int z0, const double* __restrict__ p
     double gx = 0.0, gy = 0.0, gz = 0.0;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-        const int xx = (x + Lat<Q>::cx(i) + P.nx) % P.nx;
-        const int yy = (y + Lat<Q>::cy(i) + P.ny) % P.ny;
+        int xx = x + Lat<Q>::cx(i), yy = y + Lat<Q>::cy(i);
+        // across a wall: the mirror image of this cell (zero normal gradient); else periodic
+        xx = (P.walls & 1) ? min(max(xx, 0), P.nx - 1) : (xx + P.nx) % P.nx;
+        yy = (P.walls & 2) ? min(max(yy, 0), P.ny - 1) : (yy + P.ny) % P.ny;
         const int ll = (zl + 1 + Lat<Q>::cz(i)) * P.nxy + yy * P.nx + xx;
         const double v = Lat<Q>::wd(i) * phi0s[ll];
         gx += Lat<Q>::cx(i) * v;
@@ -73,7 +75,8 @@ __global__ void init_kernel(const Params P, int z0, const double* __restrict__ p
         if (i > 0)
             Store<S>::store(moving_plane<S>(fg, P.N, i) + c, (float)(fstar - t * P.w0d), (float)(gstar - t * P.phi_ref_d), P);
     }
-    moment_plane(fg)[c] = make_float2((float)(fsum - P.w0d), (float)(gsum - P.phi_ref_d));  // plane 0: zeroth moments
+    // plane 0: the zeroth moments, sum f - w0 (FP32) and phi as the integer phi * 2^30
+    moment_plane(fg)[c] = make_float2((float)(fsum - P.w0d), __int_as_float((int)llrint(gsum * kPhiFx)));
 }
 
 cudaError_t launch_init(const Params& P, int z0, int nzs, const double* phi0s, const double* u0s,
@@ -107,21 +110,23 @@ __global__ void moments_kernel(const Params P, int z0, const void* __restrict__ 
     const int z = z0 + zl;
     const Nbr nb = make_nbr(P, x, y, z);
     const int c = (z * P.ny + y) * P.nx + x;
+    const WallSide ws = GEN ? make_wall_side(P, x, y, z) : WallSide{};
     float fb[Q], gb[Q];
-    pull<Q, true, S>(P, fg, c, nb, fb, gb);
+    int phi_fx;
+    pull<Q, true, S, GEN>(P, fg, c, nb, fb, gb, phi_fx, ws);
     Macro m;
     macro_flow<Q, GEN>(P, fb, gb, m);
     if (SCHEME == SCHEME_DF) {
         macro_interface_df<Q>(P, gb, m);
     } else {
         float gx, gy, gz;
-        fd_gradient<Q>(phi_fd, c, nb, gx, gy, gz);
+        fd_gradient<Q>(phi_fd, c, GEN ? mirror_at_walls(nb, ws) : nb, gx, gy, gz);
         macro_interface_fd(P, gx, gy, gz, m);
     }
     macro_pressure<GEN>(P, m);
     const size_t slab = (size_t)gridDim.z * P.nxy;
     const size_t l = (size_t)zl * P.nxy + (size_t)y * P.nx + x;
-    if (mask & 1) out[l] = P.phi_ref_d + (double)m.Phi;
+    if (mask & 1) out[l] = (double)phi_fx / kPhiFx;
     if (mask & 2) out[slab + l] = (P.w0d + (double)m.P) / 3.0;  // p = cs^2 (w0 + P)
     for (int a = 0; a < 3; ++a) {
         if (mask & 4) out[(2 + a) * slab + l] = (double)m.u[a];
@@ -159,42 +164,48 @@ cudaError_t launch_moments(const Params& P, int scheme, int z0, int nzs, const v
 }
 
 // ---------------------------------------------------------------------------------------
-// Mass: sum phi and sum rho phi over the propagated state, FP64 accumulation, plus a count of
-// non-finite stored populations. Grid-stride per thread, warp shuffle, shared memory per block,
-// one partial triple per block; a single block then sums the partials in a fixed order, so the
-// result does not depend on scheduling.
+// Mass: sum phi and sum rho phi over the propagated state, plus a count of non-finite stored
+// populations. sum phi is the exact integer sum of the fixed-point phi values (64-bit), so it
+// reports conservation bit for bit; the other two accumulate in FP64. Grid-stride per thread,
+// warp shuffle, shared memory per block, one partial triple per block (the integer held in the
+// bits of the first double); a single block then sums the partials in a fixed order.
 // ---------------------------------------------------------------------------------------
 constexpr int kRedThreads = 256;
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return v;
 }
 
-__device__ __forceinline__ void block_sum3(double (&v)[3], double* out) {
-    __shared__ double red[3][kRedThreads / 32];
+// Block totals of s and v[0..1]; valid in thread 0.
+__device__ __forceinline__ void block_sum(long long& s, double (&v)[2]) {
+    __shared__ long long rs[kRedThreads / 32];
+    __shared__ double rv[2][kRedThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        v[k] = warp_sum(v[k]);
-        if (lane == 0) red[k][warp] = v[k];
+    s = warp_sum(s);
+    v[0] = warp_sum(v[0]);
+    v[1] = warp_sum(v[1]);
+    if (lane == 0) {
+        rs[warp] = s;
+        rv[0][warp] = v[0];
+        rv[1][warp] = v[1];
     }
     __syncthreads();
     if (warp == 0) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            double w = (lane < kRedThreads / 32) ? red[k][lane] : 0.0;
-            w = warp_sum(w);
-            if (lane == 0) out[k] = w;
-        }
+        const bool in = lane < kRedThreads / 32;
+        s = warp_sum(in ? rs[lane] : 0ll);
+        v[0] = warp_sum(in ? rv[0][lane] : 0.0);
+        v[1] = warp_sum(in ? rv[1][lane] : 0.0);
     }
 }
 
 template <int Q, int S>
 __global__ void __launch_bounds__(kRedThreads)
 mass_kernel(const Params P, const void* __restrict__ fg, double* __restrict__ partials) {
-    double acc[3] = {0.0, 0.0, 0.0};
+    long long phi_sum = 0;
+    double acc[2] = {0.0, 0.0};
     for (long long c = (long long)blockIdx.x * kRedThreads + threadIdx.x; c < P.N;
          c += (long long)gridDim.x * kRedThreads) {
         const int z = (int)(c / P.nxy);
@@ -202,27 +213,44 @@ mass_kernel(const Params P, const void* __restrict__ fg, double* __restrict__ pa
         const int y = r / P.nx, x = r - y * P.nx;
         const Nbr nb = make_nbr(P, x, y, z);
         float fb[Q], gb[Q];
-        pull<Q, false, S>(P, fg, (int)c, nb, fb, gb);
-        const double phi = P.phi_ref_d + (double)gb[0];
-        acc[0] += phi;
-        acc[1] += (P.rho2_d + P.drho_d * phi) * phi;
+        int phi_fx;
+        pull<Q, false, S, true>(P, fg, (int)c, nb, fb, gb, phi_fx, make_wall_side(P, x, y, z));
+        const double phi = (double)phi_fx / kPhiFx;
+        phi_sum += phi_fx;
+        acc[0] += (P.rho2_d + P.drho_d * phi) * phi;
         int bad = 0;
+        const float2 m0 = __ldg(moment_plane(fg) + c);
+        bad += !isfinite(m0.x);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const float2 v = (i == 0) ? __ldg(moment_plane(fg) + c) : Store<S>::load(moving_plane<S>(fg, P.N, i) + c, P);
+        for (int i = 1; i < Q; ++i) {
+            const float2 v = Store<S>::load(moving_plane<S>(fg, P.N, i) + c, P);
             bad += !isfinite(v.x) + !isfinite(v.y);
         }
-        acc[2] += (double)bad;
+        acc[1] += (double)bad;
     }
-    block_sum3(acc, partials + 3 * blockIdx.x);
+    block_sum(phi_sum, acc);
+    if (threadIdx.x == 0) {
+        partials[3 * blockIdx.x] = __longlong_as_double(phi_sum);
+        partials[3 * blockIdx.x + 1] = acc[0];
+        partials[3 * blockIdx.x + 2] = acc[1];
+    }
 }
 
 __global__ void __launch_bounds__(kRedThreads)
 mass_finish(const double* __restrict__ partials, int n, double* __restrict__ result) {
-    double acc[3] = {0.0, 0.0, 0.0};
-    for (int b = threadIdx.x; b < n; b += kRedThreads)
-        for (int k = 0; k < 3; ++k) acc[k] += partials[3 * b + k];
-    block_sum3(acc, result);
+    long long phi_sum = 0;
+    double acc[2] = {0.0, 0.0};
+    for (int b = threadIdx.x; b < n; b += kRedThreads) {
+        phi_sum += __double_as_longlong(partials[3 * b]);
+        acc[0] += partials[3 * b + 1];
+        acc[1] += partials[3 * b + 2];
+    }
+    block_sum(phi_sum, acc);
+    if (threadIdx.x == 0) {
+        result[0] = (double)phi_sum / kPhiFx;
+        result[1] = acc[0];
+        result[2] = acc[1];
+    }
 }
 
 int mass_partials_needed(const Params& P) {
@@ -249,7 +277,8 @@ cudaError_t launch_mass(const Params& P, const void* fg, double* partials, int n
 
 // ---------------------------------------------------------------------------------------
 // Device storage <-> plain FP64 populations, all Q planes of a slab (staging [Q][nzs * nxy]).
-// Plane i >= 1: v_i + t_i ref; plane 0: the rest population (ref + v_0) - sum_{i>=1} f_i.
+// Plane i >= 1: v_i + t_i ref; plane 0: the rest population, the zeroth moment held in plane 0
+// (w0 + v_0 for f, phi_fx / 2^30 for g) minus sum_{i>=1} of the set.
 // Writing one set (f or g) re-encodes the other member of each stored pair unchanged: decoding
 // and re-encoding a stored FP32, scaled FP16 or BF16 value returns the same bits.
 // ---------------------------------------------------------------------------------------
@@ -260,7 +289,7 @@ __global__ void pops_to_f64(const Params P, const void* __restrict__ src, int is
     const double ref = is_f ? P.w0d : P.phi_ref_d;
     for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (size_t)gridDim.x * blockDim.x) {
         const float2 m0 = moment_plane(src)[base + l];
-        double rest = ref + (double)(is_f ? m0.x : m0.y);
+        double rest = is_f ? ref + (double)m0.x : (double)__float_as_int(m0.y) / kPhiFx;
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
             const float2 p = Store<S>::load(moving_plane<S>(src, P.N, i) + base + l, P);
@@ -292,7 +321,7 @@ __global__ void pops_from_f64(const Params P, const double* __restrict__ src, in
         }
         float2* m0 = moment_plane(dst) + base + l;
         if (is_f) m0->x = (float)(sum - ref);
-        else m0->y = (float)(sum - ref);
+        else m0->y = __int_as_float((int)llrint(sum * kPhiFx));  // |sum| < 2 checked by the host
     }
 }
 

@@ -1,20 +1,20 @@
 // cell.cuh -- per-cell device code of the difference-free conservative phase-field LBM
 // (Zhao, Patel & Lee, arXiv:2407.12263): Lax-Wendroff pull, macroscopic stage, collisions.
 //
-// Storage (Q planes of N FP32 pairs (f, g)). Plane i >= 1 holds the populations shifted by their lattice
-// weight times a reference level, f_i - t_i w0 (w0 = p0 / cs^2) and g_i - t_i phi_ref
+// Storage (Q planes of N (f, g) pairs). Plane i >= 1 holds the populations shifted by their
+// lattice weight times a reference level, f_i - t_i w0 (w0 = p0 / cs^2) and g_i - t_i phi_ref
 // (phi_ref = 0 or 1, the bulk phase that fills most of the grid). Plane 0 holds the zeroth
-// moment of the shifted set, sum_i f_i - w0 and phi - phi_ref, in place of the rest
-// population, which it fixes exactly (f_0 = sum_i f_i - sum_{i>=1} f_i). Both choices are
+// moments, sum_i f_i - w0 (FP32) and phi (the 32-bit fixed-point integer phi * 2^30), in place
+// of the rest populations, which they fix exactly (f_0 = sum_i f_i - sum_{i>=1} f_i). These are
 // exact changes of variables:
 //  * propagation and collision are linear with weights summing to one, so the shift passes
 //    through them, and every FP32 value is a deviation instead of a number of order t_i;
 //  * the rest population does not move and the collision conserves the zeroth moment, so
 //    phi_new(x) = phi*(x) + sum_{i>=1} [LW(g*_i)(x) - g*_i(x)] and the collision leaves it alone.
-//    In FP32 this removes the per-step bias that rounding t_i-weighted sums would add to phi
-//    in every cell, and a uniform region is an exact fixed point of the update.
-// The Lax-Wendroff update is evaluated in difference form for the same reason: it returns a
-// uniform field unchanged bit for bit. All arithmetic is FP32 with constants folded
+//    Held as an integer and advanced by integer face fluxes (see pull), sum phi is conserved
+//    exactly, and no per-step rounding bias enters phi in any cell.
+// The Lax-Wendroff update of the moving populations is evaluated in difference form: it
+// returns a uniform field unchanged bit for bit. All arithmetic is FP32 with constants folded
 // (1/cs^2 = 3, 1/(2 cs^4) = 4.5).
 #pragma once
 
@@ -42,6 +42,43 @@ __device__ __forceinline__ Nbr make_nbr(const Params& P, int x, int y, int z) {
     return n;
 }
 
+// Cells on a wall side (walls lie half-way between the last cell and the next).
+struct WallSide {
+    bool xlo, xhi, ylo, yhi, zlo, zhi;
+};
+
+__device__ __forceinline__ WallSide make_wall_side(const Params& P, int x, int y, int z) {
+    WallSide w;
+    w.xlo = (P.walls & 1) && x == 0;
+    w.xhi = (P.walls & 1) && x == P.nx - 1;
+    w.ylo = (P.walls & 2) && y == 0;
+    w.yhi = (P.walls & 2) && y == P.ny - 1;
+    w.zlo = (P.walls & 4) && z == 0;
+    w.zhi = (P.walls & 4) && z == P.nz - 1;
+    return w;
+}
+
+// Whether x + s e_i lies beyond a wall.
+template <int Q>
+__device__ __forceinline__ bool crosses_wall(const WallSide& w, int i, int s) {
+    const int ex = s * Lat<Q>::cx(i), ey = s * Lat<Q>::cy(i), ez = s * Lat<Q>::cz(i);
+    return (ex < 0 && w.xlo) || (ex > 0 && w.xhi) || (ey < 0 && w.ylo) || (ey > 0 && w.yhi) || (ez < 0 && w.zlo) ||
+           (ez > 0 && w.zhi);
+}
+
+// Offsets for gradients of phi with walls: across a wall the stencil reads the mirror image
+// of the cell, i.e. the same index along that axis (zero normal gradient).
+__device__ __forceinline__ Nbr mirror_at_walls(const Nbr& n, const WallSide& w) {
+    Nbr m = n;
+    if (w.xlo) m.xm = 0;
+    if (w.xhi) m.xp = 0;
+    if (w.ylo) m.ym = 0;
+    if (w.yhi) m.yp = 0;
+    if (w.zlo) m.zm = 0;
+    if (w.zhi) m.zp = 0;
+    return m;
+}
+
 // Offset of the cell x + s e_i (s = +1 or -1). Folds to two or three adds once unrolled.
 template <int Q>
 __device__ __forceinline__ int link_offset(const Nbr& n, int i, int s) {
@@ -54,28 +91,65 @@ __device__ __forceinline__ int link_offset(const Nbr& n, int i, int s) {
 //   fbar_i(x) = f*_i(x) - c [f*_i(x) - f*_i(x - e_i)] - c(1-c)/2 [f*_i(x + e_i) - 2 f*_i(x) + f*_i(x - e_i)]
 //             = f*_i(x) + lw_m [f*_i(x - e_i) - f*_i(x)] + lw_p [f*_i(x + e_i) - f*_i(x)],
 // the same for g, and the zeroth moments fb[0] = sum fbar - w0, gb[0] = phi - phi_ref of the
-// propagated state. Each load brings the (f_i, g_i) pair of one cell.
-template <int Q, bool WITH_F, int S>
+// propagated state. Each load brings the (f_i, g_i) pair of one cell. With WALLS, a stencil
+// point beyond a wall reads the opposite pair of this cell instead (half-way bounce-back; at
+// c = 1 it is the usual bounce-back).
+//
+// phi itself advances in flux form: the same update reads
+//   gbar_i(x) = g*_i(x) + F_i(x - e_i/2) - F_i(x + e_i/2),  F_i = lw_m g*_i(upwind) - lw_p g*_i(downwind),
+// so phi_fx (phi * 2^30, the fixed-point plane-0 value) loses, across each face x + e_i/2, the
+// net outflow of the pair (i, j = opposite of i) that crosses it,
+//   N = F_i - F_j = lw_m [g*_i(x) - g*_j(x + e_i)] - lw_p [g*_i(x + e_i) - g*_j(x)],
+// rounded to an integer. The cell on the other side evaluates the same expression with every
+// difference negated; IEEE subtraction, products and round-to-nearest are odd in sign, so it
+// gets -N bit for bit, the integers cancel in pairs and sum phi over the grid never changes.
+// At a wall the two terms of N read the same values of this cell, so N = 0 exactly.
+template <int Q, int S, bool WALLS>
+__device__ __forceinline__ void load_link(const Params& P, const void* __restrict__ state, int c, const Nbr& nb,
+                                          const WallSide& ws, int i, float2& vm, float2& v0, float2& vp) {
+    const typename Store<S>::T* q = moving_plane<S>(state, P.N, i);
+    const typename Store<S>::T* pm = q + c + link_offset<Q>(nb, i, -1);
+    const typename Store<S>::T* pp = q + c + link_offset<Q>(nb, i, +1);
+    if (WALLS) {
+        const typename Store<S>::T* back = moving_plane<S>(state, P.N, Lat<Q>::opp(i)) + c;
+        if (crosses_wall<Q>(ws, i, -1)) pm = back;
+        if (crosses_wall<Q>(ws, i, +1)) pp = back;
+    }
+    v0 = Store<S>::load_raw(q + c);
+    vm = Store<S>::load_raw(pm);
+    vp = Store<S>::load_raw(pp);
+}
+
+template <int Q, bool WITH_F, int S, bool WALLS = false>
 __device__ __forceinline__ void pull(const Params& P, const void* __restrict__ state, int c, const Nbr& nb,
-                                     float (&fb)[Q], float (&gb)[Q]) {
-    float df = 0.f, dg = 0.f;  // increments in storage units
+                                     float (&fb)[Q], float (&gb)[Q], int& phi_fx,
+                                     const WallSide& ws = WallSide{}) {
+    float df = 0.f;                 // increment of sum f, storage units
+    unsigned int dphi = 0u;         // increment of phi_fx (wraps; the true sum fits in 32 bits)
+    const float fa = P.flux_a * Store<S>::kInvG, fbk = P.flux_b * Store<S>::kInvG;
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-        const typename Store<S>::T* q = moving_plane<S>(state, P.N, i);
-        const float2 v0 = Store<S>::load_raw(q + c);
-        const float2 vm = Store<S>::load_raw(q + c + link_offset<Q>(nb, i, -1));
-        const float2 vp = Store<S>::load_raw(q + c + link_offset<Q>(nb, i, +1));
-        const float d = P.lw_m * (vm.y - v0.y) + P.lw_p * (vp.y - v0.y);
-        gb[i] = (v0.y + d) * Store<S>::kInvG;
-        dg += d;
+    for (int k = 0; k < Lat<Q>::kPairs; ++k) {
+        const int i = Lat<Q>::pair_first(k), j = Lat<Q>::pair_second(k);
+        float2 vmi, v0i, vpi, vmj, v0j, vpj;
+        load_link<Q, S, WALLS>(P, state, c, nb, ws, i, vmi, v0i, vpi);
+        load_link<Q, S, WALLS>(P, state, c, nb, ws, j, vmj, v0j, vpj);
+        gb[i] = (v0i.y + (P.lw_m * (vmi.y - v0i.y) + P.lw_p * (vpi.y - v0i.y))) * Store<S>::kInvG;
+        gb[j] = (v0j.y + (P.lw_m * (vmj.y - v0j.y) + P.lw_p * (vpj.y - v0j.y))) * Store<S>::kInvG;
+        // net outflow of phi across x + e_i/2 and across x - e_i/2 (= x + e_j/2)
+        const int out_i = __float2int_rn(__fmaf_rn(fa, __fsub_rn(v0i.y, vmj.y), __fmul_rn(fbk, __fsub_rn(vpi.y, v0j.y))));
+        const int out_j = __float2int_rn(__fmaf_rn(fa, __fsub_rn(v0j.y, vmi.y), __fmul_rn(fbk, __fsub_rn(vpj.y, v0i.y))));
+        dphi -= (unsigned int)out_i + (unsigned int)out_j;
         if (WITH_F) {
-            const float e = P.lw_m * (vm.x - v0.x) + P.lw_p * (vp.x - v0.x);
-            fb[i] = (v0.x + e) * Store<S>::kInvF;
-            df += e;
+            const float ei = P.lw_m * (vmi.x - v0i.x) + P.lw_p * (vpi.x - v0i.x);
+            const float ej = P.lw_m * (vmj.x - v0j.x) + P.lw_p * (vpj.x - v0j.x);
+            fb[i] = (v0i.x + ei) * Store<S>::kInvF;
+            fb[j] = (v0j.x + ej) * Store<S>::kInvF;
+            df += ei + ej;
         }
     }
     const float2 m0 = __ldg(moment_plane(state) + c);
-    gb[0] = m0.y + dg * Store<S>::kInvG;
+    phi_fx = (int)((unsigned int)__float_as_int(m0.y) + dphi);
+    gb[0] = __int2float_rn((int)((unsigned int)phi_fx - (unsigned int)P.phi_ref_fx)) * kPhiFxInvF;
     if (WITH_F) fb[0] = m0.x + df * Store<S>::kInvF;
 }
 
@@ -278,8 +352,7 @@ __device__ __forceinline__ void collide(const Params& P, const Macro& m, float (
         gb[i] = gb[i] - omega_g * (gb[i] - (ge + go));
         gb[j] = gb[j] - omega_g * (gb[j] - (ge - go));
     }
-    gb[0] = m.Phi;
-    fb[0] = GEN ? m.Pbar + ugr : m.Pbar;
+    fb[0] = GEN ? m.Pbar + ugr : m.Pbar;  // plane 0 keeps phi_fx: the collision conserves phi
 }
 
 }  // namespace lbm

@@ -33,6 +33,7 @@ struct Lat<9> {
     static constexpr int kPairs = 4;
     __host__ __device__ static constexpr int pair_first(int k) { return k < 2 ? 1 + k : 5 + (k - 2); }
     __host__ __device__ static constexpr int pair_second(int k) { return pair_first(k) + 2; }
+    __host__ __device__ static constexpr int opp(int i) { return i == 0 ? 0 : (i == 1 || i == 2 || i == 5 || i == 6) ? i + 2 : i - 2; }
 };
 
 template <>
@@ -63,6 +64,7 @@ struct Lat<19> {
     static constexpr int kPairs = 9;
     __host__ __device__ static constexpr int pair_first(int k) { return 2 * k + 1; }
     __host__ __device__ static constexpr int pair_second(int k) { return 2 * k + 2; }
+    __host__ __device__ static constexpr int opp(int i) { return i == 0 ? 0 : (i & 1) ? i + 1 : i - 1; }
 };
 
 }  // namespace lbm

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <new>
 
 #include "../../include/lbm.h"
@@ -42,6 +43,9 @@ struct lbm_ctx {
 namespace {
 
 constexpr size_t kStagingCap = size_t(32) << 20;  // doubles (256 MB) per staging slab at most
+// phi is held as the fixed-point integer phi * 2^30 (range [-2, 2)); initial and restored
+// states must leave room for the overshoot of a running interface.
+constexpr double kPhiMin = -1.0, kPhiMax = 1.5;
 
 thread_local char g_create_error[512] = "no error";
 
@@ -182,7 +186,9 @@ int lbm_create(lbm_ctx** out, const int grid[3], int lattice, double tau_f, doub
         return set_error(nullptr, LBM_EINVAL, "unknown scheme %d", o.scheme);
     if (o.storage < 0 || o.storage > 2)
         return set_error(nullptr, LBM_EINVAL, "storage must be 0 (FP32), 1 (FP16) or 2 (BF16), got %d", o.storage);
-    if (o.walls != 0) return set_error(nullptr, LBM_EINVAL, "walls %d are not built (0 = periodic)", o.walls);
+    if (o.walls < 0 || o.walls > 7 || (lattice == LBM_D2Q9 && (o.walls & 4)))
+        return set_error(nullptr, LBM_EINVAL, "walls must be a mask of 1 (x), 2 (y), 4 (z, D3Q19 only); got %d",
+                         o.walls);
     if (!(o.courant > 0 && o.courant <= 1)) return set_error(nullptr, LBM_EINVAL, "courant must be in (0, 1]");
     if (o.graph_steps < 0 || o.graph_steps == 1 || (o.graph_steps & 1))
         return set_error(nullptr, LBM_EINVAL, "graph_steps must be 0 or an even count >= 2 (got %d)", o.graph_steps);
@@ -212,6 +218,8 @@ int lbm_create(lbm_ctx** out, const int grid[3], int lattice, double tau_f, doub
     P.N = N;
     P.lw_m = (float)(0.5 * cc * (1.0 + cc));   // c - c(1-c)/2: weight of f*(x - e) - f*(x)
     P.lw_p = (float)(-0.5 * cc * (1.0 - cc));  // -c(1-c)/2:    weight of f*(x + e) - f*(x)
+    P.flux_a = (float)(0.5 * cc * (1.0 + cc) * 1073741824.0);  // face-flux weights times 2^30
+    P.flux_b = (float)(0.5 * cc * (1.0 - cc) * 1073741824.0);
     P.tau_phi = (float)tau_phi;
     P.omega_g = (float)(1.0 / (tau_phi + 0.5));
     P.grad_s = (float)(tau_phi / (tau_phi + 0.5));
@@ -226,7 +234,9 @@ int lbm_create(lbm_ctx** out, const int grid[3], int lattice, double tau_f, doub
     for (int a = 0; a < 3; ++a) P.G[a] = (float)G[a];
     P.w0 = 1.0f;       // p0 = cs^2 until lbm_init_phi sets it
     P.phi_ref = 1.0f;  // until lbm_init_phi picks the bulk phase of phi0
-    P.general = (rho_ratio != 1.0 || mu_ratio != 1.0 || G[0] != 0 || G[1] != 0 || G[2] != 0) ? 1 : 0;
+    P.phi_ref_fx = 1 << 30;
+    P.walls = o.walls;
+    P.general = (rho_ratio != 1.0 || mu_ratio != 1.0 || G[0] != 0 || G[1] != 0 || G[2] != 0 || o.walls) ? 1 : 0;
     P.storage = o.storage;
     // FP16 storage: f deviations scaled by 2^12 and g deviations by 2^10 (exact power-of-two
     // scaling) so that they sit in the normal FP16 range; 1 for FP32 and BF16
@@ -291,11 +301,15 @@ int lbm_init_phi(lbm_ctx* c, const double* phi0, const double* u0, double p0) {
     P.w0 = (float)P.w0d;
     // g is stored as the deviation from the bulk phase (phi = 0 or 1) that covers most cells
     double mean = 0.0;
-    for (long long k = 0; k < P.N; ++k) mean += phi0[k];
+    for (long long k = 0; k < P.N; ++k) {
+        if (!(phi0[k] >= kPhiMin && phi0[k] <= kPhiMax))
+            return set_error(c, LBM_EINVAL, "phi0[%lld] = %g outside [%g, %g]", k, phi0[k], kPhiMin, kPhiMax);
+        mean += phi0[k];
+    }
     mean /= (double)P.N;
-    if (!is_fin(mean)) return set_error(c, LBM_EINVAL, "phi0 is not finite");
     P.phi_ref_d = (mean >= 0.5) ? 1.0 : 0.0;
     P.phi_ref = (float)P.phi_ref_d;
+    P.phi_ref_fx = (mean >= 0.5) ? (1 << 30) : 0;
     drop_graphs(c);  // captured steps carry the old parameters
     const size_t nxy = (size_t)P.nxy;
     const int per_z = 1 + (u0 ? 3 : 0);
@@ -309,7 +323,8 @@ int lbm_init_phi(lbm_ctx* c, const double* phi0, const double* u0, double p0) {
         // phi0 planes z0-1 .. z0+n (periodic images at the ends); D2Q9 has only its one plane
         const int lo = (P.Q == 9) ? 0 : -1, hi = (P.Q == 9) ? n - 1 : n;
         for (int l = lo; l <= hi; ++l) {
-            const int z = ((z0 + l) % P.nz + P.nz) % P.nz;
+            // periodic image, or across a z wall the mirror image (zero normal gradient)
+            const int z = (P.walls & 4) ? std::min(std::max(z0 + l, 0), P.nz - 1) : ((z0 + l) % P.nz + P.nz) % P.nz;
             LBM_CUDA(c, cudaMemcpyAsync(phis + (size_t)(l + 1) * nxy, phi0 + (size_t)z * nxy, nxy * sizeof(double),
                                         cudaMemcpyHostToDevice, c->stream));
         }
@@ -462,6 +477,12 @@ int lbm_get_pops(lbm_ctx* c, double* f, double* g) {
 int lbm_set_pops(lbm_ctx* c, const double* f, const double* g) {
     if (!c) return set_error(nullptr, LBM_EINVAL, "null handle");
     if (!f || !g) return set_error(c, LBM_EINVAL, "f and g are required");
+    for (long long k = 0; k < c->P.N; ++k) {
+        double phi = 0.0;
+        for (int q = 0; q < c->P.Q; ++q) phi += g[(size_t)q * c->P.N + k];
+        if (!(phi >= kPhiMin && phi <= kPhiMax))
+            return set_error(c, LBM_EINVAL, "sum of g at cell %lld = %g outside [%g, %g]", k, phi, kPhiMin, kPhiMax);
+    }
     int rc = pops_io(c, nullptr, nullptr, f, g);
     if (rc == LBM_OK) c->initialised = true;
     return rc;

@@ -14,6 +14,10 @@ struct Params {
     long long N;           // nx * ny * nz
     float lw_m, lw_p;      // Lax-Wendroff, difference form (Sec. 2.2):
                            // fbar(x) = f*(x) + lw_m [f*(x - e) - f*(x)] + lw_p [f*(x + e) - f*(x)]
+    float flux_a, flux_b;  // the same update in flux form, weights times 2^30: the flux of a
+                           // population across the face between an upwind cell u and its
+                           // downwind neighbour d is 2^-30 (flux_a g*(u) + flux_b g*(d)),
+                           // flux_a = 2^30 lw_m, flux_b = -2^30 lw_p
     float tau_phi;         // phase-field relaxation time
     float omega_g;         // 1 / (tau_phi + 1/2)           (Eq. c-n_c)
     float grad_s;          // tau_phi / (tau_phi + 1/2)      grad phi = grad_s S - grad_k K1
@@ -27,8 +31,10 @@ struct Params {
     float G[3];            // body force
     float w0;              // storage shift of f: f_i is held as f_i - t_i w0 (w0 = p0 / cs^2)
     float phi_ref;         // storage shift of g: g_i is held as g_i - t_i phi_ref (phi_ref = 0 or 1)
-    int general;           // 1 if any of drho, G, mu_m1 is non-zero (selects the full collision)
+    int phi_ref_fx;        // phi_ref * 2^30, the same level in the fixed-point units of plane 0
+    int general;           // 1 if any of drho, G, mu_m1, walls is non-zero (selects the full kernels)
     int storage;           // enum StorageKind of the moving planes
+    int walls;             // bit 0: walls at x = -1/2 and nx - 1/2; bit 1: the same in y; bit 2: in z
     float scale_f, scale_g, inv_scale_f, inv_scale_g;  // FP16 storage scaling (powers of two)
     // FP64 copies for the initialisation and the conversions to and from FP64 host arrays
     double w0d, phi_ref_d, tau_phi_d, sigma_d, four_over_delta_d, drho_d, rho2_d;
@@ -39,8 +45,8 @@ enum StorageKind { STORE_F32 = 0, STORE_F16 = 1, STORE_BF16 = 2 };
 
 // Launchers (return the launch's cudaError_t). The state is one buffer of Q planes of N (f, g)
 // pairs: plane i >= 1 holds (f_i - t_i w0, g_i - t_i phi_ref) in the storage type (FP32, FP16
-// or BF16, see storage.cuh); plane 0 holds the zeroth moments of the shifted sets in FP32,
-// (sum_i f_i - w0, sum_i g_i - phi_ref = phi - phi_ref), in place of the rest populations,
+// or BF16, see storage.cuh); plane 0 holds the zeroth moments, sum_i f_i - w0 as FP32 and
+// phi = sum_i g_i as a 32-bit fixed-point integer phi * 2^30, in place of the rest populations,
 // which they determine exactly. f_i and g_i share their propagation stencil, so one load
 // serves both.
 cudaError_t launch_step(const Params& P, int scheme, const void* fg_in, void* fg_out, float* phi_fd,

@@ -37,9 +37,11 @@ step_kernel(const Params P, const void* __restrict__ fg_in, void* __restrict__ f
     if (x >= P.nx || y >= P.ny) return;
     const Nbr nb = make_nbr(P, x, y, z);
     const int c = (z * P.ny + y) * P.nx + x;
+    const WallSide ws = GEN ? make_wall_side(P, x, y, z) : WallSide{};
 
     float fb[Q], gb[Q];
-    pull<Q, true, S>(P, fg_in, c, nb, fb, gb);
+    int phi_fx;
+    pull<Q, true, S, GEN>(P, fg_in, c, nb, fb, gb, phi_fx, ws);
 
     Macro m;
     macro_flow<Q, GEN>(P, fb, gb, m);
@@ -47,20 +49,20 @@ step_kernel(const Params P, const void* __restrict__ fg_in, void* __restrict__ f
         macro_interface_df<Q>(P, gb, m);
     } else {
         float gx, gy, gz;
-        fd_gradient<Q>(phi_fd, c, nb, gx, gy, gz);
+        fd_gradient<Q>(phi_fd, c, GEN ? mirror_at_walls(nb, ws) : nb, gx, gy, gz);
         macro_interface_fd(P, gx, gy, gz, m);
     }
     macro_pressure<GEN>(P, m);
     collide<Q, GEN>(P, m, fb, gb);
 
     // streaming stores: the output is not re-read this step
-    __stcs(moment_plane(fg_out) + c, make_float2(fb[0], gb[0]));
+    __stcs(moment_plane(fg_out) + c, make_float2(fb[0], __int_as_float(phi_fx)));
 #pragma unroll
     for (int i = 1; i < Q; ++i) Store<S>::store(moving_plane<S>(fg_out, P.N, i) + c, fb[i], gb[i], P);
 }
 
 // Finite-difference variant, pass 1: the propagated phi (held as phi - phi_ref), one FP32 plane.
-template <int Q, int S>
+template <int Q, int S, bool WALLS>
 __global__ void __launch_bounds__(kStepThreads, LBM_STEP_MINB)
 fd_phi_kernel(const Params P, const void* __restrict__ fg_in, float* __restrict__ phi) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -70,7 +72,8 @@ fd_phi_kernel(const Params P, const void* __restrict__ fg_in, float* __restrict_
     const Nbr nb = make_nbr(P, x, y, z);
     const int c = (z * P.ny + y) * P.nx + x;
     float fb[Q], gb[Q];
-    pull<Q, false, S>(P, fg_in, c, nb, fb, gb);
+    int phi_fx;
+    pull<Q, false, S, WALLS>(P, fg_in, c, nb, fb, gb, phi_fx, WALLS ? make_wall_side(P, x, y, z) : WallSide{});
     phi[c] = gb[0];
 }
 
@@ -90,7 +93,8 @@ static cudaError_t step_qs(const Params& P, int scheme, const void* in, void* ou
         else step_kernel<Q, SCHEME_DF, false, S><<<grid, block, 0, s>>>(P, in, out, nullptr);
         *launches += 1;
     } else {
-        fd_phi_kernel<Q, S><<<grid, block, 0, s>>>(P, in, phi);
+        if (P.walls) fd_phi_kernel<Q, S, true><<<grid, block, 0, s>>>(P, in, phi);
+        else fd_phi_kernel<Q, S, false><<<grid, block, 0, s>>>(P, in, phi);
         if (P.general) step_kernel<Q, SCHEME_FD, true, S><<<grid, block, 0, s>>>(P, in, out, phi);
         else step_kernel<Q, SCHEME_FD, false, S><<<grid, block, 0, s>>>(P, in, out, phi);
         *launches += 2;
@@ -114,7 +118,8 @@ cudaError_t launch_step(const Params& P, int scheme, const void* fg_in, void* fg
 
 template <int Q, int S>
 static void fd_phi_qs(const Params& P, const void* in, float* phi, cudaStream_t s) {
-    fd_phi_kernel<Q, S><<<step_grid(P), step_block(P), 0, s>>>(P, in, phi);
+    if (P.walls) fd_phi_kernel<Q, S, true><<<step_grid(P), step_block(P), 0, s>>>(P, in, phi);
+    else fd_phi_kernel<Q, S, false><<<step_grid(P), step_block(P), 0, s>>>(P, in, phi);
 }
 
 cudaError_t launch_fd_phi(const Params& P, const void* fg_in, float* phi_fd, cudaStream_t s) {

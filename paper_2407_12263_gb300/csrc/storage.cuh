@@ -6,9 +6,11 @@
 //   STORE_F16   __half2 (4 bytes), f scaled by 2^12 and g by 2^10 before rounding, so the
 //               deviations sit in the normal FP16 range (|f - t w0| < 16, |g - t phi_ref| < 64)
 //   STORE_BF16  __nv_bfloat162 (4 bytes), no scaling (BF16 has the FP32 exponent range)
-// All arithmetic is FP32 in every case. Keeping plane 0 in FP32 keeps phi (and sum f)
-// at FP32 precision and sum phi conserved to FP32 round-off: the Lax-Wendroff increments that
-// update plane 0 telescope over the grid whatever precision the moving populations carry.
+// All arithmetic is FP32 in every case. Plane 0 is 8 bytes whatever the storage: sum_i f_i - w0
+// as FP32 and phi as the 32-bit integer phi * 2^30 (resolution 9.3e-10, range [-2, 2)). Each
+// step adds to it the face fluxes of g rounded to that grid one face at a time; the two cells
+// of a face round the same FP32 value, so the integers cancel in pairs and sum phi over the
+// grid is conserved exactly, bit for bit, whatever precision the moving populations carry.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -62,7 +64,11 @@ struct Store<STORE_BF16> {
     }
 };
 
-// Plane 0 (FP32 pairs) and the moving planes of a state buffer.
+// Fixed-point units of phi in plane 0.
+constexpr double kPhiFx = 1073741824.0;  // 2^30
+constexpr float kPhiFxInvF = 1.0f / 1073741824.0f;
+
+// Plane 0 ((FP32, int32) pairs held as float2) and the moving planes of a state buffer.
 __host__ __device__ __forceinline__ const float2* moment_plane(const void* state) {
     return static_cast<const float2*>(state);
 }

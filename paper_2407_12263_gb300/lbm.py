@@ -184,9 +184,9 @@ class Lattice:
 
     def __init__(self, grid, lattice, tau_f, tau_g, M, xi, sigma, rho_ratio=1.0, mu_ratio=1.0,
                  body_force=(0.0, 0.0, 0.0), scheme=LBM_SCHEME_DIFFERENCE_FREE, courant=0.997, stream=None,
-                 storage=LBM_STORAGE_FP32, graph_steps=None):
+                 storage=LBM_STORAGE_FP32, graph_steps=None, walls=0):
         o = lbm_default_opts()
-        o.scheme, o.courant, o.storage = scheme, courant, storage
+        o.scheme, o.courant, o.storage, o.walls = scheme, courant, storage, walls
         if graph_steps is not None:
             o.graph_steps = graph_steps
         o.stream = stream

@@ -71,7 +71,7 @@ def test_create_rejects_invalid_arguments(lib, over):
     assert lbm.lbm_last_error(None) != "no error"
 
 
-@pytest.mark.parametrize("field,value", [("scheme", 5), ("storage", 3), ("storage", -1), ("walls", 1), ("courant", 0.0),
+@pytest.mark.parametrize("field,value", [("scheme", 5), ("storage", 3), ("storage", -1), ("walls", 8), ("walls", -1), ("courant", 0.0),
                                          ("courant", 1.5), ("graph_steps", 1), ("graph_steps", 3),
                                          ("graph_steps", -2)])
 def test_create_rejects_invalid_options(lib, field, value):
