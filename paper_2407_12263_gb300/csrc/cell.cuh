@@ -355,4 +355,43 @@ __device__ __forceinline__ void collide(const Params& P, const Macro& m, float (
     fb[0] = GEN ? m.Pbar + ugr : m.Pbar;  // plane 0 keeps phi_fx: the collision conserves phi
 }
 
+// One whole time step of cell (x, y, z): propagate, macroscopic stage, collide, store the Q
+// post-collision pairs into fg_out. The single-case step kernel and the batched kernel both run
+// this, so a case gives the same bits whichever of them advances it.
+template <int Q, int SCHEME, bool GEN, int S>
+__device__ __forceinline__ void step_cell(const Params& P, const void* __restrict__ fg_in, void* __restrict__ fg_out,
+                                          const float* __restrict__ phi_fd, int x, int y, int z) {
+    const Nbr nb = make_nbr(P, x, y, z);
+    const int c = (z * P.ny + y) * P.nx + x;
+    const WallSide ws = GEN ? make_wall_side(P, x, y, z) : WallSide{};
+
+    float fb[Q], gb[Q];
+    int phi_fx;
+    // Only warps holding a wall cell take the propagation with per-link wall tests. The choice is
+    // per warp, so a warp never runs both versions; for a cell off the walls both read the same
+    // addresses and give the same bits, so the result does not depend on it.
+    const bool at_wall = GEN && (ws.xlo || ws.xhi || ws.ylo || ws.yhi || ws.zlo || ws.zhi);
+    if (GEN && __any_sync(__activemask(), at_wall))
+        pull<Q, true, S, true>(P, fg_in, c, nb, fb, gb, phi_fx, ws);
+    else
+        pull<Q, true, S, false>(P, fg_in, c, nb, fb, gb, phi_fx);
+
+    Macro m;
+    macro_flow<Q, GEN>(P, fb, gb, m);
+    if (SCHEME == SCHEME_DF) {
+        macro_interface_df<Q>(P, gb, m);
+    } else {
+        float gx, gy, gz;
+        fd_gradient<Q>(phi_fd, c, GEN ? mirror_at_walls(nb, ws) : nb, gx, gy, gz);
+        macro_interface_fd(P, gx, gy, gz, m);
+    }
+    macro_pressure<GEN>(P, m);
+    collide<Q, GEN>(P, m, fb, gb);
+
+    // streaming stores: the output is not re-read this step
+    __stcs(moment_plane(fg_out) + c, make_float2(fb[0], __int_as_float(phi_fx)));
+#pragma unroll
+    for (int i = 1; i < Q; ++i) Store<S>::store(moving_plane<S>(fg_out, P.N, i) + c, fb[i], gb[i], P);
+}
+
 }  // namespace lbm

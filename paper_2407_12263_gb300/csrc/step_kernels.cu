@@ -35,30 +35,7 @@ step_kernel(const Params P, const void* __restrict__ fg_in, void* __restrict__ f
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= P.nx || y >= P.ny) return;
-    const Nbr nb = make_nbr(P, x, y, z);
-    const int c = (z * P.ny + y) * P.nx + x;
-    const WallSide ws = GEN ? make_wall_side(P, x, y, z) : WallSide{};
-
-    float fb[Q], gb[Q];
-    int phi_fx;
-    pull<Q, true, S, GEN>(P, fg_in, c, nb, fb, gb, phi_fx, ws);
-
-    Macro m;
-    macro_flow<Q, GEN>(P, fb, gb, m);
-    if (SCHEME == SCHEME_DF) {
-        macro_interface_df<Q>(P, gb, m);
-    } else {
-        float gx, gy, gz;
-        fd_gradient<Q>(phi_fd, c, GEN ? mirror_at_walls(nb, ws) : nb, gx, gy, gz);
-        macro_interface_fd(P, gx, gy, gz, m);
-    }
-    macro_pressure<GEN>(P, m);
-    collide<Q, GEN>(P, m, fb, gb);
-
-    // streaming stores: the output is not re-read this step
-    __stcs(moment_plane(fg_out) + c, make_float2(fb[0], __int_as_float(phi_fx)));
-#pragma unroll
-    for (int i = 1; i < Q; ++i) Store<S>::store(moving_plane<S>(fg_out, P.N, i) + c, fb[i], gb[i], P);
+    step_cell<Q, SCHEME, GEN, S>(P, fg_in, fg_out, phi_fd, x, y, z);
 }
 
 // Finite-difference variant, pass 1: the propagated phi (held as phi - phi_ref), one FP32 plane.
