@@ -222,6 +222,7 @@ def run_ours(args):
     e2e = run_e2e(lbm, torch, grid, w, params, phi0, cells, args, world)
     small = run_small_2d(lbm, torch, stream, args, world)
     rt = run_rayleigh_taylor(lbm, torch, stream, args, world)
+    bubbles = run_batched_bubbles(lbm, torch, stream, args, world)
 
     out = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(t_df / args.steps * 1e3, 5), "higher_is_better": True,
@@ -242,6 +243,7 @@ def run_ours(args):
            "storage16": sixteen,
            "droplet2d_64": small,
            "rayleigh_taylor_128x128x512": rt,
+           "batched_rising_bubbles": bubbles,
            "sum_phi_drift": {"df": drift, "fd": fd_drift, "steps": args.warmup + args.steps}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"], out["accuracy"] = run_cpu_baseline(lbm, grid, w, params, phi0, cells, args)
@@ -319,6 +321,84 @@ def run_rayleigh_taylor(lbm, torch, stream, args, world):
         out[name] = {"value": round(v, 1), "ms_per_step": round(secs / steps * 1e3, 5), "bytes_per_cell": bpc,
                      "hbm_frac": round(bpc * cells / (secs / steps) / 1e9 / peak, 4),
                      "speedup_vs_fp32": round(v / fp32, 4), "sum_phi_change": m1 - m0}
+    return out
+
+
+CASE_KEYS = ("grid", "lattice", "tau_f", "tau_g", "M", "xi", "sigma", "rho_ratio", "mu_ratio", "body_force", "walls")
+
+
+def run_batched_bubbles(lbm, torch, stream, args, world):
+    """256 seeded rising-bubble boxes of uneven size (D3Q19, walls on every side, density ratio
+    2-10, viscosity ratio 1-10, Eo 1-50, Mo 1e-5..1e-1): aggregate MLUPS of one handle per case
+    (FP32, each case's steps launched on its own, graph-replayed, one stream) against the batch
+    (group launches per size class and dedicated launches on concurrent branches, graph-replayed)
+    untuned, tuned in form and tile, and tuned in form, tile and storage."""
+    cases = I.rising_bubble_cases()[:args.batch_cases]
+    cells = sum(int(np.prod(c["grid"])) for c in cases)
+    steps = max(2, args.steps // 50)
+    out = {"cases": len(cases), "cells": cells, "steps": steps, "warmup": args.warmup, "unit": "MLUPS",
+           "config": f"rising_bubble_cases(n=256, seed=12263)[:{len(cases)}]: widths {{32,48,64,96}} x height "
+                     "{1,2}, R = width/8, walls on all sides, gravity -z"}
+
+    def timed(step_fn):
+        torch.cuda.synchronize()
+        barrier(world)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        step_fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(ev0.elapsed_time(ev1) / 1e3, world)
+
+    # one handle per case, FP32
+    singles = []
+    for c in cases:
+        h = lbm.Lattice(c["grid"], 19, **{k: c[k] for k in CASE_KEYS[2:]}, stream=stream.cuda_stream)
+        h.init_phi(I.bubble_phi(c))
+        singles.append(h)
+    for h in singles:
+        h.step(args.warmup)
+    secs = timed(lambda: [h.step(steps) for h in singles])
+    out["one_case_per_launch_fp32"] = round(aggregate_mlups(cells, steps, secs, world), 1)
+    out["one_case_per_launch_launches_per_step"] = len(cases)
+    for h in singles:
+        h.close()
+    del singles
+
+    def batched(storage, tune):
+        structs = [lbm.make_case(**{k: c[k] for k in CASE_KEYS}, storage=storage) for c in cases]
+        b = lbm.Batch(structs, stream=stream.cuda_stream)
+        if tune:
+            b.tune(trial_steps=5)
+        for k, c in enumerate(cases):
+            b.case(k).init_phi(I.bubble_phi(c))
+        m0 = [b.case(k).mass()[0] for k in range(len(cases))]
+        b.step(args.warmup)
+        n0 = b.launch_count
+        secs = timed(lambda: b.step(steps))
+        launches = b.launch_count - n0
+        nonfinite, changed = 0, 0
+        for k in range(len(cases)):
+            try:
+                if b.case(k).mass()[0] != m0[k]:
+                    changed += 1
+            except lbm.LBMError:
+                nonfinite += 1
+        classes = {}
+        for k, c in enumerate(cases):
+            tile, st, ded = b.config(k)
+            classes["x".join(map(str, c["grid"]))] = {"form": "dedicated" if ded else "group", "tile": list(tile),
+                                                      "storage": ["fp32", "fp16", "bf16"][st]}
+        b.close()
+        return {"value": round(aggregate_mlups(cells, steps, secs, world), 1), "launches_per_step": launches / steps,
+                "classes": classes, "nonfinite_cases": nonfinite, "sum_phi_changed_cases": changed}
+
+    out["batched_fp32_default_tiles"] = batched(lbm.LBM_STORAGE_FP32, False)
+    out["batched_fp32_tuned"] = batched(lbm.LBM_STORAGE_FP32, True)
+    out["batched_auto_tuned"] = batched(lbm.LBM_STORAGE_AUTO, True)
+    base = out["one_case_per_launch_fp32"]
+    for key in ("batched_fp32_default_tiles", "batched_fp32_tuned", "batched_auto_tuned"):
+        out[key]["speedup_vs_one_case_per_launch"] = round(out[key]["value"] / base, 4)
     return out
 
 
@@ -469,6 +549,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(I.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-cases", type=int, default=256,
+                    help="rising-bubble cases of the batched leg (the first N of the seeded 256)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=90.0)
     args = ap.parse_args(argv)

@@ -57,7 +57,8 @@ enum lbm_storage {
     LBM_STORAGE_FP32 = 0, /* (f_i, g_i) pairs as 2 x FP32: 304 B per D3Q19 cell and step */
     LBM_STORAGE_FP16 = 1, /* moving pairs as 2 x FP16 (deviations scaled by 2^12 and 2^10), the
                              zeroth-moment plane in FP32: 160 B per D3Q19 cell and step */
-    LBM_STORAGE_BF16 = 2  /* moving pairs as 2 x BF16, zeroth-moment plane in FP32: 160 B */
+    LBM_STORAGE_BF16 = 2, /* moving pairs as 2 x BF16, zeroth-moment plane in FP32: 160 B */
+    LBM_STORAGE_AUTO = 3  /* batch cases only: lbm_batch_tune picks the fastest of the three */
 };
 
 enum lbm_scheme {
@@ -193,8 +194,93 @@ int lbm_mass_noalloc(const float *g, int lattice, const int grid[3], double cour
 /* Message of the last failure (see the error notes above); never NULL. */
 const char *lbm_last_error(const lbm_ctx *ctx);
 
-/* Free the handle and its device memory; NULL is a no-op. Synchronises the stream. */
+/* Free the handle and its device memory; NULL is a no-op. Synchronises the stream. A case
+ * handle of a batch (lbm_batch_case) is left alone: lbm_batch_destroy frees it. */
 void lbm_destroy(lbm_ctx *ctx);
+
+/* ---------------------------------------------------------------------------------------
+ * Batches: many independent cases advanced together.
+ *
+ * The paper advances one problem at a time; this interface has no counterpart there. It
+ * exists because a small grid cannot fill the GPU: a 32^3 case is 256 blocks of 128 cells,
+ * fewer than the 608 that 152 SMs keep resident. A step of the batch is a set of launches on
+ * eight branch streams that run concurrently:
+ *   - group launches: all cases of one grid size (and tile shape, storage) in one grid of
+ *     128-cell tiles, the case picked by blockIdx.y, its parameters read from the launch's
+ *     parameter block;
+ *   - dedicated launches: the single-case step kernel of lbm_step for one case.
+ * Every cell runs the same code as lbm_step, so a case gives the same bits whether the batch
+ * or its own handle advances it. lbm_batch_tune picks, per size class, the faster of the two
+ * forms on this GPU. Each case's steps stay on one branch, so a graph of many steps has one
+ * fork and one join and no barrier between steps; nothing spins.
+ * ------------------------------------------------------------------------------------- */
+typedef struct lbm_batch lbm_batch;
+
+/* One case: the arguments of lbm_create and its options. Every case of a batch uses the
+ * difference-free scheme and the same lattice. */
+typedef struct {
+    int grid[3];
+    int lattice;
+    double tau_f, tau_g, M, xi, sigma, rho_ratio, mu_ratio;
+    double body_force[3];
+    int walls;      /* as lbm_opts.walls */
+    int storage;    /* LBM_STORAGE_FP32 / FP16 / BF16, or LBM_STORAGE_AUTO: lbm_batch_tune
+                       times the three on this GPU and keeps the fastest (the state buffers are
+                       sized for FP32); FP32 until then */
+    double courant; /* 0 = the default 0.997 */
+} lbm_case;
+
+typedef struct {
+    void *stream;    /* cudaStream_t shared by the batch and its cases; NULL = one it owns */
+    int graph_steps; /* lbm_batch_step replays CUDA graphs of this many steps (even, >= 2;
+                        default 32); 0 launches every step directly */
+} lbm_batch_opts;
+
+void lbm_batch_default_opts(lbm_batch_opts *opts);
+
+/* Create the cases (each as lbm_create would, with the same argument checks) and the batch.
+ * n_cases >= 1; cases[] is read only during the call. Returns LBM_OK and *out, or an error
+ * with *out = NULL and the message in lbm_batch_last_error(NULL). */
+int lbm_batch_create(lbm_batch **out, int n_cases, const lbm_case *cases, const lbm_batch_opts *opts);
+
+/* The handle of case k (0 <= k < n_cases), owned by the batch, or NULL. Every single-case
+ * entry point works on it: lbm_init_phi (required before lbm_batch_step), lbm_moments,
+ * lbm_gradients, lbm_mass, lbm_get_pops / lbm_set_pops, and lbm_step, which advances that
+ * case alone. */
+lbm_ctx *lbm_batch_case(lbm_batch *b, int k);
+
+/* Tuner. For every size class (cases of one grid size) it times trial_steps steps of the
+ * class alone in each form: a group launch per tile shape 2^a x 2^b x 2^c = 128 (a >= 3, no
+ * extent beyond the grid's next power of two) and dedicated launches; where a case asks for
+ * LBM_STORAGE_AUTO and holds no state yet, each storage as well. The fastest form (and storage)
+ * is kept for the class. Trial launches read each case's current state and write only its
+ * other buffer, so the state is unchanged; cases without state are timed on the uniform rest
+ * state. Synchronous. Without it every case runs in group launches of rows of x. */
+int lbm_batch_tune(lbm_batch *b, int trial_steps);
+
+/* Tile shape (cells in x, y, z) of case k's group launch, its storage, and 1 if the case runs
+ * in dedicated launches instead; any output may be NULL. */
+int lbm_batch_case_config(const lbm_batch *b, int k, int tile[3], int *storage, int *dedicated);
+
+/* Fix case k's form by hand (to restore choices the tuner made in an earlier run, say): tile
+ * (cells in x, y, z; powers of two with product 128, z = 1 in 2D; NULL keeps the current one)
+ * and dedicated (nonzero: dedicated launches). LBM_EINVAL for an invalid tile or case. */
+int lbm_batch_set_config(lbm_batch *b, int k, const int tile[3], int dedicated);
+
+/* Advance every case by n >= 0 steps (asynchronous on the batch's stream, which the branches
+ * fork from and join back to; whole multiples of graph_steps are replayed from CUDA graphs).
+ * LBM_ESTATE if a case has no state. */
+int lbm_batch_step(lbm_batch *b, int n);
+
+/* Kernel launches of the batch so far (steps plus tuner trials), and total cells. */
+long long lbm_batch_launch_count(const lbm_batch *b);
+long long lbm_batch_cells(const lbm_batch *b);
+
+/* Message of the last failure of a batch call (b = NULL: of the last lbm_batch_create). */
+const char *lbm_batch_last_error(const lbm_batch *b);
+
+/* Free the batch and all its cases; NULL is a no-op. */
+void lbm_batch_destroy(lbm_batch *b);
 
 #ifdef __cplusplus
 }

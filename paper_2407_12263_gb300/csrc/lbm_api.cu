@@ -13,32 +13,11 @@
 
 #include "../../include/lbm.h"
 #include "lattice.cuh"
+#include "lbm_ctx.h"
 #include "lbm_internal.h"
 #include "storage.cuh"
 
 using lbm::Params;
-
-struct lbm_ctx {
-    Params P;
-    int scheme;
-    double courant;
-    int device;
-    cudaStream_t stream;
-    bool own_stream;
-    void* fg[2];           // ping-pong state: Q planes of N (f, g) pairs each (storage.cuh)
-    int cur;               // index of the buffer holding the current state
-    float* phi_fd;         // propagated phi plane of the finite-difference variant
-    double* partials;      // per-block FP64 partial sums of the mass reduction
-    int n_partials;
-    double* result;        // 3 doubles: sum phi, sum rho phi, non-finite count
-    double* staging;       // FP64 staging for host transfers, allocated on first use
-    size_t staging_elems;
-    bool initialised;
-    long long launches;
-    int graph_steps;                  // steps per replayed CUDA graph (0 = none)
-    cudaGraphExec_t graph_exec[2];    // graph of graph_steps steps starting from buffer 0 / 1
-    char err[512];
-};
 
 namespace {
 
@@ -132,6 +111,16 @@ int capture_graph(lbm_ctx* c, int start) {
     return LBM_OK;
 }
 
+// FP16 storage: f deviations scaled by 2^12 and g deviations by 2^10 (exact power-of-two
+// scaling) so that they sit in the normal FP16 range; 1 for FP32 and BF16.
+void apply_storage(Params& P, int storage) {
+    P.storage = storage;
+    P.scale_f = (storage == lbm::STORE_F16) ? 4096.0f : 1.0f;
+    P.scale_g = (storage == lbm::STORE_F16) ? 1024.0f : 1.0f;
+    P.inv_scale_f = 1.0f / P.scale_f;
+    P.inv_scale_g = 1.0f / P.scale_g;
+}
+
 int check_ctx(lbm_ctx* c) {
     if (!c) return set_error(nullptr, LBM_EINVAL, "null handle");
     LBM_CUDA(c, cudaSetDevice(c->device));
@@ -154,6 +143,18 @@ void lbm_default_opts(lbm_opts* o) {
 
 int lbm_create(lbm_ctx** out, const int grid[3], int lattice, double tau_f, double tau_g, double M, double xi,
                double sigma, double rho_ratio, double mu_ratio, const double body_force[3], const lbm_opts* opts) {
+    lbm_opts o;
+    lbm_default_opts(&o);
+    if (opts) o = *opts;
+    return lbm::create_ctx(out, grid, lattice, tau_f, tau_g, M, xi, sigma, rho_ratio, mu_ratio, body_force, &o,
+                           o.storage);
+}
+
+}  // extern "C"
+
+int lbm::create_ctx(lbm_ctx** out, const int grid[3], int lattice, double tau_f, double tau_g, double M, double xi,
+                    double sigma, double rho_ratio, double mu_ratio, const double body_force[3], const lbm_opts* opts,
+                    int alloc_storage) {
     if (!out) return set_error(nullptr, LBM_EINVAL, "out is NULL");
     *out = nullptr;
     if (!grid) return set_error(nullptr, LBM_EINVAL, "grid is NULL");
@@ -237,13 +238,7 @@ int lbm_create(lbm_ctx** out, const int grid[3], int lattice, double tau_f, doub
     P.phi_ref_fx = 1 << 30;
     P.walls = o.walls;
     P.general = (rho_ratio != 1.0 || mu_ratio != 1.0 || G[0] != 0 || G[1] != 0 || G[2] != 0 || o.walls) ? 1 : 0;
-    P.storage = o.storage;
-    // FP16 storage: f deviations scaled by 2^12 and g deviations by 2^10 (exact power-of-two
-    // scaling) so that they sit in the normal FP16 range; 1 for FP32 and BF16
-    P.scale_f = (o.storage == lbm::STORE_F16) ? 4096.0f : 1.0f;
-    P.scale_g = (o.storage == lbm::STORE_F16) ? 1024.0f : 1.0f;
-    P.inv_scale_f = 1.0f / P.scale_f;
-    P.inv_scale_g = 1.0f / P.scale_g;
+    apply_storage(P, o.storage);
     P.w0d = 1.0;
     P.phi_ref_d = 1.0;
     P.tau_phi_d = tau_phi;
@@ -269,7 +264,11 @@ int lbm_create(lbm_ctx** out, const int grid[3], int lattice, double tau_f, doub
         }
         c->own_stream = true;
     }
-    const size_t pop_bytes = lbm::state_bytes(lattice, N, o.storage);
+    if (alloc_storage < 0 || alloc_storage > 2 ||
+        lbm::state_bytes(lattice, N, alloc_storage) < lbm::state_bytes(lattice, N, o.storage))
+        alloc_storage = o.storage;
+    const size_t pop_bytes = lbm::state_bytes(lattice, N, alloc_storage);
+    c->fg_bytes = pop_bytes;
     for (int k = 0; k < 2 && rc == LBM_OK; ++k) {
         cudaError_t e = cudaMalloc(&c->fg[k], pop_bytes);
         if (e != cudaSuccess)
@@ -290,6 +289,20 @@ int lbm_create(lbm_ctx** out, const int grid[3], int lattice, double tau_f, doub
     *out = c;
     return LBM_OK;
 }
+
+int lbm::set_ctx_storage(lbm_ctx* c, int storage) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (c->initialised) return set_error(c, LBM_ESTATE, "the storage of a handle with state cannot change");
+    if (storage < 0 || storage > 2 || lbm::state_bytes(c->P.Q, c->P.N, storage) > c->fg_bytes)
+        return set_error(c, LBM_EINVAL, "storage %d does not fit this handle", storage);
+    apply_storage(c->P, storage);
+    drop_graphs(c);
+    c->version += 1;
+    return LBM_OK;
+}
+
+extern "C" {
 
 int lbm_init_phi(lbm_ctx* c, const double* phi0, const double* u0, double p0) {
     int rc = check_ctx(c);
@@ -337,6 +350,7 @@ int lbm_init_phi(lbm_ctx* c, const double* phi0, const double* u0, double p0) {
     }
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));
     c->initialised = true;
+    c->version += 1;
     return LBM_OK;
 }
 
@@ -484,6 +498,7 @@ int lbm_set_pops(lbm_ctx* c, const double* f, const double* g) {
             return set_error(c, LBM_EINVAL, "sum of g at cell %lld = %g outside [%g, %g]", k, phi, kPhiMin, kPhiMax);
     }
     int rc = pops_io(c, nullptr, nullptr, f, g);
+    c->version += 1;
     if (rc == LBM_OK) c->initialised = true;
     return rc;
 }
@@ -494,7 +509,10 @@ double lbm_tau_phi(const lbm_ctx* c) { return c ? c->P.tau_phi_d : 0.0; }
 
 const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err : g_create_error; }
 
-void lbm_destroy(lbm_ctx* c) { free_ctx(c); }
+void lbm_destroy(lbm_ctx* c) {
+    if (c && c->batch_owned) return;  // a case of a batch: freed by lbm_batch_destroy
+    free_ctx(c);
+}
 
 int lbm_lattice_tables(int lattice, int* d, int* e, double* w) {
     if (lattice == LBM_D2Q9) {

@@ -77,4 +77,40 @@ cudaError_t launch_pops_to_f64(const Params& P, const void* src, int is_f, int z
 cudaError_t launch_pops_from_f64(const Params& P, const double* src, int is_f, int z0, int nzs, void* dst,
                                  cudaStream_t s);
 
+// ---------------------------------------------------------------------------------------
+// Batches of independent cases (lbm_batch_*).
+// ---------------------------------------------------------------------------------------
+constexpr int kBatchThreads = 128;    // cells per tile and threads per block
+constexpr int kMaxLaunchCases = 128;  // cases per group launch: their table fits the 32 KB parameter space
+
+// One case of a group launch, as the kernel reads it from its parameter block.
+struct LaunchCase {
+    Params P;
+    void* fg[2];    // the case's ping-pong state buffers
+    int cur;        // buffer holding the state when the group was built
+    int pad_;
+};
+
+// The whole parameter block of a group launch: up to kMaxLaunchCases cases of one grid size,
+// tile shape, kernel variant and storage.
+struct BatchLaunch {
+    int n_cases;
+    int flip;       // step parity: reads fg[cur ^ flip]
+    int tx_shift;   // tile of 2^tx_shift x 2^ty_shift x 2^(7 - tx_shift - ty_shift) cells
+    int ty_shift;
+    int ntx;        // tiles along x, y and z
+    int nty;
+    int ntz;
+    int general;
+    int storage;
+    int pad_;
+    LaunchCase cases[kMaxLaunchCases];
+};
+
+// One step of every case of the group: grid (ntx * nty, n_cases, ntz), one tile per block.
+cudaError_t launch_batch_group(int Q, const BatchLaunch& L, cudaStream_t s);
+// The uniform rest state phi = 1, p = 1/3, u = 0 in the storage of P (plane 0 = (0, 2^30),
+// moving planes 0), used by the tuner on cases that hold no state yet.
+cudaError_t launch_fill_rest(const Params& P, void* fg, cudaStream_t s);
+
 }  // namespace lbm

@@ -150,3 +150,54 @@ def shear_wave(grid, amplitude, axis_u=0, axis_k=1, k=1):
 def sine_phi(grid, mean, amplitude, axis=0, k=1):
     coords = cell_coords(grid)
     return mean + amplitude * np.sin(2 * np.pi * k * coords[axis] / grid[axis])
+
+
+def rising_bubble_cases(n=256, seed=12263, sizes=(32, 48, 64, 96), heights=(1, 2), xi=4.0, M=0.02,
+                        U=0.04, U_max=0.1, tau_min=0.01):
+    """Seeded batch of independent rising-bubble boxes (D3Q19, walls on every side, gravity along
+    -z). Per case: width s from `sizes` and height factor h from `heights` (uniform), grid
+    (s, s, h s); bubble radius R = s/8 (D = 2R), centred at (s/2, s/2, 2D) with phi = 0 inside;
+    density ratio rho1/rho2 uniform in [2, 10], viscosity ratio eta1/eta2 uniform in [1, 10];
+    Eotvos Eo = drho g D^2 / sigma log-uniform in [1, 50] and Morton
+    Mo = g eta1^4 drho / (rho1^2 sigma^3) log-uniform in [1e-5, 1e-1]. The velocity scale
+    U = sqrt(g D) is 0.04, raised (up to 0.1) where the smaller relaxation time
+    3 min(eta1/rho1, eta2/rho2) would fall below tau_min. Returns a list of dicts with the
+    lbm_create arguments, plus 'R', 'centre', 'Eo', 'Mo', 'U'."""
+    rng = np.random.default_rng(seed)
+    cases = []
+    for _ in range(n):
+        s = int(rng.choice(sizes))
+        h = int(rng.choice(heights))
+        rho1 = rng.uniform(2.0, 10.0)
+        mu_ratio = rng.uniform(1.0, 10.0)
+        Eo = float(np.exp(rng.uniform(np.log(1.0), np.log(50.0))))
+        Mo = float(np.exp(rng.uniform(np.log(1e-5), np.log(1e-1))))
+        R = s / 8.0
+        D = 2.0 * R
+        drho = rho1 - 1.0
+
+        def groups(u):
+            g = u * u / D
+            sigma = drho * g * D * D / Eo
+            eta1 = (Mo * rho1 * rho1 * sigma ** 3 / (g * drho)) ** 0.25
+            return g, sigma, eta1
+
+        g, sigma, eta1 = groups(U)
+        u = U
+        tau = 3.0 * min(eta1 / rho1, eta1 / mu_ratio)
+        if tau < tau_min:  # eta1 grows linearly with U at fixed Eo and Mo
+            u = min(U_max, U * tau_min / tau)
+            g, sigma, eta1 = groups(u)
+        eta2 = eta1 / mu_ratio
+        cases.append(dict(grid=(s, s, h * s), lattice=19, tau_f=3.0 * eta2, tau_g=0.8, M=M, xi=xi, sigma=sigma,
+                          rho_ratio=rho1, mu_ratio=mu_ratio, body_force=(0.0, 0.0, -g), walls=7,
+                          R=R, centre=(s / 2.0 - 0.5, s / 2.0 - 0.5, 2.0 * D), Eo=Eo, Mo=Mo, U=u))
+    return cases
+
+
+def bubble_phi(case):
+    """phi = 1 in the liquid, 0 inside the bubble (tanh of width xi), no periodic images."""
+    x, y, z = cell_coords(case["grid"])
+    c = case["centre"]
+    r = np.sqrt((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2)
+    return 0.5 * (1.0 + np.tanh(2.0 * (r - case["R"]) / case["xi"]))

@@ -18,7 +18,7 @@ import numpy as np
 LBM_D2Q9, LBM_D3Q19 = 9, 19
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENONFINITE, LBM_ETIMEOUT, LBM_ESTATE = 0, -1, -2, -3, -4, -5, -6
 LBM_SCHEME_DIFFERENCE_FREE, LBM_SCHEME_FINITE_DIFFERENCE = 0, 1
-LBM_STORAGE_FP32, LBM_STORAGE_FP16, LBM_STORAGE_BF16 = 0, 1, 2
+LBM_STORAGE_FP32, LBM_STORAGE_FP16, LBM_STORAGE_BF16, LBM_STORAGE_AUTO = 0, 1, 2, 3
 
 _LIB_PATH = Path(__file__).resolve().parent / "_build" / "liblbm_gb300.so"
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -28,6 +28,18 @@ _ip = ctypes.POINTER(ctypes.c_int)
 class lbm_opts(ctypes.Structure):
     _fields_ = [("scheme", ctypes.c_int), ("storage", ctypes.c_int), ("courant", ctypes.c_double),
                 ("walls", ctypes.c_int), ("stream", ctypes.c_void_p), ("graph_steps", ctypes.c_int)]
+
+
+class lbm_case(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_int * 3), ("lattice", ctypes.c_int), ("tau_f", ctypes.c_double),
+                ("tau_g", ctypes.c_double), ("M", ctypes.c_double), ("xi", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("rho_ratio", ctypes.c_double), ("mu_ratio", ctypes.c_double),
+                ("body_force", ctypes.c_double * 3), ("walls", ctypes.c_int), ("storage", ctypes.c_int),
+                ("courant", ctypes.c_double)]
+
+
+class lbm_batch_opts(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_void_p), ("graph_steps", ctypes.c_int)]
 
 
 class LBMError(RuntimeError):
@@ -55,6 +67,18 @@ SIGNATURES = [
                                         ctypes.c_void_p, ctypes.c_void_p]),
     ("lbm_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("lbm_destroy", None, [ctypes.c_void_p]),
+    ("lbm_batch_default_opts", None, [ctypes.POINTER(lbm_batch_opts)]),
+    ("lbm_batch_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(lbm_case),
+                                        ctypes.POINTER(lbm_batch_opts)]),
+    ("lbm_batch_case", ctypes.c_void_p, [ctypes.c_void_p, ctypes.c_int]),
+    ("lbm_batch_tune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("lbm_batch_case_config", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _ip, _ip, _ip]),
+    ("lbm_batch_set_config", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _ip, ctypes.c_int]),
+    ("lbm_batch_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("lbm_batch_launch_count", ctypes.c_longlong, [ctypes.c_void_p]),
+    ("lbm_batch_cells", ctypes.c_longlong, [ctypes.c_void_p]),
+    ("lbm_batch_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+    ("lbm_batch_destroy", None, [ctypes.c_void_p]),
 ]
 
 _lib = None
@@ -178,13 +202,96 @@ def lbm_destroy(h):
         load().lbm_destroy(h)
 
 
+def _bcheck(b, status):
+    if status != LBM_OK:
+        msg = load().lbm_batch_last_error(b)
+        raise LBMError(status, msg.decode() if msg else "")
+    return status
+
+
+def lbm_batch_default_opts() -> lbm_batch_opts:
+    o = lbm_batch_opts()
+    load().lbm_batch_default_opts(ctypes.byref(o))
+    return o
+
+
+def make_case(grid, lattice, tau_f, tau_g, M, xi, sigma, rho_ratio=1.0, mu_ratio=1.0,
+              body_force=(0.0, 0.0, 0.0), walls=0, storage=LBM_STORAGE_FP32, courant=0.0) -> lbm_case:
+    c = lbm_case()
+    c.grid[:] = [int(v) for v in grid]
+    c.lattice, c.tau_f, c.tau_g, c.M, c.xi, c.sigma = int(lattice), tau_f, tau_g, M, xi, sigma
+    c.rho_ratio, c.mu_ratio = rho_ratio, mu_ratio
+    c.body_force[:] = [float(v) for v in body_force]
+    c.walls, c.storage, c.courant = int(walls), int(storage), courant
+    return c
+
+
+def lbm_batch_create(cases, opts: lbm_batch_opts | None = None):
+    arr = (lbm_case * len(cases))(*cases)
+    b = ctypes.c_void_p()
+    st = load().lbm_batch_create(ctypes.byref(b), len(cases), arr, ctypes.byref(opts) if opts is not None else None)
+    _bcheck(None, st)
+    return b
+
+
+def lbm_batch_case(b, k):
+    h = load().lbm_batch_case(b, int(k))
+    if not h:
+        raise LBMError(LBM_EINVAL, f"no case {k}")
+    return ctypes.c_void_p(h)
+
+
+def lbm_batch_tune(b, trial_steps):
+    _bcheck(b, load().lbm_batch_tune(b, int(trial_steps)))
+
+
+def lbm_batch_case_config(b, k):
+    """(tile shape, storage, dedicated) of case k."""
+    tile = (ctypes.c_int * 3)()
+    storage, dedicated = ctypes.c_int(), ctypes.c_int()
+    _bcheck(b, load().lbm_batch_case_config(b, int(k), tile, ctypes.byref(storage), ctypes.byref(dedicated)))
+    return tuple(tile), storage.value, bool(dedicated.value)
+
+
+def lbm_batch_set_config(b, k, tile=None, dedicated=False):
+    t = None if tile is None else (ctypes.c_int * 3)(*[int(v) for v in tile])
+    _bcheck(b, load().lbm_batch_set_config(b, int(k), t, int(bool(dedicated))))
+
+
+def lbm_batch_step(b, n):
+    _bcheck(b, load().lbm_batch_step(b, int(n)))
+
+
+def lbm_batch_launch_count(b) -> int:
+    return int(load().lbm_batch_launch_count(b))
+
+
+def lbm_batch_cells(b) -> int:
+    return int(load().lbm_batch_cells(b))
+
+
+def lbm_batch_last_error(b=None) -> str:
+    return load().lbm_batch_last_error(b).decode()
+
+
+def lbm_batch_destroy(b):
+    if b:
+        load().lbm_batch_destroy(b)
+
+
 # ---------------------------------------------------------------- convenience wrapper
 class Lattice:
     """One handle; arrays shaped (nz, ny, nx). Same parameters as lbm_create."""
 
-    def __init__(self, grid, lattice, tau_f, tau_g, M, xi, sigma, rho_ratio=1.0, mu_ratio=1.0,
+    def __init__(self, grid, lattice, tau_f=0.8, tau_g=0.8, M=0.02, xi=4.0, sigma=1e-3, rho_ratio=1.0, mu_ratio=1.0,
                  body_force=(0.0, 0.0, 0.0), scheme=LBM_SCHEME_DIFFERENCE_FREE, courant=0.997, stream=None,
-                 storage=LBM_STORAGE_FP32, graph_steps=None, walls=0):
+                 storage=LBM_STORAGE_FP32, graph_steps=None, walls=0, handle=None):
+        if handle is not None:  # a handle owned elsewhere (a case of a Batch)
+            self.h, self._owned = handle, False
+            nx, ny, nz = grid
+            self.Q, self.grid, self.shape, self.N = lattice, tuple(grid), (nz, ny, nx), nx * ny * nz
+            return
+        self._owned = True
         o = lbm_default_opts()
         o.scheme, o.courant, o.storage, o.walls = scheme, courant, storage, walls
         if graph_steps is not None:
@@ -196,7 +303,8 @@ class Lattice:
 
     def close(self):
         if getattr(self, "h", None):
-            lbm_destroy(self.h)
+            if getattr(self, "_owned", True):
+                lbm_destroy(self.h)
             self.h = None
 
     __del__ = close
@@ -243,3 +351,56 @@ class Lattice:
 
     def set_pops(self, f, g):
         lbm_set_pops(self.h, np.ascontiguousarray(f, dtype=np.float64), np.ascontiguousarray(g, dtype=np.float64))
+
+
+class Batch:
+    """Many independent cases advanced by one launch per step. ``cases`` are lbm_case structs
+    (see make_case); ``case(k)`` is a Lattice view of case k (owned by the batch)."""
+
+    def __init__(self, cases, stream=None, graph_steps=None):
+        o = lbm_batch_default_opts()
+        o.stream = stream
+        if graph_steps is not None:
+            o.graph_steps = graph_steps
+        self.b = lbm_batch_create(cases, o)
+        self.n = len(cases)
+        self._views = [Lattice(tuple(c.grid), c.lattice, handle=lbm_batch_case(self.b, k)) for k, c in enumerate(cases)]
+
+    def close(self):
+        if getattr(self, "b", None):
+            for v in self._views:
+                v.h = None
+            lbm_batch_destroy(self.b)
+            self.b = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def case(self, k) -> Lattice:
+        return self._views[k]
+
+    def tune(self, trial_steps=10):
+        lbm_batch_tune(self.b, trial_steps)
+
+    def config(self, k):
+        """(tile, storage, dedicated) of case k."""
+        return lbm_batch_case_config(self.b, k)
+
+    def set_config(self, k, tile=None, dedicated=False):
+        lbm_batch_set_config(self.b, k, tile, dedicated)
+
+    def step(self, n=1):
+        lbm_batch_step(self.b, n)
+
+    @property
+    def launch_count(self):
+        return lbm_batch_launch_count(self.b)
+
+    @property
+    def cells(self):
+        return lbm_batch_cells(self.b)

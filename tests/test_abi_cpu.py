@@ -103,3 +103,63 @@ def test_product_path_does_not_import_the_oracle():
     for src in list(pkg.rglob("*.py")) + list(pkg.rglob("*.cu")) + list(pkg.rglob("*.cuh")) + list(pkg.rglob("*.h")):
         text = src.read_text()
         assert "import oracle" not in text and "from oracle" not in text and "lbm_oracle" not in text, src
+
+
+def _case(**over):
+    c = dict(grid=(8, 8, 8), lattice=19, tau_f=0.8, tau_g=0.8, M=0.02, xi=4.0, sigma=1e-3)
+    c.update(over)
+    return lbm.make_case(**c)
+
+
+@pytest.mark.parametrize("cases,opts", [
+    ([], None),
+    ([_case(), _case(lattice=9, grid=(8, 8, 1))], None),
+    ([_case(storage=4)], None),
+    ([_case(storage=-1)], None),
+    ([_case(grid=(2, 8, 8))], None),
+    ([_case()], dict(graph_steps=3)),
+    ([_case()], dict(graph_steps=-2)),
+])
+def test_batch_create_rejects_invalid_arguments(lib, cases, opts):
+    o = None
+    if opts:
+        o = lbm.lbm_batch_default_opts()
+        for k, v in opts.items():
+            setattr(o, k, v)
+    with pytest.raises(lbm.LBMError) as exc:
+        lbm.lbm_batch_create(cases, o)
+    assert exc.value.status == lbm.LBM_EINVAL
+    assert lbm.lbm_batch_last_error(None) != "no error"
+
+
+def test_batch_null_calls_fail_cleanly(lib):
+    assert lib.lbm_batch_step(None, 1) == lbm.LBM_EINVAL
+    assert lib.lbm_batch_tune(None, 1) == lbm.LBM_EINVAL
+    assert lib.lbm_batch_case(None, 0) is None
+    assert lib.lbm_batch_case_config(None, 0, None, None, None) == lbm.LBM_EINVAL
+    assert lib.lbm_batch_set_config(None, 0, None, 0) == lbm.LBM_EINVAL
+    assert lib.lbm_batch_launch_count(None) == 0
+    lib.lbm_batch_destroy(None)
+    o = lbm.lbm_batch_default_opts()
+    assert (o.stream, o.graph_steps) == (None, 32)
+
+
+def test_rising_bubble_recipe_matches_its_groups():
+    """The seeded batch recipe: grid and radius rules, ranges, and the Eotvos and Morton numbers
+    recomputed from the lattice parameters."""
+    from paper_2407_12263_gb300 import inputs as I
+    cases = I.rising_bubble_cases()
+    assert len(cases) == 256
+    assert cases == I.rising_bubble_cases()  # seeded
+    for c in cases:
+        s = c["grid"][0]
+        assert s in (32, 48, 64, 96) and c["grid"][1] == s and c["grid"][2] in (s, 2 * s)
+        assert c["R"] == s / 8 and c["walls"] == 7
+        assert 2 <= c["rho_ratio"] <= 10 and 1 <= c["mu_ratio"] <= 10
+        D, g, drho = 2 * c["R"], -c["body_force"][2], c["rho_ratio"] - 1
+        eta2 = c["tau_f"] / 3.0
+        eta1 = eta2 * c["mu_ratio"]
+        assert drho * g * D * D / c["sigma"] == pytest.approx(c["Eo"], rel=1e-12)
+        assert g * eta1 ** 4 * drho / (c["rho_ratio"] ** 2 * c["sigma"] ** 3) == pytest.approx(c["Mo"], rel=1e-12)
+        assert 1 <= c["Eo"] <= 50 and 1e-5 <= c["Mo"] <= 1e-1
+        assert np.sqrt(g * D) == pytest.approx(c["U"], rel=1e-12) and 0.04 <= c["U"] <= 0.1
