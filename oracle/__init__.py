@@ -70,6 +70,7 @@ def _load():
     lib.oracle_macroscopic_cell.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp]
     lib.oracle_collide_cell.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp, _dp]
     lib.oracle_init_phi.argtypes = [ctypes.c_void_p, _dp, _dp, ctypes.c_double]
+    lib.oracle_init_fields.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, ctypes.c_double]
     lib.oracle_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
     lib.oracle_moments.argtypes = [ctypes.c_void_p] + [_dp] * 5
     lib.oracle_mass.argtypes = [ctypes.c_void_p, _dp, _dp]
@@ -176,10 +177,12 @@ class Oracle:
 
     __del__ = close
 
-    def init_phi(self, phi0, u0=None, p0=CS2):
+    def init_phi(self, phi0, u0=None, p0=CS2, p=None):
+        """Initial state; p (a pressure field, optional) replaces the uniform p0 in f^eq."""
         phi0 = np.ascontiguousarray(phi0, dtype=np.float64).reshape(self.shape)
         u0 = None if u0 is None else np.ascontiguousarray(u0, dtype=np.float64).reshape((3,) + self.shape)
-        _load().oracle_init_phi(self._h, _ptr(phi0), _ptr(u0), p0)
+        p = None if p is None else np.ascontiguousarray(p, dtype=np.float64).reshape(self.shape)
+        _load().oracle_init_fields(self._h, _ptr(phi0), _ptr(u0), _ptr(p), p0)
 
     def step(self, n=1):
         if _load().oracle_step(self._h, int(n)) != 0:

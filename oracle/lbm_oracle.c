@@ -470,6 +470,11 @@ static void fd_phi_pass(oracle *o)
 
 int oracle_init_phi(oracle *o, const double *phi0, const double *u0, double p0)
 {
+    return oracle_init_fields(o, phi0, u0, NULL, p0);
+}
+
+int oracle_init_fields(oracle *o, const double *phi0, const double *u0, const double *p, double p0)
+{
     const lattice *L = &o->L;
     long c;
     double *grad = o->grad;
@@ -490,7 +495,7 @@ int oracle_init_phi(oracle *o, const double *phi0, const double *u0, double p0)
         for (a = 0; a < 3; ++a) S[a] = smag * n[a];
         rho = o->rho1 * phi0[c] + o->rho2 * (1.0 - phi0[c]);
         oracle_css_tensor(L->d, o->sigma, gn, n, pis);
-        oracle_feq(L->Q, p0, rho, u, pis, o->pis_sign, feq);
+        oracle_feq(L->Q, p ? p[c] : p0, rho, u, pis, o->pis_sign, feq);
         oracle_geq(L->Q, phi0[c], u, S, o->geq_source_tau ? o->tau_phi : 1.0, geq);
         for (i = 0; i < L->Q; ++i) {
             o->f[(long)i * o->N + c] = feq[i];

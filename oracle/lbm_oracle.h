@@ -78,6 +78,10 @@ void oracle_collide_cell(const oracle *o, const double *fbar, const double *g,
 
 /* Initial post-collision populations from phi0 (N), u0 (3 planes or NULL), p0. */
 int oracle_init_phi(oracle *o, const double *phi0, const double *u0, double p0);
+/* As oracle_init_phi, with the pressure of f^eq taken per cell from p (N values) when p is not
+ * NULL (p0 is then unused): the initial state of the Taylor-Green case of Sec. 3.4, whose
+ * pressure field is part of the initial condition. */
+int oracle_init_fields(oracle *o, const double *phi0, const double *u0, const double *p, double p0);
 int oracle_step(oracle *o, int nsteps);
 
 /* Fields of the propagated current state (what the next collision uses).

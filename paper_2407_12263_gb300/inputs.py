@@ -201,3 +201,21 @@ def bubble_phi(case):
     c = case["centre"]
     r = np.sqrt((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2)
     return 0.5 * (1.0 + np.tanh(2.0 * (r - case["R"]) / case["xi"]))
+
+
+def taylor_green_velocity(grid, u0):
+    """Taylor-Green vortex of the Taylor-Green case (Sec. 3.4) with period = the domain side
+    (arguments 2 pi x / n): u = u0 sin X cos Y cos Z, v = -u0 cos X sin Y cos Z, w = 0."""
+    x, y, z = cell_coords(grid)
+    X, Y, Z = (2 * np.pi * x / grid[0], 2 * np.pi * y / grid[1], 2 * np.pi * z / grid[2])
+    u = np.zeros((3,) + x.shape)
+    u[0] = u0 * np.sin(X) * np.cos(Y) * np.cos(Z)
+    u[1] = -u0 * np.cos(X) * np.sin(Y) * np.cos(Z)
+    return u
+
+
+def taylor_green_pressure(grid, u0, p0=CS2, rho0=1.0):
+    """Its pressure: p = p0 + rho0 u0^2 / 16 (cos 2X + cos 2Y)(cos 2Z + 2)."""
+    x, y, z = cell_coords(grid)
+    X, Y, Z = (2 * np.pi * x / grid[0], 2 * np.pi * y / grid[1], 2 * np.pi * z / grid[2])
+    return p0 + rho0 * u0 * u0 / 16.0 * (np.cos(2 * X) + np.cos(2 * Y)) * (np.cos(2 * Z) + 2.0)
