@@ -223,6 +223,7 @@ def run_ours(args):
     small = run_small_2d(lbm, torch, stream, args, world)
     rt = run_rayleigh_taylor(lbm, torch, stream, args, world)
     bubbles = run_batched_bubbles(lbm, torch, stream, args, world)
+    tgv = run_taylor_green(lbm, torch, stream, args, world)
 
     out = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(t_df / args.steps * 1e3, 5), "higher_is_better": True,
@@ -244,10 +245,12 @@ def run_ours(args):
            "droplet2d_64": small,
            "rayleigh_taylor_128x128x512": rt,
            "batched_rising_bubbles": bubbles,
+           "taylor_green_256": tgv,
            "sum_phi_drift": {"df": drift, "fd": fd_drift, "steps": args.warmup + args.steps}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"], out["accuracy"] = run_cpu_baseline(lbm, grid, w, params, phi0, cells, args)
         out["accuracy"]["rayleigh_taylor_32x32x128"] = run_rt_accuracy(lbm)
+        out["accuracy"]["taylor_green_64"] = run_tgv_accuracy(lbm)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -321,6 +324,72 @@ def run_rayleigh_taylor(lbm, torch, stream, args, world):
         out[name] = {"value": round(v, 1), "ms_per_step": round(secs / steps * 1e3, 5), "bytes_per_cell": bpc,
                      "hbm_frac": round(bpc * cells / (secs / steps) / 1e9 / peak, 4),
                      "speedup_vs_fp32": round(v / fp32, 4), "sum_phi_change": m1 - m0}
+    return out
+
+
+def tgv_fields(w):
+    grid = w["grid"]
+    return (I.droplet_phi(grid, w["R"], w["xi"]), I.taylor_green_velocity(grid, w["u0"]),
+            I.taylor_green_pressure(grid, w["u0"]))
+
+
+def run_taylor_green(lbm, torch, stream, args, world):
+    """Droplet breakup in a Taylor-Green vortex at 256^3 (periodic, u0 = 0.04, Re = 1000, We = 20,
+    R = 32, initial pressure field): the difference-free step in FP16 storage (the workload's)
+    and FP32, device-timed over steps / 5 steps."""
+    w = I.WORKLOADS["taylor_green_256"]
+    grid = w["grid"]
+    cells = grid[0] * grid[1] * grid[2]
+    phi0, u0, p = tgv_fields(w)
+    steps = max(args.steps // 5, 1)
+    peak = measured_peak_hbm()[0]
+    out = {"unit": "MLUPS", "steps": steps, "warmup": args.warmup,
+           "config": "D3Q19 256^3 periodic, u0=0.04, Re=1000, We=20, droplet R=32 at the centre, xi=4, "
+                     "Taylor-Green pressure field, arguments 2 pi x / 256"}
+    fp32 = None
+    for name, storage, bpc in (("fp16", lbm.LBM_STORAGE_FP16, BYTES_PER_CELL_16), ("fp32", 0, BYTES_PER_CELL["df"])):
+        g = lbm.Lattice(grid, 19, stream=stream.cuda_stream, storage=storage, tau_f=w["tau_f"], tau_g=w["tau_g"],
+                        M=w["M"], xi=w["xi"], sigma=w["sigma"])
+        g.init_phi(phi0, u0, p=p)
+        m0 = g.mass()[0]
+        g.step(args.warmup)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(world)
+        ev0.record(stream)
+        g.step(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        secs = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, world)
+        m1 = g.mass()[0]
+        g.close()
+        v = aggregate_mlups(cells, steps, secs, world)
+        out[name] = {"value": round(v, 1), "ms_per_step": round(secs / steps * 1e3, 5), "bytes_per_cell": bpc,
+                     "hbm_frac": round(bpc * cells / (secs / steps) / 1e9 / peak, 4), "sum_phi_change": m1 - m0}
+    out["fp16_speedup_vs_fp32"] = round(out["fp16"]["value"] / out["fp32"]["value"], 4)
+    return out
+
+
+def run_tgv_accuracy(lbm):
+    """The 64^3 copy of the Taylor-Green breakup case after 200 steps against the FP64 oracle."""
+    import oracle
+    w = I.WORKLOADS["taylor_green_64"]
+    phi0, u0, p = tgv_fields(w)
+    params = dict(tau_f=w["tau_f"], tau_g=w["tau_g"], M=w["M"], xi=w["xi"], sigma=w["sigma"])
+    ref = oracle.Oracle(19, w["grid"], **params)
+    ref.init_phi(phi0, u0, p=p)
+    ref.step(200)
+    phi_o, p_o, u_o = ref.moments()
+    out = {"steps": 200}
+    for name, storage in (("fp32", 0), ("fp16", lbm.LBM_STORAGE_FP16), ("bf16", lbm.LBM_STORAGE_BF16)):
+        g = lbm.Lattice(w["grid"], 19, storage=storage, **params)
+        g.init_phi(phi0, u0, p=p)
+        g.step(200)
+        phi_g, p_g, u_g = g.moments()
+        g.close()
+        out[name] = {"max_abs_phi": float(np.abs(phi_g - phi_o).max()),
+                     "rel_l2_u": float(np.linalg.norm(u_g - u_o) / np.linalg.norm(u_o)),
+                     "max_abs_p": float(np.abs(p_g - p_o).max())}
     return out
 
 

@@ -115,6 +115,15 @@ int lbm_create(lbm_ctx **out, const int grid[3], int lattice, double tau_f, doub
  */
 int lbm_init_phi(lbm_ctx *ctx, const double *phi0, const double *u0, double p0);
 
+/*
+ * lbm_init_phi with the pressure of f^eq given per cell: p (host FP64, nx*ny*nz, every value
+ * > 0 and finite) replaces the uniform p0, which remains the reference level the f storage is
+ * shifted by (take the mean pressure). The initial condition of the Taylor-Green case of
+ * Sec. 3.4 includes such a field; without it the vortex starts out of balance and launches an
+ * acoustic transient. p = NULL is lbm_init_phi. Synchronous.
+ */
+int lbm_init_fields(lbm_ctx *ctx, const double *phi0, const double *u0, const double *p, double p0);
+
 /* Advance n >= 0 time steps (asynchronous on the handle's stream). Whole multiples of
  * opts.graph_steps are replayed from CUDA graphs the handle captures on first use; the rest
  * are launched directly. Both give bit-identical results. */

@@ -18,7 +18,8 @@ constexpr int kAuxBX = 32, kAuxBY = 4;
 // ---------------------------------------------------------------------------------------
 template <int Q, int S>
 __global__ void init_kernel(const Params P, int z0, const double* __restrict__ phi0s,
-                            const double* __restrict__ u0s, double p0, void* __restrict__ fg) {
+                            const double* __restrict__ u0s, const double* __restrict__ ps, double p0,
+                            void* __restrict__ fg) {
     const int x = blockIdx.x * kAuxBX + threadIdx.x;
     const int y = blockIdx.y * kAuxBY + threadIdx.y;
     const int zl = blockIdx.z;
@@ -53,6 +54,7 @@ __global__ void init_kernel(const Params P, int z0, const double* __restrict__ p
     const size_t slab = (size_t)nzs * P.nxy;
     const int lu = zl * P.nxy + y * P.nx + x;
     const double u[3] = {u0s ? u0s[lu] : 0.0, u0s ? u0s[slab + lu] : 0.0, u0s ? u0s[2 * slab + lu] : 0.0};
+    const double pc = ps ? ps[lu] : p0;
     const double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     const double sg = P.sigma_d * gn;
     const double trc = (double)Lat<Q>::D - (n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
@@ -68,7 +70,7 @@ __global__ void init_kernel(const Params P, int z0, const double* __restrict__ p
         const double eg = Lat<Q>::cx(i) * gx + Lat<Q>::cy(i) * gy + Lat<Q>::cz(i) * gz;
         const double gam = 3.0 * eu + 4.5 * eu * eu - 1.5 * u2;
         const double pis = sg * ((double)Lat<Q>::e2(i) - en * en - trc / 3.0);
-        const double fstar = t * (3.0 * p0 + rho * gam - 4.5 * pis);
+        const double fstar = t * (3.0 * pc + rho * gam - 4.5 * pis);
         const double gstar = t * (phi * (1.0 + gam) + P.tau_phi_d * es) - t * (P.tau_phi_d - 0.5) * eg;
         fsum += fstar;
         gsum += gstar;
@@ -80,9 +82,9 @@ __global__ void init_kernel(const Params P, int z0, const double* __restrict__ p
 }
 
 cudaError_t launch_init(const Params& P, int z0, int nzs, const double* phi0s, const double* u0s,
-                        double p0, void* fg, cudaStream_t s) {
+                        const double* ps, double p0, void* fg, cudaStream_t s) {
     const dim3 grid((P.nx + kAuxBX - 1) / kAuxBX, (P.ny + kAuxBY - 1) / kAuxBY, nzs), block(kAuxBX, kAuxBY);
-#define LBM_INIT(Q, S) init_kernel<Q, S><<<grid, block, 0, s>>>(P, z0, phi0s, u0s, p0, fg)
+#define LBM_INIT(Q, S) init_kernel<Q, S><<<grid, block, 0, s>>>(P, z0, phi0s, u0s, ps, p0, fg)
     if (P.Q == 9) {
         if (P.storage == STORE_F16) LBM_INIT(9, STORE_F16);
         else if (P.storage == STORE_BF16) LBM_INIT(9, STORE_BF16);

@@ -305,10 +305,17 @@ int lbm::set_ctx_storage(lbm_ctx* c, int storage) {
 extern "C" {
 
 int lbm_init_phi(lbm_ctx* c, const double* phi0, const double* u0, double p0) {
+    return lbm_init_fields(c, phi0, u0, nullptr, p0);
+}
+
+int lbm_init_fields(lbm_ctx* c, const double* phi0, const double* u0, const double* p, double p0) {
     int rc = check_ctx(c);
     if (rc) return rc;
     if (!phi0) return set_error(c, LBM_EINVAL, "phi0 is NULL");
     if (!(p0 > 0) || !is_fin(p0)) return set_error(c, LBM_EINVAL, "p0 must be > 0 and finite");
+    if (p)
+        for (long long k = 0; k < c->P.N; ++k)
+            if (!(p[k] > 0) || !is_fin(p[k])) return set_error(c, LBM_EINVAL, "p[%lld] = %g must be > 0 and finite", k, p[k]);
     Params& P = c->P;
     P.w0d = p0 * 3.0;  // w0 = p0 / cs^2: the level the f storage is shifted by
     P.w0 = (float)P.w0d;
@@ -325,12 +332,13 @@ int lbm_init_phi(lbm_ctx* c, const double* phi0, const double* u0, double p0) {
     P.phi_ref_fx = (mean >= 0.5) ? (1 << 30) : 0;
     drop_graphs(c);  // captured steps carry the old parameters
     const size_t nxy = (size_t)P.nxy;
-    const int per_z = 1 + (u0 ? 3 : 0);
+    const int per_z = 1 + (u0 ? 3 : 0) + (p ? 1 : 0);
     const int nzs = slab_depth(c, per_z, 2);
-    rc = ensure_staging(c, (size_t)(nzs + 2 + (u0 ? 3 * nzs : 0)) * nxy);
+    rc = ensure_staging(c, (size_t)(nzs + 2 + (u0 ? 3 * nzs : 0) + (p ? nzs : 0)) * nxy);
     if (rc) return rc;
     double* phis = c->staging;
     double* us = c->staging + (size_t)(nzs + 2) * nxy;
+    double* ps = us + (u0 ? (size_t)3 * nzs * nxy : 0);
     for (int z0 = 0; z0 < P.nz; z0 += nzs) {
         const int n = (z0 + nzs <= P.nz) ? nzs : P.nz - z0;
         // phi0 planes z0-1 .. z0+n (periodic images at the ends); D2Q9 has only its one plane
@@ -345,7 +353,11 @@ int lbm_init_phi(lbm_ctx* c, const double* phi0, const double* u0, double p0) {
             for (int a = 0; a < 3; ++a)
                 LBM_CUDA(c, cudaMemcpyAsync(us + (size_t)a * n * nxy, u0 + (size_t)a * P.N + (size_t)z0 * nxy,
                                             (size_t)n * nxy * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-        LBM_CUDA(c, lbm::launch_init(P, z0, n, phis, u0 ? us : nullptr, p0, c->fg[c->cur], c->stream));
+        if (p)
+            LBM_CUDA(c, cudaMemcpyAsync(ps, p + (size_t)z0 * nxy, (size_t)n * nxy * sizeof(double),
+                                        cudaMemcpyHostToDevice, c->stream));
+        LBM_CUDA(c, lbm::launch_init(P, z0, n, phis, u0 ? us : nullptr, p ? ps : nullptr, p0, c->fg[c->cur],
+                                     c->stream));
         c->launches += 1;
     }
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));

@@ -55,9 +55,10 @@ cudaError_t launch_fd_phi(const Params& P, const void* fg_in, float* phi_fd, cud
 
 // Initial populations for z in [z0, z0 + nzs). phi0s holds planes z0-1 .. z0+nzs of phi0
 // (periodic images for the two halo planes; D2Q9 holds the single plane at index 1);
-// u0s (or nullptr) holds 3 x nzs planes of the velocity for the slab.
+// u0s (or nullptr) holds 3 x nzs planes of the velocity for the slab; ps (or nullptr) holds nzs
+// planes of the pressure, else the pressure is p0 everywhere.
 cudaError_t launch_init(const Params& P, int z0, int nzs, const double* phi0s, const double* u0s,
-                        double p0, void* fg, cudaStream_t s);
+                        const double* ps, double p0, void* fg, cudaStream_t s);
 
 // Macroscopic fields for z in [z0, z0 + nzs) written as FP64 planes of the slab into out:
 // plane k of field j at out + (j * nzs) * nxy ... see the field order in the definition.

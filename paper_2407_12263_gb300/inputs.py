@@ -88,6 +88,24 @@ WORKLOADS["rayleigh_taylor_128x128x512"] = _rayleigh_taylor((128, 128, 512))
 WORKLOADS["rayleigh_taylor_32x32x128"] = _rayleigh_taylor((32, 32, 128))
 
 
+def _taylor_green(n, Re=1000.0, We=20.0, u0=0.04, xi=4.0, M=0.02):
+    """Droplet breakup in a Taylor-Green vortex (Sec. 3.4): periodic cube of side L0 = n, droplet
+    of radius n/8 at the centre (phi = 0 inside), density and viscosity ratio 1,
+    Re = rho0 u0 L0 / eta, We = rho0 u0^2 D / sigma (D = n/4), tau_f = eta / (rho0 cs^2)."""
+    R = n / 8.0
+    eta = u0 * n / Re
+    return dict(Q=19, grid=(n, n, n), R=R, xi=xi, sigma=u0 * u0 * 2 * R / We, tau_f=3.0 * eta, tau_g=0.8, M=M,
+                rho_ratio=1.0, mu_ratio=1.0, body_force=(0.0, 0.0, 0.0), u0=u0, steps=int(n / u0),
+                time_scale=n / u0)
+
+
+# Taylor-Green breakup: 256^3, u0 = 0.04, Re = 1000, R = 32, We = 20 (16-bit storage in the
+# benchmark), and a 64^3 copy with the same dimensionless groups for the comparison with the
+# oracle.
+WORKLOADS["taylor_green_256"] = _taylor_green(256)
+WORKLOADS["taylor_green_64"] = _taylor_green(64)
+
+
 def rayleigh_taylor_phi(grid, amplitude, xi):
     """Heavy fluid (phi = 1) above the plane z = (nz - 1)/2 + A cos(2 pi (x + 1/2)/nx) cos(2 pi (y + 1/2)/ny)."""
     nx, ny, nz = grid

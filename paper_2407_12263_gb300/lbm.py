@@ -54,6 +54,7 @@ SIGNATURES = [
     ("lbm_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), _ip, ctypes.c_int] + [ctypes.c_double] * 7
      + [_dp, ctypes.POINTER(lbm_opts)]),
     ("lbm_init_phi", ctypes.c_int, [ctypes.c_void_p, _dp, _dp, ctypes.c_double]),
+    ("lbm_init_fields", ctypes.c_int, [ctypes.c_void_p, _dp, _dp, _dp, ctypes.c_double]),
     ("lbm_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("lbm_moments", ctypes.c_int, [ctypes.c_void_p, _dp, _dp, _dp]),
     ("lbm_gradients", ctypes.c_int, [ctypes.c_void_p, _dp, _dp]),
@@ -139,6 +140,10 @@ def lbm_create(grid, lattice, tau_f, tau_g, M, xi, sigma, rho_ratio=1.0, mu_rati
 
 def lbm_init_phi(h, phi0, u0=None, p0=1.0 / 3.0):
     _check(h, load().lbm_init_phi(h, _ptr(phi0), _ptr(u0), p0))
+
+
+def lbm_init_fields(h, phi0, u0=None, p=None, p0=1.0 / 3.0):
+    _check(h, load().lbm_init_fields(h, _ptr(phi0), _ptr(u0), _ptr(p), p0))
 
 
 def lbm_step(h, n):
@@ -323,10 +328,14 @@ class Lattice:
     def launch_count(self):
         return lbm_launch_count(self.h)
 
-    def init_phi(self, phi0, u0=None, p0=1.0 / 3.0):
+    def init_phi(self, phi0, u0=None, p0=1.0 / 3.0, p=None):
+        """Initial state; p (a pressure field, optional) replaces the uniform p0 in f^eq."""
         phi0 = np.ascontiguousarray(phi0, dtype=np.float64).reshape(self.shape)
         u0 = None if u0 is None else np.ascontiguousarray(u0, dtype=np.float64).reshape((3,) + self.shape)
-        lbm_init_phi(self.h, phi0, u0, p0)
+        if p is None:
+            lbm_init_phi(self.h, phi0, u0, p0)
+        else:
+            lbm_init_fields(self.h, phi0, u0, np.ascontiguousarray(p, dtype=np.float64).reshape(self.shape), p0)
 
     def step(self, n=1):
         lbm_step(self.h, n)
