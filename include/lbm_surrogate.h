@@ -1,0 +1,98 @@
+/*
+ * lbm_surrogate.h -- a small 3D convolutional surrogate that fast-forwards the coarsened state
+ * of the difference-free conservative phase-field LBM (include/lbm.h), with the solver as its
+ * judge and fallback.
+ *
+ * The paper has no counterpart: it advances every step with the LBM. This part stands on its
+ * own. It is trained only on trajectories this solver generates. It has its own forward and
+ * backward kernels, and is checked against an FP64 restatement of the same network.
+ *
+ * The network. C = 5 field channels (phi, u, v, w, p), each normalised as (value - mean) / std.
+ * Four periodic 3x3x3 convolutions, 5 -> 32 -> 32 -> 32 -> 5 channels, ReLU after the first
+ * three; the prediction is input + output (a residual step). Convolutions accumulate in FP32;
+ * activations between layers are stored in FP16 (or FP32, for gradient checks). Weights are
+ * FP32 ([Cout][Cin][27] then bias [Cout] per layer, tap = 9 dz + 3 dy + dx for the input offset
+ * (dz-1, dy-1, dx-1)). Training minimises the mean squared error with Adam (0.9, 0.999, 1e-8).
+ *
+ * Arrays of fields are device FP32 [B][5][D][H][W], W fastest, owned by the caller.
+ * Every call returns an lbm_status; nothing throws. Calls on one network are asynchronous on
+ * its stream unless marked synchronous.
+ */
+#ifndef LBM_SURROGATE_H
+#define LBM_SURROGATE_H
+
+#include "lbm.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_net lbm_net;
+
+/* Create a network with seeded weights: He-normal (std sqrt(2 / (27 Cin))) drawn from a
+ * SplitMix64 stream started at `seed`, the last layer scaled by 0.1, biases 0.
+ * activations_fp16: 1 stores activations in FP16, 0 in FP32. stream: cudaStream_t or NULL (one
+ * the network owns). */
+int lbm_net_create(lbm_net **out, int activations_fp16, unsigned long long seed, void *stream);
+
+/* Number of FP32 parameters, and host copies of the parameters, of the gradients of the last
+ * lbm_net_gradients call, and into the parameters (synchronous). */
+long long lbm_net_param_count(const lbm_net *net);
+int lbm_net_get_params(lbm_net *net, float *host);
+int lbm_net_set_params(lbm_net *net, const float *host);
+int lbm_net_get_grads(lbm_net *net, float *host);
+
+/* y = x + net(x) for a batch on a grid (each extent >= 1). x and y may not alias. */
+int lbm_net_forward(lbm_net *net, const float *x, float *y, int batch, const int grid[3]);
+
+/* The loss mean((x + net(x) - target)^2) over every element of the batch into *loss
+ * (synchronous) and its gradients with respect to all parameters (kept on the device). */
+int lbm_net_gradients(lbm_net *net, const float *x, const float *target, int batch, const int grid[3], double *loss);
+
+/* One Adam step with learning rate lr from the gradients of the last lbm_net_gradients. */
+int lbm_net_adam(lbm_net *net, float lr);
+
+const char *lbm_net_last_error(const lbm_net *net);
+void lbm_net_destroy(lbm_net *net);
+
+/* The lattice side. factor f divides nx, ny, nz; the handle uses the difference-free scheme.
+ * lbm_coarse_fields: device out [5][nz/f][ny/f][nx/f] = block means over f^3 cells of phi, u,
+ * v, w and p as lbm_moments computes them. */
+int lbm_coarse_fields(lbm_ctx *ctx, int factor, float *out);
+
+/* Replace the state by the one lbm_init_fields builds from coarse fields (device [5][...] as
+ * above) upsampled trilinearly between coarse cell centres (periodic; clamped across walls),
+ * with p0 the reference pressure of the storage. sum phi is then set back exactly to its
+ * value before the call (the difference, in units of 2^-30, spread over the cells). */
+int lbm_restart_from_coarse(lbm_ctx *ctx, int factor, const float *coarse, double p0);
+
+typedef struct {
+    int accepted;       /* 1: the state holds the prediction advanced by judge_steps steps;
+                           0: it holds the LBM's own k steps from the starting state */
+    double mass_error;  /* |sum phi of the prediction - sum phi before| / sum phi before */
+    double relax_ratio; /* how fast the LBM moves phi right after the restart, relative to the
+                           rate the prediction implies (1 = consistent) */
+    double seconds_surrogate; /* host wall time of the jump, judge included */
+} lbm_jump_report;
+
+/*
+ * Fast-forward k steps with the surrogate, judged by the LBM:
+ *   1. coarsen the state by `factor`, normalise with mean_std (5 means, then 5 stds), predict,
+ *      denormalise;
+ *   2. reject if the prediction's sum phi is off by more than mass_tol (relative);
+ *   3. restart the lattice from the prediction with sum phi held exactly;
+ *   4. run judge_steps LBM steps and compare how far phi moves per step with the rate the
+ *      prediction implies (|phi_after - phi_restart| / judge_steps against
+ *      |phi_pred - phi_before| / k, coarse, L1, phi_restart the coarse phi right after the
+ *      restart); reject if the ratio exceeds relax_tol: a prediction whose phi, u and p do not
+ *      fit together relaxes fast;
+ *   5. on rejection restore the starting state and advance it k steps with the LBM.
+ * Synchronous. Needs 2x the state's device memory while it runs.
+ */
+int lbm_surrogate_jump(lbm_ctx *ctx, lbm_net *net, int factor, const float mean_std[10], int k, int judge_steps,
+                       double mass_tol, double relax_tol, lbm_jump_report *report);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -252,6 +252,7 @@ mass_finish(const double* __restrict__ partials, int n, double* __restrict__ res
         result[0] = (double)phi_sum / kPhiFx;
         result[1] = acc[0];
         result[2] = acc[1];
+        result[3] = __longlong_as_double(phi_sum);  // the exact integer sum, bit for bit
     }
 }
 

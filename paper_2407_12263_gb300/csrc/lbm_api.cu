@@ -16,6 +16,7 @@
 #include "lbm_ctx.h"
 #include "lbm_internal.h"
 #include "storage.cuh"
+#include "surrogate.h"
 
 using lbm::Params;
 
@@ -282,11 +283,59 @@ int lbm::create_ctx(lbm_ctx** out, const int grid[3], int lattice, double tau_f,
     if (rc == LBM_OK) {
         c->n_partials = lbm::mass_partials_needed(P);
         cudaError_t e = cudaMalloc(&c->partials, (size_t)3 * c->n_partials * sizeof(double));
-        if (e == cudaSuccess) e = cudaMalloc(&c->result, 3 * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&c->result, 4 * sizeof(double));
         if (e != cudaSuccess) rc = set_error(c, LBM_ENOMEM, "allocating reduction scratch failed: %s", cudaGetErrorString(e));
     }
     if (rc != LBM_OK) return fail(rc);
     *out = c;
+    return LBM_OK;
+}
+
+int lbm::ctx_error(lbm_ctx* c, int code, const char* msg) { return set_error(c, code, "%s", msg); }
+
+int lbm::ctx_check(lbm_ctx* c) { return check_ctx(c); }
+
+int lbm::ctx_mass_fixed(lbm_ctx* c, long long* sum) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!c->initialised) return set_error(c, LBM_ESTATE, "no state: call lbm_init_phi first");
+    LBM_CUDA(c, lbm::launch_mass(c->P, c->fg[c->cur], c->partials, c->n_partials, c->result, c->stream));
+    c->launches += 2;
+    double r[4];
+    LBM_CUDA(c, cudaMemcpyAsync(r, c->result, sizeof r, cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    std::memcpy(sum, &r[3], sizeof *sum);
+    return LBM_OK;
+}
+
+int lbm::ctx_restart_from_coarse(lbm_ctx* c, int f, const float* coarse, double p0) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    Params& P = c->P;
+    P.w0d = p0 * 3.0;
+    P.w0 = (float)P.w0d;
+    drop_graphs(c);
+    const size_t nxy = (size_t)P.nxy;
+    const int nzs = slab_depth(c, 5, 2);
+    rc = ensure_staging(c, (size_t)(nzs + 2 + 4 * nzs) * nxy);
+    if (rc) return rc;
+    double* phis = c->staging;
+    double* us = phis + (size_t)(nzs + 2) * nxy;
+    double* ps = us + (size_t)3 * nzs * nxy;
+    for (int z0 = 0; z0 < P.nz; z0 += nzs) {
+        const int n = (z0 + nzs <= P.nz) ? nzs : P.nz - z0;
+        LBM_CUDA(c, lbm::launch_upsample_slab(P, coarse, f, z0, n, phis, us, ps, c->stream));
+        LBM_CUDA(c, lbm::launch_init(P, z0, n, phis, us, ps, p0, c->fg[c->cur], c->stream));
+        c->launches += 2;
+    }
+    c->initialised = true;
+    c->version += 1;
+    return LBM_OK;
+}
+
+int lbm::ctx_adjust_phi(lbm_ctx* c, long long delta) {
+    LBM_CUDA(c, lbm::launch_adjust_phi(c->P, c->fg[c->cur], delta, c->stream));
+    c->launches += 1;
     return LBM_OK;
 }
 

@@ -45,4 +45,15 @@ int create_ctx(lbm_ctx** out, const int grid[3], int lattice, double tau_f, doub
 // lbm_set_pops, LBM_EINVAL if the buffers are too small for it).
 int set_ctx_storage(lbm_ctx* c, int storage);
 
+// Helpers of the surrogate entry points (lbm_surrogate.cu).
+int ctx_error(lbm_ctx* c, int code, const char* msg);
+int ctx_check(lbm_ctx* c);
+// The exact 64-bit sum of the fixed-point phi values of the propagated state. Synchronous.
+int ctx_mass_fixed(lbm_ctx* c, long long* sum);
+// Replace the state by the one lbm_init_fields builds from the coarse fields [5][nz/f][ny/f][nx/f]
+// (device FP32: phi, u, v, w, p) upsampled trilinearly; p0 = the storage reference pressure.
+int ctx_restart_from_coarse(lbm_ctx* c, int f, const float* coarse, double p0);
+// Add delta fixed-point units of phi, spread so that the sum changes by exactly delta.
+int ctx_adjust_phi(lbm_ctx* c, long long delta);
+
 }  // namespace lbm

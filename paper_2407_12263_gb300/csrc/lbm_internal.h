@@ -66,9 +66,10 @@ cudaError_t launch_init(const Params& P, int z0, int nzs, const double* phi0s, c
 cudaError_t launch_moments(const Params& P, int scheme, int z0, int nzs, const void* fg,
                            const float* phi_fd, int mask, double* out, cudaStream_t s);
 
-// sum phi, sum rho phi (FP64) and the count of non-finite stored populations.
+// sum phi, sum rho phi (FP64), the count of non-finite stored populations, and in result[3]
+// the bits of the exact 64-bit sum of the fixed-point phi values.
 cudaError_t launch_mass(const Params& P, const void* fg, double* partials, int n_partials,
-                        double* result /* 3 doubles */, cudaStream_t s);
+                        double* result /* 4 doubles */, cudaStream_t s);
 int mass_partials_needed(const Params& P);
 
 // All Q populations of the slab [z0, z0 + nzs) between the device storage and FP64 staging

@@ -1,0 +1,411 @@
+// lbm_surrogate.cu -- the surrogate entry points (include/lbm_surrogate.h): the network's
+// parameters and workspaces, its forward pass, gradients and Adam step (surrogate_kernels.cu),
+// and the judged jump of a lattice (surrogate_glue.cu for the field transfers).
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "../../include/lbm_surrogate.h"
+#include "lbm_ctx.h"
+#include "surrogate.h"
+
+using lbm::net::kFieldChannels;
+using lbm::net::kHidden;
+using lbm::net::kLayers;
+
+struct lbm_net {
+    int fp16;
+    cudaStream_t stream;
+    bool own_stream;
+    int cin[kLayers], cout[kLayers];
+    long long w_off[kLayers], b_off[kLayers], n_params;
+    float *params, *grads, *m, *v;   // device, n_params each
+    float* wt;                        // adjoint weights of one layer
+    int adam_step;
+    // workspace for (batch, voxels)
+    long long ws_elems;               // batch * voxels the workspace holds
+    void* x_t;                        // input in the activation type
+    void* h[kLayers - 1];             // hidden activations
+    float* d;                         // last layer's output [B][5]
+    float *ga, *gb;                   // gradient ping-pong [B][32]
+    double* partials;
+    int n_partials;
+    char err[512];
+};
+
+namespace {
+
+thread_local char g_net_error[512] = "no error";
+
+int nerr(lbm_net* n, int code, const char* fmt, ...) {
+    char* dst = n ? n->err : g_net_error;
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(dst, 512, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define LBM_NCUDA(n, call)                                                                      \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return nerr((n), e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA,          \
+                        "%s failed: %s", #call, cudaGetErrorString(e_));                        \
+    } while (0)
+
+void free_ws(lbm_net* n) {
+    cudaFree(n->x_t);
+    for (int l = 0; l < kLayers - 1; ++l) cudaFree(n->h[l]);
+    cudaFree(n->d);
+    cudaFree(n->ga);
+    cudaFree(n->gb);
+    cudaFree(n->partials);
+    n->x_t = nullptr;
+    for (int l = 0; l < kLayers - 1; ++l) n->h[l] = nullptr;
+    n->d = n->ga = n->gb = nullptr;
+    n->partials = nullptr;
+    n->ws_elems = 0;
+}
+
+void free_net(lbm_net* n) {
+    if (!n) return;
+    if (n->stream) cudaStreamSynchronize(n->stream);
+    free_ws(n);
+    cudaFree(n->params);
+    cudaFree(n->grads);
+    cudaFree(n->m);
+    cudaFree(n->v);
+    cudaFree(n->wt);
+    if (n->own_stream && n->stream) cudaStreamDestroy(n->stream);
+    delete n;
+}
+
+int ensure_ws(lbm_net* n, int batch, long long vox) {
+    const long long e = (long long)batch * vox;
+    const size_t act = n->fp16 ? 2 : 4;
+    if (e <= n->ws_elems) return LBM_OK;
+    free_ws(n);
+    LBM_NCUDA(n, cudaMalloc(&n->x_t, (size_t)e * kFieldChannels * act));
+    for (int l = 0; l < kLayers - 1; ++l) LBM_NCUDA(n, cudaMalloc(&n->h[l], (size_t)e * kHidden * act));
+    LBM_NCUDA(n, cudaMalloc(&n->d, (size_t)e * kFieldChannels * sizeof(float)));
+    LBM_NCUDA(n, cudaMalloc(&n->ga, (size_t)e * kHidden * sizeof(float)));
+    LBM_NCUDA(n, cudaMalloc(&n->gb, (size_t)e * kHidden * sizeof(float)));
+    n->n_partials = lbm::net::loss_blocks(e * kFieldChannels);
+    LBM_NCUDA(n, cudaMalloc(&n->partials, (size_t)n->n_partials * sizeof(double)));
+    n->ws_elems = e;
+    return LBM_OK;
+}
+
+// SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number generators", 2014)
+// and a Box-Muller normal from two of its outputs.
+struct SplitMix64 {
+    unsigned long long s;
+    unsigned long long next() {
+        unsigned long long z = (s += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+    double uniform() { return ((next() >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+    double normal() {
+        const double u1 = uniform(), u2 = uniform();
+        return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+    }
+};
+
+int check_grid(lbm_net* n, int batch, const int grid[3]) {
+    if (!grid || batch < 1 || grid[0] < 1 || grid[1] < 1 || grid[2] < 1)
+        return nerr(n, LBM_EINVAL, "need batch >= 1 and a grid of positive extents");
+    return LBM_OK;
+}
+
+// Forward pass keeping the activations; the last layer's output in n->d.
+int forward_keep(lbm_net* n, const float* x, int batch, const int grid[3]) {
+    const int D = grid[2], H = grid[1], W = grid[0];
+    const long long vox = (long long)D * H * W;
+    int rc = ensure_ws(n, batch, vox);
+    if (rc) return rc;
+    LBM_NCUDA(n, lbm::net::cast_to(x, n->x_t, n->fp16, (long long)batch * kFieldChannels * vox, n->stream));
+    const void* in = n->x_t;
+    for (int l = 0; l < kLayers; ++l) {
+        const bool last = l == kLayers - 1;
+        void* out = last ? (void*)n->d : n->h[l];
+        LBM_NCUDA(n, lbm::net::conv_forward(in, n->fp16, n->cin[l], n->params + n->w_off[l], n->params + n->b_off[l], out,
+                                            last ? 0 : n->fp16, n->cout[l], last ? 0 : 1, batch, D, H, W, n->stream));
+        in = out;
+    }
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_net_create(lbm_net** out, int activations_fp16, unsigned long long seed, void* stream) {
+    if (!out) return nerr(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    lbm_net* n = new (std::nothrow) lbm_net();
+    if (!n) return nerr(nullptr, LBM_ENOMEM, "host allocation failed");
+    std::snprintf(n->err, sizeof n->err, "no error");
+    n->fp16 = activations_fp16 ? 1 : 0;
+    auto fail = [&](int code) {
+        std::snprintf(g_net_error, sizeof g_net_error, "%s", n->err);
+        free_net(n);
+        return code;
+    };
+    if (stream) {
+        n->stream = (cudaStream_t)stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&n->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return fail(nerr(n, LBM_ECUDA, "cudaStreamCreate failed: %s", cudaGetErrorString(e)));
+        n->own_stream = true;
+    }
+    const int chans[kLayers + 1] = {kFieldChannels, kHidden, kHidden, kHidden, kFieldChannels};
+    long long off = 0;
+    for (int l = 0; l < kLayers; ++l) {
+        n->cin[l] = chans[l];
+        n->cout[l] = chans[l + 1];
+        n->w_off[l] = off;
+        off += (long long)n->cout[l] * n->cin[l] * 27;
+        n->b_off[l] = off;
+        off += n->cout[l];
+    }
+    n->n_params = off;
+    std::vector<float> h((size_t)off, 0.f);
+    SplitMix64 rng{seed};
+    for (int l = 0; l < kLayers; ++l) {
+        const double sd = std::sqrt(2.0 / (27.0 * n->cin[l])) * (l == kLayers - 1 ? 0.1 : 1.0);
+        for (long long i = 0; i < (long long)n->cout[l] * n->cin[l] * 27; ++i) h[n->w_off[l] + i] = (float)(sd * rng.normal());
+    }
+    const size_t bytes = (size_t)off * sizeof(float);
+    cudaError_t e = cudaMalloc(&n->params, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&n->grads, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&n->m, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&n->v, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&n->wt, (size_t)kHidden * kHidden * 27 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(n->params, h.data(), bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(n->grads, 0, bytes);
+    if (e == cudaSuccess) e = cudaMemset(n->m, 0, bytes);
+    if (e == cudaSuccess) e = cudaMemset(n->v, 0, bytes);
+    if (e != cudaSuccess) return fail(nerr(n, LBM_ENOMEM, "allocating the network failed: %s", cudaGetErrorString(e)));
+    *out = n;
+    return LBM_OK;
+}
+
+long long lbm_net_param_count(const lbm_net* n) { return n ? n->n_params : 0; }
+
+int lbm_net_get_params(lbm_net* n, float* host) {
+    if (!n || !host) return nerr(n, LBM_EINVAL, "null argument");
+    LBM_NCUDA(n, cudaMemcpyAsync(host, n->params, (size_t)n->n_params * sizeof(float), cudaMemcpyDeviceToHost, n->stream));
+    LBM_NCUDA(n, cudaStreamSynchronize(n->stream));
+    return LBM_OK;
+}
+
+int lbm_net_set_params(lbm_net* n, const float* host) {
+    if (!n || !host) return nerr(n, LBM_EINVAL, "null argument");
+    LBM_NCUDA(n, cudaMemcpyAsync(n->params, host, (size_t)n->n_params * sizeof(float), cudaMemcpyHostToDevice, n->stream));
+    LBM_NCUDA(n, cudaStreamSynchronize(n->stream));
+    return LBM_OK;
+}
+
+int lbm_net_get_grads(lbm_net* n, float* host) {
+    if (!n || !host) return nerr(n, LBM_EINVAL, "null argument");
+    LBM_NCUDA(n, cudaMemcpyAsync(host, n->grads, (size_t)n->n_params * sizeof(float), cudaMemcpyDeviceToHost, n->stream));
+    LBM_NCUDA(n, cudaStreamSynchronize(n->stream));
+    return LBM_OK;
+}
+
+int lbm_net_forward(lbm_net* n, const float* x, float* y, int batch, const int grid[3]) {
+    if (!n || !x || !y) return nerr(n, LBM_EINVAL, "null argument");
+    int rc = check_grid(n, batch, grid);
+    if (rc) return rc;
+    rc = forward_keep(n, x, batch, grid);
+    if (rc) return rc;
+    const long long e = (long long)batch * kFieldChannels * grid[0] * grid[1] * grid[2];
+    LBM_NCUDA(n, lbm::net::residual(x, n->d, y, e, n->stream));
+    return LBM_OK;
+}
+
+int lbm_net_gradients(lbm_net* n, const float* x, const float* target, int batch, const int grid[3], double* loss) {
+    if (!n || !x || !target) return nerr(n, LBM_EINVAL, "null argument");
+    int rc = check_grid(n, batch, grid);
+    if (rc) return rc;
+    rc = forward_keep(n, x, batch, grid);
+    if (rc) return rc;
+    const int D = grid[2], H = grid[1], W = grid[0];
+    const long long vox = (long long)D * H * W, e = (long long)batch * kFieldChannels * vox;
+    LBM_NCUDA(n, lbm::net::loss_and_grad(x, n->d, target, n->ga, e, n->partials, n->stream));
+    LBM_NCUDA(n, cudaMemsetAsync(n->grads, 0, (size_t)n->n_params * sizeof(float), n->stream));
+    float* g = n->ga;      // gradient of the current layer's output
+    float* other = n->gb;
+    for (int l = kLayers - 1; l >= 0; --l) {
+        const void* h_in = (l == 0) ? n->x_t : n->h[l - 1];
+        LBM_NCUDA(n, lbm::net::conv_wgrad(g, n->cout[l], h_in, n->fp16, n->cin[l], n->grads + n->w_off[l],
+                                          n->grads + n->b_off[l], batch, D, H, W, n->stream));
+        if (l == 0) break;
+        LBM_NCUDA(n, lbm::net::flip_transpose(n->params + n->w_off[l], n->cout[l], n->cin[l], n->wt, n->stream));
+        LBM_NCUDA(n, lbm::net::conv_forward(g, 0, n->cout[l], n->wt, nullptr, other, 0, n->cin[l], 0, batch, D, H, W,
+                                            n->stream));
+        LBM_NCUDA(n, lbm::net::relu_mask(other, n->h[l - 1], n->fp16, (long long)batch * n->cin[l] * vox, n->stream));
+        float* t = g;
+        g = other;
+        other = t;
+    }
+    if (loss) {
+        std::vector<double> part((size_t)n->n_partials);
+        LBM_NCUDA(n, cudaMemcpyAsync(part.data(), n->partials, part.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                     n->stream));
+        LBM_NCUDA(n, cudaStreamSynchronize(n->stream));
+        double s = 0.0;
+        for (double v : part) s += v;
+        *loss = s / (double)e;
+    }
+    return LBM_OK;
+}
+
+int lbm_net_adam(lbm_net* n, float lr) {
+    if (!n) return nerr(nullptr, LBM_EINVAL, "null network");
+    if (!(lr > 0.f)) return nerr(n, LBM_EINVAL, "lr must be > 0");
+    n->adam_step += 1;
+    LBM_NCUDA(n, lbm::net::adam(n->params, n->grads, n->m, n->v, n->n_params, lr, n->adam_step, n->stream));
+    return LBM_OK;
+}
+
+const char* lbm_net_last_error(const lbm_net* n) { return n ? n->err : g_net_error; }
+
+void lbm_net_destroy(lbm_net* n) { free_net(n); }
+
+int lbm_coarse_fields(lbm_ctx* c, int f, float* out) {
+    int rc = lbm::ctx_check(c);
+    if (rc) return rc;
+    if (!out || f < 1 || c->P.nx % f || c->P.ny % f || c->P.nz % f)
+        return lbm::ctx_error(c, LBM_EINVAL, "factor must divide nx, ny and nz, and out may not be NULL");
+    if (!c->initialised) return lbm::ctx_error(c, LBM_ESTATE, "no state: call lbm_init_phi first");
+    if (c->scheme != LBM_SCHEME_DIFFERENCE_FREE) return lbm::ctx_error(c, LBM_EINVAL, "coarse fields need the difference-free scheme");
+    cudaError_t e = lbm::launch_coarsen(c->P, c->fg[c->cur], f, out, c->stream);
+    if (e != cudaSuccess) return lbm::ctx_error(c, LBM_ECUDA, cudaGetErrorString(e));
+    c->launches += 1;
+    return LBM_OK;
+}
+
+int lbm_restart_from_coarse(lbm_ctx* c, int f, const float* coarse, double p0) {
+    int rc = lbm::ctx_check(c);
+    if (rc) return rc;
+    if (!coarse || f < 1 || c->P.nx % f || c->P.ny % f || c->P.nz % f)
+        return lbm::ctx_error(c, LBM_EINVAL, "factor must divide nx, ny and nz, and coarse may not be NULL");
+    if (!(p0 > 0) || !std::isfinite(p0)) return lbm::ctx_error(c, LBM_EINVAL, "p0 must be > 0 and finite");
+    if (!c->initialised) return lbm::ctx_error(c, LBM_ESTATE, "no state to hold the mass of: call lbm_init_phi first");
+    long long before = 0, after = 0;
+    rc = lbm::ctx_mass_fixed(c, &before);
+    if (rc) return rc;
+    rc = lbm::ctx_restart_from_coarse(c, f, coarse, p0);
+    if (rc) return rc;
+    rc = lbm::ctx_mass_fixed(c, &after);
+    if (rc) return rc;
+    if (after != before) {
+        rc = lbm::ctx_adjust_phi(c, before - after);
+        if (rc) return rc;
+    }
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return lbm::ctx_error(c, LBM_ECUDA, cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+int lbm_surrogate_jump(lbm_ctx* c, lbm_net* n, int f, const float mean_std[10], int k, int judge_steps, double mass_tol,
+                       double relax_tol, lbm_jump_report* rep) {
+    int rc = lbm::ctx_check(c);
+    if (rc) return rc;
+    if (!n || !mean_std || !rep || k < 1 || judge_steps < 1 || !(mass_tol >= 0) || !(relax_tol > 0))
+        return lbm::ctx_error(c, LBM_EINVAL, "need a network, mean_std, a report, k >= 1, judge_steps >= 1 and tolerances");
+    if (f < 1 || c->P.nx % f || c->P.ny % f || c->P.nz % f)
+        return lbm::ctx_error(c, LBM_EINVAL, "factor must divide nx, ny and nz");
+    if (!c->initialised) return lbm::ctx_error(c, LBM_ESTATE, "no state: call lbm_init_phi first");
+    const auto t0 = std::chrono::steady_clock::now();
+    std::memset(rep, 0, sizeof *rep);
+    const int grid_c[3] = {c->P.nx / f, c->P.ny / f, c->P.nz / f};
+    const long long nc = (long long)grid_c[0] * grid_c[1] * grid_c[2];
+    const size_t fbytes = (size_t)5 * nc * sizeof(float);
+    float *in = nullptr, *xin = nullptr, *yout = nullptr, *pred = nullptr;
+    void* backup = nullptr;
+    struct Frees {
+        float **a, **b, **cc, **d;
+        void** e;
+        ~Frees() {
+            cudaFree(*a);
+            cudaFree(*b);
+            cudaFree(*cc);
+            cudaFree(*d);
+            cudaFree(*e);
+        }
+    } frees{&in, &xin, &yout, &pred, &backup};
+    auto cu = [&](cudaError_t e) { return e == cudaSuccess ? LBM_OK : lbm::ctx_error(c, LBM_ECUDA, cudaGetErrorString(e)); };
+    if ((rc = cu(cudaMalloc(&in, fbytes))) || (rc = cu(cudaMalloc(&xin, fbytes))) || (rc = cu(cudaMalloc(&yout, fbytes))) ||
+        (rc = cu(cudaMalloc(&pred, fbytes))) || (rc = cu(cudaMalloc(&backup, c->fg_bytes))))
+        return rc;
+    const int saved_cur = c->cur;
+    const lbm::Params saved_P = c->P;
+    if ((rc = cu(cudaMemcpyAsync(backup, c->fg[c->cur], c->fg_bytes, cudaMemcpyDeviceToDevice, c->stream)))) return rc;
+    long long m_before = 0;
+    if ((rc = lbm::ctx_mass_fixed(c, &m_before))) return rc;
+    // 1. predict
+    if ((rc = lbm_coarse_fields(c, f, in))) return rc;
+    if ((rc = cu(cudaStreamSynchronize(c->stream)))) return rc;
+    if ((rc = cu(lbm::launch_normalize(in, xin, nc, mean_std, +1, n->stream)))) return rc;
+    if ((rc = lbm_net_forward(n, xin, yout, 1, grid_c))) return lbm::ctx_error(c, rc, lbm_net_last_error(n));
+    if ((rc = cu(lbm::launch_normalize(yout, pred, nc, mean_std, -1, n->stream)))) return rc;
+    if ((rc = cu(cudaStreamSynchronize(n->stream)))) return rc;
+    std::vector<float> h_in((size_t)nc), h_pred((size_t)nc);
+    if ((rc = cu(cudaMemcpy(h_in.data(), in, (size_t)nc * sizeof(float), cudaMemcpyDeviceToHost)))) return rc;
+    if ((rc = cu(cudaMemcpy(h_pred.data(), pred, (size_t)nc * sizeof(float), cudaMemcpyDeviceToHost)))) return rc;
+    // 2. mass of the prediction
+    const double mass_before = (double)m_before / 1073741824.0;
+    double mass_pred = 0.0, jump = 0.0;
+    for (long long i = 0; i < nc; ++i) {
+        mass_pred += (double)h_pred[i] * f * f * f;
+        jump += std::fabs((double)h_pred[i] - (double)h_in[i]);
+    }
+    rep->mass_error = std::fabs(mass_pred - mass_before) / std::fabs(mass_before);
+    bool accept = rep->mass_error <= mass_tol;
+    // 3-4. restart and judge
+    if (accept) {
+        if ((rc = lbm_restart_from_coarse(c, f, pred, saved_P.w0d / 3.0))) return rc;
+        // phi right after the restart (it differs from the prediction by the smoothing of
+        // upsampling and block means, which is not motion) and judge_steps steps later
+        std::vector<float> h_r((size_t)nc), h_after((size_t)nc);
+        if ((rc = lbm_coarse_fields(c, f, in))) return rc;
+        if ((rc = cu(cudaStreamSynchronize(c->stream)))) return rc;
+        if ((rc = cu(cudaMemcpy(h_r.data(), in, (size_t)nc * sizeof(float), cudaMemcpyDeviceToHost)))) return rc;
+        if ((rc = lbm_step(c, judge_steps))) return rc;
+        if ((rc = lbm_coarse_fields(c, f, in))) return rc;
+        if ((rc = cu(cudaStreamSynchronize(c->stream)))) return rc;
+        if ((rc = cu(cudaMemcpy(h_after.data(), in, (size_t)nc * sizeof(float), cudaMemcpyDeviceToHost)))) return rc;
+        double relax = 0.0;
+        for (long long i = 0; i < nc; ++i) relax += std::fabs((double)h_after[i] - (double)h_r[i]);
+        const double rate_pred = jump / k, rate_after = relax / judge_steps;
+        rep->relax_ratio = rate_pred > 0 ? rate_after / rate_pred : (rate_after > 0 ? INFINITY : 0.0);
+        accept = rep->relax_ratio <= relax_tol;
+    }
+    // 5. fallback
+    if (!accept) {
+        c->P = saved_P;
+        c->cur = saved_cur;
+        if ((rc = cu(cudaMemcpyAsync(c->fg[c->cur], backup, c->fg_bytes, cudaMemcpyDeviceToDevice, c->stream)))) return rc;
+        c->initialised = true;
+        c->version += 1;
+        if ((rc = lbm_step(c, k))) return rc;
+        if ((rc = cu(cudaStreamSynchronize(c->stream)))) return rc;
+    }
+    rep->accepted = accept ? 1 : 0;
+    rep->seconds_surrogate = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return LBM_OK;
+}
+
+}  // extern "C"

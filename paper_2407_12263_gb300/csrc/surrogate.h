@@ -1,0 +1,49 @@
+// surrogate.h -- launchers of the convolutional surrogate's kernels (surrogate_kernels.cu) and
+// of the field transfers between the lattice and the coarse grid (surrogate_glue.cu).
+// Internal to the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+namespace net {
+
+constexpr int kFieldChannels = 5;  // phi, u, v, w, p
+constexpr int kHidden = 32;        // channels of the hidden layers
+constexpr int kLayers = 4;
+
+// Periodic 3x3x3 convolution of a batch [B][cin][D][H][W] into [B][cout][D][H][W]
+// (cout = 32 or 5), FP32 accumulation; inputs and outputs FP16 or FP32; relu on the output if
+// asked. bias may be NULL.
+cudaError_t conv_forward(const void* in, int in_fp16, int cin, const float* W, const float* bias, void* out, int out_fp16,
+                         int cout, int relu, int batch, int D, int H, int Wd, cudaStream_t s);
+// gW [cout][cin][27] += correlation of g [B][cout] with h [B][cin]; gb [cout] += sum of g.
+cudaError_t conv_wgrad(const float* g, int cout, const void* h, int h_fp16, int cin, float* gW, float* gb, int batch,
+                       int D, int H, int Wd, cudaStream_t s);
+// Wt [cin][cout][27] with the taps reversed: the adjoint convolution's weights.
+cudaError_t flip_transpose(const float* W, int cout, int cin, float* Wt, cudaStream_t s);
+cudaError_t relu_mask(float* g, const void* h, int h_fp16, long long n, cudaStream_t s);
+cudaError_t cast_to(const float* x, void* y, int fp16, long long n, cudaStream_t s);
+cudaError_t residual(const float* x, const float* d, float* y, long long n, cudaStream_t s);
+int loss_blocks(long long n);
+cudaError_t loss_and_grad(const float* x, const float* d, const float* target, float* g, long long n, double* partials,
+                          cudaStream_t s);
+cudaError_t adam(float* p, const float* g, float* m, float* v, long long n, float lr, int step, cudaStream_t s);
+
+}  // namespace net
+
+// Coarse fields [5][nz/f][ny/f][nx/f] (phi, u, v, w, p; means over f^3 cells of the macroscopic
+// fields of the difference-free scheme) of the propagated state fg.
+cudaError_t launch_coarsen(const Params& P, const void* fg, int factor, float* out, cudaStream_t s);
+// The staging of launch_init for the slab [z0, z0 + nzs) from coarse fields, trilinear between
+// coarse cell centres (periodic, clamped across walls): phi planes z0-1 .. z0+nzs, u, p.
+cudaError_t launch_upsample_slab(const Params& P, const float* coarse, int factor, int z0, int nzs, double* phis,
+                                 double* us, double* ps, cudaStream_t s);
+// Adds delta units (2^-30) of phi to the state, spread over the cells so that it sums exactly.
+cudaError_t launch_adjust_phi(const Params& P, void* fg, long long delta, cudaStream_t s);
+// (x - mean[c]) / std[c] per channel of [5][n] (dir = +1) or x std[c] + mean[c] (dir = -1).
+cudaError_t launch_normalize(const float* x, float* y, long long n, const float* mean_std, int dir, cudaStream_t s);
+
+}  // namespace lbm

@@ -42,6 +42,11 @@ class lbm_batch_opts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("graph_steps", ctypes.c_int)]
 
 
+class lbm_jump_report(ctypes.Structure):
+    _fields_ = [("accepted", ctypes.c_int), ("mass_error", ctypes.c_double), ("relax_ratio", ctypes.c_double),
+                ("seconds_surrogate", ctypes.c_double)]
+
+
 class LBMError(RuntimeError):
     def __init__(self, status, message):
         super().__init__(f"lbm status {status}: {message}")
@@ -80,6 +85,22 @@ SIGNATURES = [
     ("lbm_batch_cells", ctypes.c_longlong, [ctypes.c_void_p]),
     ("lbm_batch_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("lbm_batch_destroy", None, [ctypes.c_void_p]),
+    # include/lbm_surrogate.h
+    ("lbm_net_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_ulonglong, ctypes.c_void_p]),
+    ("lbm_net_param_count", ctypes.c_longlong, [ctypes.c_void_p]),
+    ("lbm_net_get_params", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
+    ("lbm_net_set_params", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
+    ("lbm_net_get_grads", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
+    ("lbm_net_forward", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, _ip]),
+    ("lbm_net_gradients", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, _ip, _dp]),
+    ("lbm_net_adam", ctypes.c_int, [ctypes.c_void_p, ctypes.c_float]),
+    ("lbm_net_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+    ("lbm_net_destroy", None, [ctypes.c_void_p]),
+    ("lbm_coarse_fields", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    ("lbm_restart_from_coarse", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_double]),
+    ("lbm_surrogate_jump", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
+                                          ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                          ctypes.POINTER(lbm_jump_report)]),
 ]
 
 _lib = None
@@ -413,3 +434,81 @@ class Batch:
     @property
     def cells(self):
         return lbm_batch_cells(self.b)
+
+
+# ---------------------------------------------------------------- the surrogate (include/lbm_surrogate.h)
+_fp = ctypes.POINTER(ctypes.c_float)
+
+
+def _ncheck(n, status):
+    if status != LBM_OK:
+        msg = load().lbm_net_last_error(n)
+        raise LBMError(status, msg.decode() if msg else "")
+    return status
+
+
+class Net:
+    """The convolutional surrogate. Field batches are device FP32 arrays [B][5][D][H][W] passed
+    by pointer (e.g. torch tensors' data_ptr()); grids are (nx, ny, nz)."""
+
+    def __init__(self, fp16=True, seed=0, stream=None):
+        h = ctypes.c_void_p()
+        _ncheck(None, load().lbm_net_create(ctypes.byref(h), int(bool(fp16)), int(seed), stream))
+        self.n = h
+
+    def close(self):
+        if getattr(self, "n", None):
+            load().lbm_net_destroy(self.n)
+            self.n = None
+
+    __del__ = close
+
+    @property
+    def param_count(self):
+        return int(load().lbm_net_param_count(self.n))
+
+    def get_params(self):
+        a = np.empty(self.param_count, dtype=np.float32)
+        _ncheck(self.n, load().lbm_net_get_params(self.n, a.ctypes.data_as(_fp)))
+        return a
+
+    def set_params(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        assert a.size == self.param_count
+        _ncheck(self.n, load().lbm_net_set_params(self.n, a.ctypes.data_as(_fp)))
+
+    def get_grads(self):
+        a = np.empty(self.param_count, dtype=np.float32)
+        _ncheck(self.n, load().lbm_net_get_grads(self.n, a.ctypes.data_as(_fp)))
+        return a
+
+    def forward(self, x_ptr, y_ptr, batch, grid):
+        g = (ctypes.c_int * 3)(*[int(v) for v in grid])
+        _ncheck(self.n, load().lbm_net_forward(self.n, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), int(batch), g))
+
+    def gradients(self, x_ptr, t_ptr, batch, grid):
+        g = (ctypes.c_int * 3)(*[int(v) for v in grid])
+        loss = ctypes.c_double()
+        _ncheck(self.n, load().lbm_net_gradients(self.n, ctypes.c_void_p(x_ptr), ctypes.c_void_p(t_ptr), int(batch), g,
+                                                 ctypes.byref(loss)))
+        return loss.value
+
+    def adam(self, lr):
+        _ncheck(self.n, load().lbm_net_adam(self.n, float(lr)))
+
+
+def lbm_coarse_fields(h, factor, out_ptr):
+    _check(h, load().lbm_coarse_fields(h, int(factor), ctypes.c_void_p(out_ptr)))
+
+
+def lbm_restart_from_coarse(h, factor, coarse_ptr, p0=1.0 / 3.0):
+    _check(h, load().lbm_restart_from_coarse(h, int(factor), ctypes.c_void_p(coarse_ptr), float(p0)))
+
+
+def lbm_surrogate_jump(h, net, factor, mean_std, k, judge_steps, mass_tol, relax_tol):
+    ms = (ctypes.c_float * 10)(*[float(v) for v in mean_std])
+    rep = lbm_jump_report()
+    _check(h, load().lbm_surrogate_jump(h, net.n, int(factor), ms, int(k), int(judge_steps), float(mass_tol),
+                                        float(relax_tol), ctypes.byref(rep)))
+    return {"accepted": bool(rep.accepted), "mass_error": rep.mass_error, "relax_ratio": rep.relax_ratio,
+            "seconds": rep.seconds_surrogate}
