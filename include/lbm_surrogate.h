@@ -12,7 +12,8 @@
  * three; the prediction is input + output (a residual step). Convolutions accumulate in FP32;
  * activations between layers are stored in FP16 (or FP32, for gradient checks). Weights are
  * FP32 ([Cout][Cin][27] then bias [Cout] per layer, tap = 9 dz + 3 dy + dx for the input offset
- * (dz-1, dy-1, dx-1)). Training minimises the mean squared error with Adam (0.9, 0.999, 1e-8).
+ * (dz-1, dy-1, dx-1)). Training minimises the (channel-weighted) mean squared error with Adam
+ * (0.9, 0.999, 1e-8).
  *
  * Arrays of fields are device FP32 [B][5][D][H][W], W fastest, owned by the caller.
  * Every call returns an lbm_status; nothing throws. Calls on one network are asynchronous on
@@ -45,7 +46,11 @@ int lbm_net_get_grads(lbm_net *net, float *host);
 /* y = x + net(x) for a batch on a grid (each extent >= 1). x and y may not alias. */
 int lbm_net_forward(lbm_net *net, const float *x, float *y, int batch, const int grid[3]);
 
-/* The loss mean((x + net(x) - target)^2) over every element of the batch into *loss
+/* Per-channel weights w_c >= 0 of the loss (default 1): fields whose changes are small next to
+ * their spread (the velocity over a short jump) can be weighted up. */
+int lbm_net_set_loss_weights(lbm_net *net, const float w[5]);
+
+/* The loss mean(w_c (x + net(x) - target)^2) over every element of the batch into *loss
  * (synchronous) and its gradients with respect to all parameters (kept on the device). */
 int lbm_net_gradients(lbm_net *net, const float *x, const float *target, int batch, const int grid[3], double *loss);
 

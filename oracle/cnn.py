@@ -9,7 +9,8 @@ network the CUDA library implements so that its forward pass and its gradients c
       conv(h; W, b)[o, z, y, x] = b[o] + sum_{c, dz, dy, dx} W[o, c, dz, dy, dx] h[c, z+dz-1, y+dy-1, x+dx-1]
       with indices taken modulo the grid (periodic padding), W of shape [Cout][Cin][3][3][3];
   prediction: x + h_L (a residual step);
-  loss: mean over every element of (prediction - target)^2.
+  loss: mean over every element of w_c (prediction - target)^2, w_c the weight of the element's
+  channel (1 unless given).
 
 Everything is FP64; a library routine (numpy roll, tensordot) serves each convolution term.
 """
@@ -58,12 +59,14 @@ def forward(x, weights):
     return x + h, pre
 
 
-def loss_and_gradients(x, target, weights):
+def loss_and_gradients(x, target, weights, channel_weights=None):
     """Mean-squared loss of the prediction and its gradients [(gW, gb), ...] for one sample."""
     pred, pre = forward(x, weights)
     diff = pred - target
-    loss = float((diff * diff).mean())
-    g = 2.0 * diff / diff.size          # d loss / d h_L (the residual adds x, which has no weights)
+    w = np.ones(x.shape[0]) if channel_weights is None else np.asarray(channel_weights, dtype=np.float64)
+    wd = w[:, None, None, None] * diff
+    loss = float((wd * diff).mean())
+    g = 2.0 * wd / diff.size            # d loss / d h_L (the residual adds x, which has no weights)
     grads = [None] * len(weights)
     for l in range(len(weights) - 1, -1, -1):
         h_in = x if l == 0 else np.maximum(pre[l - 1], 0.0)

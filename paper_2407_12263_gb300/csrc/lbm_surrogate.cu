@@ -29,6 +29,7 @@ struct lbm_net {
     float *params, *grads, *m, *v;   // device, n_params each
     float* wt;                        // adjoint weights of one layer
     int adam_step;
+    float loss_w[kFieldChannels];     // per-channel weights of the loss
     // workspace for (batch, voxels)
     long long ws_elems;               // batch * voxels the workspace holds
     void* x_t;                        // input in the activation type
@@ -156,6 +157,7 @@ int lbm_net_create(lbm_net** out, int activations_fp16, unsigned long long seed,
     if (!n) return nerr(nullptr, LBM_ENOMEM, "host allocation failed");
     std::snprintf(n->err, sizeof n->err, "no error");
     n->fp16 = activations_fp16 ? 1 : 0;
+    for (int c = 0; c < kFieldChannels; ++c) n->loss_w[c] = 1.f;
     auto fail = [&](int code) {
         std::snprintf(g_net_error, sizeof g_net_error, "%s", n->err);
         free_net(n);
@@ -242,7 +244,7 @@ int lbm_net_gradients(lbm_net* n, const float* x, const float* target, int batch
     if (rc) return rc;
     const int D = grid[2], H = grid[1], W = grid[0];
     const long long vox = (long long)D * H * W, e = (long long)batch * kFieldChannels * vox;
-    LBM_NCUDA(n, lbm::net::loss_and_grad(x, n->d, target, n->ga, e, n->partials, n->stream));
+    LBM_NCUDA(n, lbm::net::loss_and_grad(x, n->d, target, n->ga, e, vox, n->loss_w, n->partials, n->stream));
     LBM_NCUDA(n, cudaMemsetAsync(n->grads, 0, (size_t)n->n_params * sizeof(float), n->stream));
     float* g = n->ga;      // gradient of the current layer's output
     float* other = n->gb;
@@ -268,6 +270,14 @@ int lbm_net_gradients(lbm_net* n, const float* x, const float* target, int batch
         for (double v : part) s += v;
         *loss = s / (double)e;
     }
+    return LBM_OK;
+}
+
+int lbm_net_set_loss_weights(lbm_net* n, const float w[5]) {
+    if (!n || !w) return nerr(n, LBM_EINVAL, "null argument");
+    for (int c = 0; c < kFieldChannels; ++c)
+        if (!(w[c] >= 0.f) || !std::isfinite(w[c])) return nerr(n, LBM_EINVAL, "loss weights must be finite and >= 0");
+    for (int c = 0; c < kFieldChannels; ++c) n->loss_w[c] = w[c];
     return LBM_OK;
 }
 

@@ -28,8 +28,9 @@ cudaError_t relu_mask(float* g, const void* h, int h_fp16, long long n, cudaStre
 cudaError_t cast_to(const float* x, void* y, int fp16, long long n, cudaStream_t s);
 cudaError_t residual(const float* x, const float* d, float* y, long long n, cudaStream_t s);
 int loss_blocks(long long n);
-cudaError_t loss_and_grad(const float* x, const float* d, const float* target, float* g, long long n, double* partials,
-                          cudaStream_t s);
+// loss sum_i w_c(i) (x + d - target)_i^2 / n and its gradient; w: 5 host weights, vox: cells per channel.
+cudaError_t loss_and_grad(const float* x, const float* d, const float* target, float* g, long long n, long long vox,
+                          const float* w, double* partials, cudaStream_t s);
 cudaError_t adam(float* p, const float* g, float* m, float* v, long long n, float lr, int step, cudaStream_t s);
 
 }  // namespace net

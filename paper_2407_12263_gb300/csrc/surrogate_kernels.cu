@@ -180,16 +180,20 @@ __global__ void residual_kernel(const float* __restrict__ x, const float* __rest
         y[i] = x[i] + d[i];
 }
 
-// diff = x + d - target; g = 2 diff / n; per-block partial sums of diff^2 (FP64).
+// diff = x + d - target; loss term w_c diff^2 and its gradient g = 2 w_c diff / n, with w_c the
+// weight of the element's channel (elements [B][5][vox]); per-block partial sums (FP64).
 __global__ void loss_kernel(const float* __restrict__ x, const float* __restrict__ d, const float* __restrict__ target,
-                            float* __restrict__ g, long long n, double* __restrict__ partials) {
+                            float* __restrict__ g, long long n, long long vox, float w0, float w1, float w2, float w3,
+                            float w4, double* __restrict__ partials) {
     __shared__ double red[256 / 32];
+    const float w[kFieldChannels] = {w0, w1, w2, w3, w4};
     double acc = 0.0;
     const float scale = (float)(2.0 / (double)n);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float wc = w[(i / vox) % kFieldChannels];
         const float diff = x[i] + d[i] - target[i];
-        g[i] = scale * diff;
-        acc += (double)diff * (double)diff;
+        g[i] = scale * wc * diff;
+        acc += (double)wc * (double)diff * (double)diff;
     }
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -284,9 +288,9 @@ cudaError_t residual(const float* x, const float* d, float* y, long long n, cuda
 
 int loss_blocks(long long n) { return (int)ew_blocks(n); }
 
-cudaError_t loss_and_grad(const float* x, const float* d, const float* target, float* g, long long n, double* partials,
-                          cudaStream_t s) {
-    loss_kernel<<<ew_blocks(n), 256, 0, s>>>(x, d, target, g, n, partials);
+cudaError_t loss_and_grad(const float* x, const float* d, const float* target, float* g, long long n, long long vox,
+                          const float* w, double* partials, cudaStream_t s) {
+    loss_kernel<<<ew_blocks(n), 256, 0, s>>>(x, d, target, g, n, vox, w[0], w[1], w[2], w[3], w[4], partials);
     return cudaGetLastError();
 }
 

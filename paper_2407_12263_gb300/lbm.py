@@ -93,6 +93,7 @@ SIGNATURES = [
     ("lbm_net_get_grads", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
     ("lbm_net_forward", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, _ip]),
     ("lbm_net_gradients", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, _ip, _dp]),
+    ("lbm_net_set_loss_weights", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
     ("lbm_net_adam", ctypes.c_int, [ctypes.c_void_p, ctypes.c_float]),
     ("lbm_net_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("lbm_net_destroy", None, [ctypes.c_void_p]),
@@ -492,6 +493,10 @@ class Net:
         _ncheck(self.n, load().lbm_net_gradients(self.n, ctypes.c_void_p(x_ptr), ctypes.c_void_p(t_ptr), int(batch), g,
                                                  ctypes.byref(loss)))
         return loss.value
+
+    def set_loss_weights(self, w):
+        a = (ctypes.c_float * 5)(*[float(v) for v in w])
+        _ncheck(self.n, load().lbm_net_set_loss_weights(self.n, a))
 
     def adam(self, lr):
         _ncheck(self.n, load().lbm_net_adam(self.n, float(lr)))

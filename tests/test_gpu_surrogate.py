@@ -46,8 +46,13 @@ def _dev(a):
     return torch.tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
 
 
+def _net(fp16, seed):
+    """A network on torch's current stream, the stream that writes its input tensors."""
+    return lbm.Net(fp16=fp16, seed=seed, stream=torch.cuda.current_stream().cuda_stream)
+
+
 def _random_net(fp16, seed=3):
-    net = lbm.Net(fp16=fp16, seed=seed)
+    net = _net(fp16, seed)
     p = net.get_params()
     rng = np.random.default_rng(seed)
     p += rng.normal(0, 0.01, p.size).astype(np.float32)  # non-zero biases as well
@@ -71,9 +76,11 @@ def test_forward_matches_oracle(fp16, tol):
         assert np.abs(y[b] - want).max() <= tol * scale
 
 
-@pytest.mark.parametrize("fp16,tol", [(False, 1e-5), (True, 2e-2)])
-def test_gradients_match_oracle(fp16, tol):
+@pytest.mark.parametrize("fp16,tol,cw", [(False, 1e-5, None), (True, 2e-2, None), (False, 1e-5, (1, 30, 30, 30, 0.5))])
+def test_gradients_match_oracle(fp16, tol, cw):
     net, weights = _random_net(fp16, seed=5)
+    if cw is not None:
+        net.set_loss_weights(cw)
     rng = np.random.default_rng(12)
     grid = (8, 8, 8)
     x = rng.normal(0, 1, (2, 5, 8, 8, 8)).astype(np.float32)
@@ -81,7 +88,7 @@ def test_gradients_match_oracle(fp16, tol):
     xd, td = _dev(x), _dev(t)  # held: the library reads them after this line
     loss = net.gradients(xd.data_ptr(), td.data_ptr(), 2, grid)
     g = unpack(net.get_grads().astype(np.float64))
-    losses, grads = zip(*(cnn.loss_and_gradients(x[b].astype(np.float64), t[b].astype(np.float64), weights)
+    losses, grads = zip(*(cnn.loss_and_gradients(x[b].astype(np.float64), t[b].astype(np.float64), weights, cw)
                           for b in range(2)))
     assert loss == pytest.approx(np.mean(losses), rel=tol)
     for l in range(4):
@@ -120,6 +127,7 @@ def _tgv_lattice(c, stream=None):
 def _coarse(g, f):
     n = g.grid
     out = torch.empty((5, n[2] // f, n[1] // f, n[0] // f), device="cuda")
+    torch.cuda.synchronize()
     lbm.lbm_coarse_fields(g.h, f, out.data_ptr())
     torch.cuda.synchronize()
     return out
@@ -155,7 +163,7 @@ def test_restart_holds_sum_phi_exactly():
 def test_wild_prediction_is_rejected_and_the_lbm_takes_over():
     c = _tgv_case(16, 0.04, 4.0, 20.0)
     g, twin = _tgv_lattice(c), _tgv_lattice(c)
-    net = lbm.Net(fp16=True, seed=1)
+    net = _net(True, 1)
     net.set_params(np.random.default_rng(0).normal(0, 1.0, net.param_count).astype(np.float32))
     rep = lbm.lbm_surrogate_jump(g.h, net, 2, [0.5, 0, 0, 0, 1 / 3, 0.5, 0.04, 0.04, 0.04, 1e-4], 16, 4, 1e-3, 4.0)
     assert not rep["accepted"]
@@ -189,7 +197,7 @@ def test_trained_surrogate_beats_persistence_and_is_accepted():
     std = X.std(dim=(0, 2, 3, 4)) + 1e-12
     norm = lambda a: ((a - mean[None, :, None, None, None]) / std[None, :, None, None, None]).contiguous()
     Xn, Yn = norm(X), norm(Y)
-    net = lbm.Net(fp16=True, seed=7)
+    net = _net(True, 7)
     grid_c = (n // f,) * 3
     gen = torch.Generator(device="cpu").manual_seed(0)
     first = None

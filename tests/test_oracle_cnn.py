@@ -50,12 +50,12 @@ def test_conv_of_a_delta_is_the_flipped_kernel():
         assert out[0, (1 - dz) % 5, (1 - dy) % 5, (1 - dx) % 5] == W[0, 0, dz, dy, dx]
 
 
-@pytest.mark.parametrize("chans", [(2, 3, 2), (3, 4, 4, 3)])
-def test_gradients_match_finite_differences(chans):
+@pytest.mark.parametrize("chans,cw", [((2, 3, 2), None), ((3, 4, 4, 3), None), ((3, 4, 3), (0.5, 2.0, 7.0))])
+def test_gradients_match_finite_differences(chans, cw):
     rng = np.random.default_rng(7)
     grid = (3, 4, 3)
     weights, x, t = _net(rng, chans, grid)
-    loss, grads = cnn.loss_and_gradients(x, t, weights)
+    loss, grads = cnn.loss_and_gradients(x, t, weights, cw)
     eps = 1e-6
     for l, (W, b) in enumerate(weights):
         for idx in [(0, 0, 1, 1, 1), (W.shape[0] - 1, W.shape[1] - 1, 0, 2, 1), (0, W.shape[1] - 1, 2, 0, 0)]:
@@ -63,14 +63,14 @@ def test_gradients_match_finite_differences(chans):
             Wm = [(w.copy(), bb.copy()) for w, bb in weights]
             Wp[l][0][idx] += eps
             Wm[l][0][idx] -= eps
-            fd = (cnn.loss_and_gradients(x, t, Wp)[0] - cnn.loss_and_gradients(x, t, Wm)[0]) / (2 * eps)
+            fd = (cnn.loss_and_gradients(x, t, Wp, cw)[0] - cnn.loss_and_gradients(x, t, Wm, cw)[0]) / (2 * eps)
             assert grads[l][0][idx] == pytest.approx(fd, rel=1e-5, abs=1e-9)
         for o in range(b.shape[0]):
             Wp = [(w.copy(), bb.copy()) for w, bb in weights]
             Wm = [(w.copy(), bb.copy()) for w, bb in weights]
             Wp[l][1][o] += eps
             Wm[l][1][o] -= eps
-            fd = (cnn.loss_and_gradients(x, t, Wp)[0] - cnn.loss_and_gradients(x, t, Wm)[0]) / (2 * eps)
+            fd = (cnn.loss_and_gradients(x, t, Wp, cw)[0] - cnn.loss_and_gradients(x, t, Wm, cw)[0]) / (2 * eps)
             assert grads[l][1][o] == pytest.approx(fd, rel=1e-5, abs=1e-9)
 
 
