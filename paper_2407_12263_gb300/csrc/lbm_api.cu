@@ -112,15 +112,8 @@ int capture_graph(lbm_ctx* c, int start) {
     return LBM_OK;
 }
 
-// FP16 storage: f deviations scaled by 2^12 and g deviations by 2^10 (exact power-of-two
-// scaling) so that they sit in the normal FP16 range; 1 for FP32 and BF16.
-void apply_storage(Params& P, int storage) {
-    P.storage = storage;
-    P.scale_f = (storage == lbm::STORE_F16) ? 4096.0f : 1.0f;
-    P.scale_g = (storage == lbm::STORE_F16) ? 1024.0f : 1.0f;
-    P.inv_scale_f = 1.0f / P.scale_f;
-    P.inv_scale_g = 1.0f / P.scale_g;
-}
+// The storage of the moving pairs (the FP16 scaling is a compile-time constant of Store<S>).
+void apply_storage(Params& P, int storage) { P.storage = storage; }
 
 int check_ctx(lbm_ctx* c) {
     if (!c) return set_error(nullptr, LBM_EINVAL, "null handle");

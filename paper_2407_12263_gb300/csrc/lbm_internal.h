@@ -35,7 +35,6 @@ struct Params {
     int general;           // 1 if any of drho, G, mu_m1, walls is non-zero (selects the full kernels)
     int storage;           // enum StorageKind of the moving planes
     int walls;             // bit 0: walls at x = -1/2 and nx - 1/2; bit 1: the same in y; bit 2: in z
-    float scale_f, scale_g, inv_scale_f, inv_scale_g;  // FP16 storage scaling (powers of two)
     // FP64 copies for the initialisation and the conversions to and from FP64 host arrays
     double w0d, phi_ref_d, tau_phi_d, sigma_d, four_over_delta_d, drho_d, rho2_d;
 };

@@ -163,6 +163,29 @@ def test_long_horizon_within_fp64_sensitivity():
     assert gpu.mass()[0] == s0
 
 
+def test_3d_copy_5000_steps_within_fp64_sensitivity():
+    """The 32^3 copy of the 3D workload (R = 6, xi = 4, same tau and sigma) over 5000 steps: the GPU
+    stays within a few times the distance between the oracle and the oracle restarted from its
+    own state perturbed by 3e-8 (relative), the size of FP32 rounding; sum phi does not change."""
+    w = I.WORKLOADS["droplet3d_128"]
+    grid = (32, 32, 32)
+    phi0 = I.droplet_phi(grid, 6.0, w["xi"])
+    gpu, ref = _pair(19, grid, phi0)
+    pert = O.Oracle(19, grid, w["tau_f"], w["tau_g"], w["M"], w["xi"], w["sigma"])
+    f, g = ref.get_pops()
+    rng = np.random.default_rng(1)
+    pert.set_pops(f * (1 + 3e-8 * rng.standard_normal(f.shape)), g * (1 + 3e-8 * rng.standard_normal(g.shape)))
+    s0 = gpu.mass()[0]
+    for o in (gpu, ref, pert):
+        o.step(5000)
+    (phi_g, _, u_g), (phi_o, _, u_o), (phi_p, _, u_p) = gpu.moments(), ref.moments(), pert.moments()
+    self_phi = np.abs(phi_p - phi_o).max()
+    self_u = np.linalg.norm(u_p - u_o) / np.linalg.norm(u_o)
+    assert np.abs(phi_g - phi_o).max() <= max(PHI_TOL, 5 * self_phi)
+    assert np.linalg.norm(u_g - u_o) / np.linalg.norm(u_o) <= max(U_REL_TOL, 5 * self_u)
+    assert gpu.mass()[0] == s0
+
+
 # ---------------------------------------------------------------- full size
 def test_full_size_droplet_parity():
     """The 3D workload at its full size (D3Q19, 128^3, R = 24, xi = 4) in the launch configuration
