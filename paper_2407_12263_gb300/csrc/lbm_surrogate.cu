@@ -28,6 +28,8 @@ struct lbm_net {
     long long w_off[kLayers], b_off[kLayers], n_params;
     float *params, *grads, *m, *v;   // device, n_params each
     float* wt;                        // adjoint weights of one layer
+    __half* wimg;                     // FP16 tensor-core weight image of one 32 -> 32 layer
+    int* tc_err;                      // set by the tensor-core kernel if a wait timed out
     int adam_step;
     float loss_w[kFieldChannels];     // per-channel weights of the loss
     // workspace for (batch, voxels)
@@ -85,6 +87,8 @@ void free_net(lbm_net* n) {
     cudaFree(n->m);
     cudaFree(n->v);
     cudaFree(n->wt);
+    cudaFree(n->wimg);
+    cudaFree(n->tc_err);
     if (n->own_stream && n->stream) cudaStreamDestroy(n->stream);
     delete n;
 }
@@ -128,6 +132,18 @@ int check_grid(lbm_net* n, int batch, const int grid[3]) {
     return LBM_OK;
 }
 
+// The layers run on the tensor cores with FP16 activations (channels zero-padded to 32); the FP32
+// mode stays on the CUDA-core kernels, whose results the gradient checks compare with FP64 at 1e-5.
+bool on_tensor_cores(const lbm_net* n) { return n->fp16 != 0; }
+
+// A timeout of the tensor-core kernel, read at a point where the stream has been synchronised.
+int check_tc(lbm_net* n) {
+    int flag = 0;
+    LBM_NCUDA(n, cudaMemcpy(&flag, n->tc_err, sizeof flag, cudaMemcpyDeviceToHost));
+    if (flag) return nerr(n, LBM_ETIMEOUT, "a tensor-core convolution timed out waiting for its MMAs");
+    return LBM_OK;
+}
+
 // Forward pass keeping the activations; the last layer's output in n->d.
 int forward_keep(lbm_net* n, const float* x, int batch, const int grid[3]) {
     const int D = grid[2], H = grid[1], W = grid[0];
@@ -139,8 +155,14 @@ int forward_keep(lbm_net* n, const float* x, int batch, const int grid[3]) {
     for (int l = 0; l < kLayers; ++l) {
         const bool last = l == kLayers - 1;
         void* out = last ? (void*)n->d : n->h[l];
-        LBM_NCUDA(n, lbm::net::conv_forward(in, n->fp16, n->cin[l], n->params + n->w_off[l], n->params + n->b_off[l], out,
-                                            last ? 0 : n->fp16, n->cout[l], last ? 0 : 1, batch, D, H, W, n->stream));
+        if (on_tensor_cores(n)) {
+            LBM_NCUDA(n, lbm::net::weight_image(n->params + n->w_off[l], n->cout[l], n->cin[l], n->wimg, n->stream));
+            LBM_NCUDA(n, lbm::net::conv32_tc(in, 1, n->cin[l], 1.0f, n->wimg, n->params + n->b_off[l], out, last ? 0 : 1,
+                                             n->cout[l], last ? 0 : 1, batch, D, H, W, n->tc_err, n->stream));
+        } else {
+            LBM_NCUDA(n, lbm::net::conv_forward(in, n->fp16, n->cin[l], n->params + n->w_off[l], n->params + n->b_off[l],
+                                                out, last ? 0 : n->fp16, n->cout[l], last ? 0 : 1, batch, D, H, W, n->stream));
+        }
         in = out;
     }
     return LBM_OK;
@@ -193,6 +215,9 @@ int lbm_net_create(lbm_net** out, int activations_fp16, unsigned long long seed,
     if (e == cudaSuccess) e = cudaMalloc(&n->m, bytes);
     if (e == cudaSuccess) e = cudaMalloc(&n->v, bytes);
     if (e == cudaSuccess) e = cudaMalloc(&n->wt, (size_t)kHidden * kHidden * 27 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&n->wimg, lbm::net::weight_image_bytes());
+    if (e == cudaSuccess) e = cudaMalloc(&n->tc_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(n->tc_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(n->params, h.data(), bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(n->grads, 0, bytes);
     if (e == cudaSuccess) e = cudaMemset(n->m, 0, bytes);
@@ -208,7 +233,7 @@ int lbm_net_get_params(lbm_net* n, float* host) {
     if (!n || !host) return nerr(n, LBM_EINVAL, "null argument");
     LBM_NCUDA(n, cudaMemcpyAsync(host, n->params, (size_t)n->n_params * sizeof(float), cudaMemcpyDeviceToHost, n->stream));
     LBM_NCUDA(n, cudaStreamSynchronize(n->stream));
-    return LBM_OK;
+    return check_tc(n);
 }
 
 int lbm_net_set_params(lbm_net* n, const float* host) {
@@ -248,14 +273,26 @@ int lbm_net_gradients(lbm_net* n, const float* x, const float* target, int batch
     LBM_NCUDA(n, cudaMemsetAsync(n->grads, 0, (size_t)n->n_params * sizeof(float), n->stream));
     float* g = n->ga;      // gradient of the current layer's output
     float* other = n->gb;
+    const float grad_scale = std::ldexp(1.0f, std::ilogb((double)e));  // the power of two nearest below e
     for (int l = kLayers - 1; l >= 0; --l) {
         const void* h_in = (l == 0) ? n->x_t : n->h[l - 1];
-        LBM_NCUDA(n, lbm::net::conv_wgrad(g, n->cout[l], h_in, n->fp16, n->cin[l], n->grads + n->w_off[l],
-                                          n->grads + n->b_off[l], batch, D, H, W, n->stream));
+        if (on_tensor_cores(n))
+            LBM_NCUDA(n, lbm::net::wgrad32_tc(g, n->cout[l], grad_scale, h_in, n->fp16, n->cin[l], n->grads + n->w_off[l],
+                                              n->grads + n->b_off[l], batch, D, H, W, n->tc_err, n->stream));
+        else
+            LBM_NCUDA(n, lbm::net::conv_wgrad(g, n->cout[l], h_in, n->fp16, n->cin[l], n->grads + n->w_off[l],
+                                              n->grads + n->b_off[l], batch, D, H, W, n->stream));
         if (l == 0) break;
         LBM_NCUDA(n, lbm::net::flip_transpose(n->params + n->w_off[l], n->cout[l], n->cin[l], n->wt, n->stream));
-        LBM_NCUDA(n, lbm::net::conv_forward(g, 0, n->cout[l], n->wt, nullptr, other, 0, n->cin[l], 0, batch, D, H, W,
-                                            n->stream));
+        if (on_tensor_cores(n)) {
+            LBM_NCUDA(n, lbm::net::weight_image(n->wt, n->cin[l], n->cout[l], n->wimg, n->stream));
+            // the loss gradient is 2 diff / (elements): scale it back to order one before FP16
+            LBM_NCUDA(n, lbm::net::conv32_tc(g, 0, n->cout[l], grad_scale, n->wimg, nullptr, other, 0, n->cin[l], 0, batch,
+                                             D, H, W, n->tc_err, n->stream));
+        } else {
+            LBM_NCUDA(n, lbm::net::conv_forward(g, 0, n->cout[l], n->wt, nullptr, other, 0, n->cin[l], 0, batch, D, H, W,
+                                                n->stream));
+        }
         LBM_NCUDA(n, lbm::net::relu_mask(other, n->h[l - 1], n->fp16, (long long)batch * n->cin[l] * vox, n->stream));
         float* t = g;
         g = other;
@@ -269,8 +306,10 @@ int lbm_net_gradients(lbm_net* n, const float* x, const float* target, int batch
         double s = 0.0;
         for (double v : part) s += v;
         *loss = s / (double)e;
+    } else {
+        LBM_NCUDA(n, cudaStreamSynchronize(n->stream));
     }
-    return LBM_OK;
+    return check_tc(n);
 }
 
 int lbm_net_set_loss_weights(lbm_net* n, const float w[5]) {
@@ -372,6 +411,7 @@ int lbm_surrogate_jump(lbm_ctx* c, lbm_net* n, int f, const float mean_std[10], 
     if ((rc = lbm_net_forward(n, xin, yout, 1, grid_c))) return lbm::ctx_error(c, rc, lbm_net_last_error(n));
     if ((rc = cu(lbm::launch_normalize(yout, pred, nc, mean_std, -1, n->stream)))) return rc;
     if ((rc = cu(cudaStreamSynchronize(n->stream)))) return rc;
+    if ((rc = check_tc(n))) return lbm::ctx_error(c, rc, lbm_net_last_error(n));
     std::vector<float> h_in((size_t)nc), h_pred((size_t)nc);
     if ((rc = cu(cudaMemcpy(h_in.data(), in, (size_t)nc * sizeof(float), cudaMemcpyDeviceToHost)))) return rc;
     if ((rc = cu(cudaMemcpy(h_pred.data(), pred, (size_t)nc * sizeof(float), cudaMemcpyDeviceToHost)))) return rc;

@@ -3,6 +3,7 @@
 // Internal to the library.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "lbm_internal.h"
@@ -32,6 +33,21 @@ int loss_blocks(long long n);
 cudaError_t loss_and_grad(const float* x, const float* d, const float* target, float* g, long long n, long long vox,
                           const float* w, double* partials, cudaStream_t s);
 cudaError_t adam(float* p, const float* g, float* m, float* v, long long n, float lr, int step, cudaStream_t s);
+
+// The 32 -> 32 convolution on the tensor cores (tcgen05): FP16 operands, FP32 accumulation.
+// wimg is the layer's weight image (weight_image, weight_image_bytes() bytes); inputs FP16 or
+// FP32, multiplied by in_scale (a power of two) before they are rounded to FP16 and the sums
+// divided by it again (so small gradients keep their bits); outputs FP16 with relu or FP32
+// without. *err is set to 1 if a wait for the tensor cores timed out.
+// Layers with cin, cout <= 32 (the unused channels are zero-padded).
+size_t weight_image_bytes();
+cudaError_t weight_image(const float* W, int cout, int cin, __half* img, cudaStream_t s);
+cudaError_t conv32_tc(const void* in, int in_fp16, int cin, float in_scale, const __half* wimg, const float* bias, void* out,
+                      int out_fp16, int cout, int relu, int batch, int D, int H, int Wd, int* err, cudaStream_t s);
+// gW [cout][cin][27] += correlation of g [B][cout] with h [B][cin] on the tensor cores (g scaled by
+// g_scale, a power of two, before FP16 rounding and unscaled after); gb [cout] += sum of g.
+cudaError_t wgrad32_tc(const float* g, int cout, float g_scale, const void* h, int h_fp16, int cin, float* gW, float* gb,
+                       int batch, int D, int H, int Wd, int* err, cudaStream_t s);
 
 }  // namespace net
 

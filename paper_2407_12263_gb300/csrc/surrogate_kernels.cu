@@ -8,6 +8,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <cstdint>
+
 #include "surrogate.h"
 
 namespace lbm {
@@ -28,8 +30,13 @@ __device__ __forceinline__ float from_f<float>(float v) { return v; }
 template <>
 __device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
 
-// periodic index for any i (tiles may reach more than one period past a grid smaller than them)
-__device__ __forceinline__ int wrap(int i, int n) { return ((i % n) + n) % n; }
+// periodic index for any i: in range, one period off, or (a grid smaller than a tile) further
+__device__ __forceinline__ int wrap(int i, int n) {
+    if (i >= 0 && i < n) return i;
+    if (i < 0 && i + n >= 0) return i + n;
+    if (i >= n && i < 2 * n) return i - n;
+    return ((i % n) + n) % n;
+}
 
 struct Tiles {
     int tx, ty, tz;  // tiles per axis
@@ -298,6 +305,433 @@ cudaError_t adam(float* p, const float* g, float* m, float* v, long long n, floa
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     const float c1 = (float)(1.0 / (1.0 - pow((double)b1, step))), c2 = (float)(1.0 / (1.0 - pow((double)b2, step)));
     adam_kernel<<<ew_blocks(n), 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// The 32 -> 32 channel convolution on the fifth-generation tensor cores (tcgen05), FP16
+// operands, FP32 accumulation in tensor memory.
+//
+// Implicit GEMM: a tile of 128 output voxels (8 in x, 16 in y, one z plane) is the M = 128 side,
+// the 32 output channels the N = 32 side, and the reduction runs over 27 taps x 32 input
+// channels. The haloed input tile (10 x 18 x 3 voxels, 32 channels) sits in shared memory in
+// "chunk planes": element (haloed voxel h, channel k) at (k / 8) * PL + 16 h + 2 (k % 8). In the
+// canonical no-swizzle K-major operand layout (core matrices of 8 rows x 16 bytes), the rows of
+// an 8-voxel x-run are then 16 bytes apart and successive y-runs one haloed row (160 bytes)
+// apart, so the A operand of every tap is the same descriptor at a different start address.
+// The weights of all taps are a preformatted FP16 image (2 KB per tap) loaded once per CTA.
+// One thread issues the 54 MMAs (27 taps x 2 of K = 16) and commits them to an mbarrier; the
+// four warps then read their 32 rows of the accumulator with tcgen05.ld and write the output.
+// Waits are bounded: on a timeout the kernel raises *err, frees its tensor memory and returns.
+// ---------------------------------------------------------------------------------------
+namespace tc {
+
+constexpr int TX = 8, TY = 16, HX = TX + 2, HY = TY + 2, HZ = 3;
+constexpr int HALO = HX * HY * HZ;           // 540 haloed voxels
+constexpr uint32_t PL = HALO * 16;           // bytes of one chunk plane (8 channels)
+constexpr uint32_t A_BYTES = 4 * PL;         // 32 channels
+constexpr uint32_t W_TAP = 2048;             // bytes of one tap's 32 x 32 FP16 weights
+constexpr uint32_t W_BYTES = 27 * W_TAP;
+constexpr uint32_t SMEM = A_BYTES + W_BYTES;
+constexpr long long kSpin = 1ll << 26;        // polls of an mbarrier before giving up
+
+// offset of weight (out n, in k) of a tap inside its 2 KB block: core matrix (k/8, n/8)
+__host__ __device__ inline uint32_t w_off(int n, int k) { return (k / 8) * 512 + (n / 8) * 128 + (n % 8) * 16 + (k % 8) * 2; }
+
+__device__ inline uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);  // no swizzle, version 1
+}
+
+// kind::f16 instruction descriptor: FP32 D, FP16 A and B, both K-major, M = 128, N = 32
+constexpr uint32_t kIdesc = (1u << 4) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+// The FP16 weight image of a layer with cout, cin <= 32: zero where n >= cout or k >= cin.
+__global__ void weight_image_kernel(const float* __restrict__ W, int cout, int cin, __half* __restrict__ img) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;  // over [32 out][32 in][27]
+    if (i >= 32 * 32 * 27) return;
+    const int tap = i % 27, k = (i / 27) % 32, n = i / (27 * 32);
+    const float w = (n < cout && k < cin) ? W[((long long)n * cin + k) * 27 + tap] : 0.f;
+    *reinterpret_cast<__half*>(reinterpret_cast<unsigned char*>(img) + tap * W_TAP + w_off(n, k)) = __float2half_rn(w);
+}
+
+__device__ inline bool wait_parity(uint32_t mbar, uint32_t parity) {
+    for (long long it = 0; it < kSpin; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred P1;\n\tmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\tselp.b32 %0, 1, 0, P1;\n\t}\n"
+            : "=r"(ok)
+            : "r"(mbar), "r"(parity));
+        if (ok) return true;
+    }
+    return false;
+}
+
+template <typename TIN, int MODE, typename TOUT>
+__global__ void __launch_bounds__(128)
+conv32_tc_kernel(const TIN* __restrict__ in, int cin, float in_scale, const __half* __restrict__ wimg,
+                 const float* __restrict__ bias, TOUT* __restrict__ out, int cout, int D, int H, int Wd, int tiles_x,
+                 int tiles_y, int n_tiles, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sA = smem;
+    unsigned char* sW = smem + A_BYTES;
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_fail;
+    const int t = threadIdx.x;
+    const uint32_t mbar_a = (uint32_t)__cvta_generic_to_shared(&mbar);
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_a));
+        s_fail = 0;
+    }
+    if (t < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(
+            (uint32_t)__cvta_generic_to_shared(&tmem_slot)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    // weights: the preformatted image, 16 bytes at a time
+    for (int i = t; i < (int)(W_BYTES / 16); i += 128)
+        reinterpret_cast<uint4*>(sW)[i] = __ldg(reinterpret_cast<const uint4*>(wimg) + i);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_slot;
+    const uint32_t a_addr = (uint32_t)__cvta_generic_to_shared(sA), w_addr = (uint32_t)__cvta_generic_to_shared(sW);
+    const long long vox = (long long)D * H * Wd;
+    const int tiles_xy = tiles_x * tiles_y, tiles_per_b = tiles_xy * D;
+    const float out_scale = 1.0f / in_scale;  // in_scale is a power of two: exact
+    uint32_t phase = 0;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int b = tile / tiles_per_b, r = tile - b * tiles_per_b;
+        const int z0 = r / tiles_xy, ty = (r - z0 * tiles_xy) / tiles_x, tx = r - z0 * tiles_xy - ty * tiles_x;
+        const int x0 = tx * TX, y0 = ty * TY;
+        const TIN* inb = in + (long long)b * cin * vox;
+        // stage the haloed tile, converted to FP16, in chunk planes (channels >= cin are zero):
+        // a thread takes one haloed voxel, all 32 channels in flight, and writes 8 channels (16
+        // bytes) at a time
+        for (int h = t; h < HALO; h += 128) {
+            const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
+            const long long goff =
+                ((long long)wrap(z0 + hz - 1, D) * H + wrap(y0 + hy - 1, H)) * Wd + wrap(x0 + hx - 1, Wd);
+            float v[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) v[c] = c < cin ? to_f(inb[(long long)c * vox + goff]) : 0.f;
+#pragma unroll
+            for (int c8 = 0; c8 < 4; ++c8) {
+                __half2 q[4];
+#pragma unroll
+                for (int j2 = 0; j2 < 4; ++j2)
+                    q[j2] = __floats2half2_rn(v[8 * c8 + 2 * j2] * in_scale, v[8 * c8 + 2 * j2 + 1] * in_scale);
+                *reinterpret_cast<uint4*>(sA + c8 * PL + h * 16) = *reinterpret_cast<const uint4*>(q);
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (t == 0) {
+            const uint32_t h0 = (uint32_t)((HY + 1) * HX + 1);  // haloed index of output voxel (0, 0, 0)
+            for (int tap = 0; tap < 27; ++tap) {
+                const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+                const int shift = (dz - 1) * HY * HX + (dy - 1) * HX + (dx - 1);
+                for (int kk = 0; kk < 2; ++kk) {
+                    const uint64_t ad = smem_desc(a_addr + (uint32_t)(2 * kk) * PL + (uint32_t)((int)h0 + shift) * 16, PL, HX * 16);
+                    const uint64_t bd = smem_desc(w_addr + (uint32_t)tap * W_TAP + (uint32_t)(2 * kk) * 512, 512, 128);
+                    const uint32_t acc = (tap | kk) ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_a));
+        }
+        const bool ok = wait_parity(mbar_a, phase);
+        phase ^= 1u;
+        if (!ok) {
+            s_fail = 1;
+            atomicExch(err, 1);
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        __syncthreads();
+        if (s_fail) break;
+        // the accumulator: warp w holds rows 32 w .. 32 w + 31 (row m = 8 ly + lx)
+        const int warp = t / 32;
+        uint32_t v[32];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+              "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+              "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+              "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(tmem + ((uint32_t)(warp * 32) << 16)));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        const int m = t, lx = m % TX, ly = m / TX;
+        const int x = x0 + lx, y = y0 + ly;
+        if (x < Wd && y < H) {
+            const long long vv = ((long long)z0 * H + y) * Wd + x;
+            TOUT* ob = out + (long long)b * cout * vox;
+#pragma unroll
+            for (int o = 0; o < 32; ++o) {
+                if (o >= cout) break;
+                float a = __uint_as_float(v[o]) * out_scale + (bias ? bias[o] : 0.f);
+                if (MODE == 1) a = fmaxf(a, 0.f);
+                ob[(long long)o * vox + vv] = from_f<TOUT>(a);
+            }
+        }
+        // every thread is done with the accumulator and the staged tile before the next MMAs
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (t < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
+}
+
+// ---------------------------------------------------------------------------------------
+// Weight gradients on the tensor cores:
+//   gW[o][c][tap] = sum over voxels v of h[c][v + off(tap)] g[o][v],
+// a GEMM over the voxels for each of the 9 (dz, dy) pairs: D_(dz,dy)[m][o] with the M = 128 rows
+// m = 32 dx + c (dx = 0, 1, 2 and a fourth, zero, slot) and N = 32 columns o. A tile is 8 voxels
+// in x by 16 in y in one z plane (K = 128). The haloed rows of h (3 z-planes x 18 y-rows) are
+// staged as three x-shifted copies of each 8-voxel row side by side: element (row r, dx, c, lx)
+// at 2048 r + 512 dx + 16 c + 2 lx holds h[c][z0 + hz - 1][y0 + hy - 1][x0 + lx + dx - 1]. In the
+// K-major no-swizzle layout that is an operand with 128 bytes between groups of 8 rows (SBO) and
+// 2 KB between successive 8-voxel K chunks (LBO), the pair (dz, dy) selecting the start row. g is
+// staged the same way as the N x K operand (16 o + 2 lx within a 512-byte row). Nine 128 x 32
+// FP32 accumulators live in tensor memory (288 of 512 columns; one CTA per SM) for all the tiles
+// a CTA takes, and are added to gW at the end.
+// ---------------------------------------------------------------------------------------
+constexpr int WG_TX = 8, WG_TY = 16, WG_ROWS = 3 * (WG_TY + 2);  // 54 haloed x-rows
+constexpr uint32_t WG_ROW_BYTES = 4 * 512;                       // 4 dx slots x 32 channels x 8 voxels
+constexpr uint32_t WG_H_BYTES = WG_ROWS * WG_ROW_BYTES;           // 110,592
+constexpr uint32_t WG_G_BYTES = WG_TY * 512;                      // 8,192
+constexpr uint32_t WG_SMEM = WG_H_BYTES + WG_G_BYTES;
+
+template <typename TH>
+__global__ void __launch_bounds__(128, 1)
+wgrad32_tc_kernel(const float* __restrict__ g, int cout, float g_scale, const TH* __restrict__ h, int cin,
+                  float* __restrict__ gW, int D, int H, int Wd, int tiles_x, int tiles_y, int n_tiles, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sH = smem;
+    unsigned char* sG = smem + WG_H_BYTES;
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_fail;
+    const int t = threadIdx.x;
+    const uint32_t mbar_a = (uint32_t)__cvta_generic_to_shared(&mbar);
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_a));
+        s_fail = 0;
+    }
+    if (t < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+            (uint32_t)__cvta_generic_to_shared(&tmem_slot)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    // the fourth dx slot of every row stays zero
+    for (int i = t; i < (int)(WG_H_BYTES / 16); i += 128) reinterpret_cast<uint4*>(sH)[i] = make_uint4(0, 0, 0, 0);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_slot;
+    const uint32_t h_addr = (uint32_t)__cvta_generic_to_shared(sH), g_addr = (uint32_t)__cvta_generic_to_shared(sG);
+    const long long vox = (long long)D * H * Wd;
+    const int tiles_xy = tiles_x * tiles_y, tiles_per_b = tiles_xy * D;
+    constexpr uint32_t kIdescW = (1u << 4) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+    uint32_t phase = 0;
+    bool first = true;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int b = tile / tiles_per_b, r0 = tile - b * tiles_per_b;
+        const int z0 = r0 / tiles_xy, ty = (r0 - z0 * tiles_xy) / tiles_x, tx = r0 - z0 * tiles_xy - ty * tiles_x;
+        const int x0 = tx * WG_TX, y0 = ty * WG_TY;
+        // h: rows (hz, hy), three x-shifted copies: a thread takes one (row, channel), loads its
+        // ten x-values once and writes the three shifted 8-voxel windows, 16 bytes each
+        for (int pr2 = t; pr2 < WG_ROWS * 32; pr2 += 128) {
+            const int r = pr2 / 32, c = pr2 % 32;
+            const int hy = r % (WG_TY + 2), hz = r / (WG_TY + 2);
+            float v[WG_TX + 2];
+            if (c < cin) {
+                const long long base = ((long long)b * cin + c) * vox + ((long long)wrap(z0 + hz - 1, D) * H + wrap(y0 + hy - 1, H)) * Wd;
+#pragma unroll
+                for (int q = 0; q < WG_TX + 2; ++q) v[q] = to_f(h[base + wrap(x0 + q - 1, Wd)]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < WG_TX + 2; ++q) v[q] = 0.f;
+            }
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                __half2 w2[4];
+#pragma unroll
+                for (int j2 = 0; j2 < 4; ++j2) w2[j2] = __floats2half2_rn(v[dx + 2 * j2], v[dx + 2 * j2 + 1]);
+                *reinterpret_cast<uint4*>(sH + r * WG_ROW_BYTES + dx * 512 + c * 16) = *reinterpret_cast<const uint4*>(w2);
+            }
+        }
+        // g: the tile's own voxels (zero outside the grid and for o >= cout), scaled; one
+        // (row, output channel) per thread, 8 voxels in one 16-byte store
+        for (int pr2 = t; pr2 < WG_TY * 32; pr2 += 128) {
+            const int ly = pr2 / 32, o = pr2 % 32;
+            const int y = y0 + ly;
+            float v[WG_TX];
+#pragma unroll
+            for (int lx = 0; lx < WG_TX; ++lx) {
+                const int x = x0 + lx;
+                v[lx] = (o < cout && x < Wd && y < H) ? g[((long long)b * cout + o) * vox + ((long long)z0 * H + y) * Wd + x] * g_scale : 0.f;
+            }
+            __half2 w2[4];
+#pragma unroll
+            for (int j2 = 0; j2 < 4; ++j2) w2[j2] = __floats2half2_rn(v[2 * j2], v[2 * j2 + 1]);
+            *reinterpret_cast<uint4*>(sG + ly * 512 + o * 16) = *reinterpret_cast<const uint4*>(w2);
+        }
+        asm volatile("fence.proxy.async.shared::cta;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (t == 0) {
+            for (int pr = 0; pr < 9; ++pr) {
+                const int dz = pr / 3, dy = pr % 3;
+                const uint32_t row0 = (uint32_t)(dz * (WG_TY + 2) + dy);
+                for (int kk = 0; kk < WG_TY / 2; ++kk) {  // two 8-voxel rows per MMA (K = 16)
+                    const uint64_t ad = tc::smem_desc(h_addr + (row0 + 2 * kk) * WG_ROW_BYTES, WG_ROW_BYTES, 128);
+                    const uint64_t bd = tc::smem_desc(g_addr + (uint32_t)(2 * kk) * 512, 512, 128);
+                    const uint32_t acc = (first && kk == 0) ? 0u : 1u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem + (uint32_t)(pr * 32)),
+                        "l"(ad), "l"(bd), "r"(kIdescW), "r"(acc));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_a));
+        }
+        first = false;
+        const bool ok = tc::wait_parity(mbar_a, phase);
+        phase ^= 1u;
+        if (!ok) {
+            s_fail = 1;
+            atomicExch(err, 1);
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        __syncthreads();
+        if (s_fail) break;
+    }
+    // read the nine accumulators out: warp w holds rows 32 w .. 32 w + 31, i.e. dx = w, c = lane
+    if (!s_fail && !first) {
+        const int warp = t / 32, c = t % 32;
+        const float inv = 1.0f / g_scale;
+        for (int pr = 0; pr < 9; ++pr) {
+            uint32_t v[32];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+                  "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+                  "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+                  "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(pr * 32)));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            if (warp < 3 && c < cin) {
+                const int tap = 9 * (pr / 3) + 3 * (pr % 3) + warp;
+                for (int o = 0; o < cout; ++o) atomicAdd(&gW[((long long)o * cin + c) * 27 + tap], __uint_as_float(v[o]) * inv);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (t < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+}
+
+// gb[o] += sum over the batch and the voxels of g[b][o][v]
+__global__ void bias_grad_kernel(const float* __restrict__ g, int cout, long long vox, int batch, float* __restrict__ gb) {
+    __shared__ float red[256 / 32];
+    const int o = blockIdx.y;
+    float acc = 0.f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < vox * batch; i += (long long)gridDim.x * blockDim.x) {
+        const long long b = i / vox, v = i - b * vox;
+        acc += g[(b * cout + o) * vox + v];
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        atomicAdd(&gb[o], s);
+    }
+}
+
+}  // namespace tc
+
+cudaError_t weight_image(const float* W, int cout, int cin, __half* img, cudaStream_t s) {
+    if (cout > 32 || cin > 32) return cudaErrorInvalidValue;
+    const int n = 32 * 32 * 27;
+    tc::weight_image_kernel<<<(n + 255) / 256, 256, 0, s>>>(W, cout, cin, img);
+    return cudaGetLastError();
+}
+
+size_t weight_image_bytes() { return tc::W_BYTES; }
+
+static int tc_blocks() {
+    static int blocks = 0;
+    if (!blocks) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        blocks = 2 * (sms > 0 ? sms : 1);
+    }
+    return blocks;
+}
+
+cudaError_t wgrad32_tc(const float* g, int cout, float g_scale, const void* h, int h_fp16, int cin, float* gW, float* gb,
+                       int batch, int D, int H, int Wd, int* err, cudaStream_t s) {
+    if (cin > 32 || cout > 32) return cudaErrorInvalidValue;
+    const int tx = (Wd + tc::WG_TX - 1) / tc::WG_TX, ty = (H + tc::WG_TY - 1) / tc::WG_TY;
+    const int n_tiles = tx * ty * D * batch;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = n_tiles < sms ? n_tiles : sms;  // 512 tensor-memory columns each: one per SM
+    cudaError_t e;
+    if (h_fp16) {
+        e = cudaFuncSetAttribute(tc::wgrad32_tc_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::WG_SMEM);
+        if (e != cudaSuccess) return e;
+        tc::wgrad32_tc_kernel<__half><<<blocks, 128, tc::WG_SMEM, s>>>(g, cout, g_scale, (const __half*)h, cin, gW, D, H, Wd, tx, ty,
+                                                               n_tiles, err);
+    } else {
+        e = cudaFuncSetAttribute(tc::wgrad32_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::WG_SMEM);
+        if (e != cudaSuccess) return e;
+        tc::wgrad32_tc_kernel<float><<<blocks, 128, tc::WG_SMEM, s>>>(g, cout, g_scale, (const float*)h, cin, gW, D, H, Wd, tx, ty,
+                                                              n_tiles, err);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long long vox = (long long)D * H * Wd;
+    const long long blk = (vox * batch + 255) / 256;
+    tc::bias_grad_kernel<<<dim3((unsigned)(blk < 256 ? blk : 256), (unsigned)cout), 256, 0, s>>>(g, cout, vox, batch, gb);
+    return cudaGetLastError();
+}
+
+cudaError_t conv32_tc(const void* in, int in_fp16, int cin, float in_scale, const __half* wimg, const float* bias, void* out,
+                      int out_fp16, int cout, int relu, int batch, int D, int H, int Wd, int* err, cudaStream_t s) {
+    if (cin > 32 || cout > 32) return cudaErrorInvalidValue;
+    const int tx = (Wd + tc::TX - 1) / tc::TX, ty = (H + tc::TY - 1) / tc::TY;
+    const int n_tiles = tx * ty * D * batch;
+    const int blocks = n_tiles < tc_blocks() ? n_tiles : tc_blocks();
+#define LBM_TC(TIN, MODE, TOUT)                                                                                    \
+    do {                                                                                                           \
+        cudaError_t e_ = cudaFuncSetAttribute(tc::conv32_tc_kernel<TIN, MODE, TOUT>,                              \
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM);         \
+        if (e_ != cudaSuccess) return e_;                                                                          \
+        tc::conv32_tc_kernel<TIN, MODE, TOUT><<<blocks, 128, tc::SMEM, s>>>((const TIN*)in, cin, in_scale, wimg, bias,     \
+                                                                            (TOUT*)out, cout, D, H, Wd, tx, ty,    \
+                                                                            n_tiles, err);                         \
+    } while (0)
+    if (in_fp16 && out_fp16 && relu) LBM_TC(__half, 1, __half);
+    else if (!in_fp16 && !out_fp16 && !relu) LBM_TC(float, 0, float);
+    else if (in_fp16 && !out_fp16 && !relu) LBM_TC(__half, 0, float);
+    else return cudaErrorInvalidValue;
+#undef LBM_TC
     return cudaGetLastError();
 }
 
