@@ -418,7 +418,7 @@ def run_surrogate(lbm, torch, stream, args, world):
     net = lbm.Net(fp16=True, seed=7, stream=torch.cuda.current_stream().cuda_stream)
     grid_c = tuple(int(v) for v in X.shape[2:][::-1])
     gen = torch.Generator(device="cpu").manual_seed(0)
-    iters, batch = 300, 4
+    iters, batch = 1500, 4
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     first = last = None
@@ -427,7 +427,7 @@ def run_surrogate(lbm, torch, stream, args, world):
         xb, yb = Xn[idx].contiguous(), Yn[idx].contiguous()
         last = net.gradients(xb.data_ptr(), yb.data_ptr(), batch, grid_c)
         first = last if first is None else first
-        net.adam(1e-3 if it < 200 else 3e-4)
+        net.adam(1e-3 if it < 1000 else 3e-4)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     del X, Y, Xn, Yn
