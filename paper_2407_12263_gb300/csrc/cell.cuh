@@ -106,7 +106,8 @@ __device__ __forceinline__ int link_offset(const Nbr& n, int i, int s) {
 // At a wall the two terms of N read the same values of this cell, so N = 0 exactly.
 template <int Q, int S, bool WALLS>
 __device__ __forceinline__ void load_link(const Params& P, const void* __restrict__ state, int c, const Nbr& nb,
-                                          const WallSide& ws, int i, float2& vm, float2& v0, float2& vp) {
+                                          const WallSide& ws, int i, typename Store<S>::Raw& rm,
+                                          typename Store<S>::Raw& r0, typename Store<S>::Raw& rp) {
     const typename Store<S>::T* q = moving_plane<S>(state, P.N, i);
     const typename Store<S>::T* pm = q + c + link_offset<Q>(nb, i, -1);
     const typename Store<S>::T* pp = q + c + link_offset<Q>(nb, i, +1);
@@ -115,42 +116,50 @@ __device__ __forceinline__ void load_link(const Params& P, const void* __restric
         if (crosses_wall<Q>(ws, i, -1)) pm = back;
         if (crosses_wall<Q>(ws, i, +1)) pp = back;
     }
-    v0 = Store<S>::load_raw(q + c);
-    vm = Store<S>::load_raw(pm);
-    vp = Store<S>::load_raw(pp);
+    r0 = Store<S>::ld(q + c);
+    rm = Store<S>::ld(pm);
+    rp = Store<S>::ld(pp);
 }
 
-template <int Q, bool WITH_F, int S, bool WALLS = false>
+// RAW: fb[i], gb[i] (i >= 1) stay in storage units (see storage.cuh); fb[0], gb[0] are always in
+// population units. Every difference of two stored values is taken as (neighbour) - (FP32 of
+// this cell's value) with one rounding; a difference a - b in the flux is written -(b - a),
+// which is the same number.
+template <int Q, bool WITH_F, int S, bool WALLS = false, bool RAW = false>
 __device__ __forceinline__ void pull(const Params& P, const void* __restrict__ state, int c, const Nbr& nb,
                                      float (&fb)[Q], float (&gb)[Q], int& phi_fx,
                                      const WallSide& ws = WallSide{}) {
+    using St = Store<S>;
+    constexpr float sf = RAW ? 1.0f : St::kInvF, sg = RAW ? 1.0f : St::kInvG;
     float df = 0.f;                 // increment of sum f, storage units
     unsigned int dphi = 0u;         // increment of phi_fx (wraps; the true sum fits in 32 bits)
-    const float fa = P.flux_a * Store<S>::kInvG, fbk = P.flux_b * Store<S>::kInvG;
+    const float fa = P.flux_a * St::kInvG, fbk = P.flux_b * St::kInvG;
 #pragma unroll
     for (int k = 0; k < Lat<Q>::kPairs; ++k) {
         const int i = Lat<Q>::pair_first(k), j = Lat<Q>::pair_second(k);
-        float2 vmi, v0i, vpi, vmj, v0j, vpj;
-        load_link<Q, S, WALLS>(P, state, c, nb, ws, i, vmi, v0i, vpi);
-        load_link<Q, S, WALLS>(P, state, c, nb, ws, j, vmj, v0j, vpj);
-        gb[i] = (v0i.y + (P.lw_m * (vmi.y - v0i.y) + P.lw_p * (vpi.y - v0i.y))) * Store<S>::kInvG;
-        gb[j] = (v0j.y + (P.lw_m * (vmj.y - v0j.y) + P.lw_p * (vpj.y - v0j.y))) * Store<S>::kInvG;
-        // net outflow of phi across x + e_i/2 and across x - e_i/2 (= x + e_j/2)
-        const int out_i = __float2int_rn(__fmaf_rn(fa, __fsub_rn(v0i.y, vmj.y), __fmul_rn(fbk, __fsub_rn(vpi.y, v0j.y))));
-        const int out_j = __float2int_rn(__fmaf_rn(fa, __fsub_rn(v0j.y, vmi.y), __fmul_rn(fbk, __fsub_rn(vpj.y, v0i.y))));
+        typename St::Raw rmi, r0i, rpi, rmj, r0j, rpj;
+        load_link<Q, S, WALLS>(P, state, c, nb, ws, i, rmi, r0i, rpi);
+        load_link<Q, S, WALLS>(P, state, c, nb, ws, j, rmj, r0j, rpj);
+        const float2 v0i = St::cvt(r0i), v0j = St::cvt(r0j);
+        gb[i] = (v0i.y + (P.lw_m * St::sub_g(rmi, v0i.y) + P.lw_p * St::sub_g(rpi, v0i.y))) * sg;
+        gb[j] = (v0j.y + (P.lw_m * St::sub_g(rmj, v0j.y) + P.lw_p * St::sub_g(rpj, v0j.y))) * sg;
+        // net outflow of phi across x + e_i/2 and across x - e_i/2 (= x + e_j/2):
+        //   fa (g_i(x) - g_j(x + e_i)) + fbk (g_i(x + e_i) - g_j(x)), and the same with i, j swapped
+        const int out_i = __float2int_rn(__fmaf_rn(-fa, St::sub_g(rmj, v0i.y), __fmul_rn(fbk, St::sub_g(rpi, v0j.y))));
+        const int out_j = __float2int_rn(__fmaf_rn(-fa, St::sub_g(rmi, v0j.y), __fmul_rn(fbk, St::sub_g(rpj, v0i.y))));
         dphi -= (unsigned int)out_i + (unsigned int)out_j;
         if (WITH_F) {
-            const float ei = P.lw_m * (vmi.x - v0i.x) + P.lw_p * (vpi.x - v0i.x);
-            const float ej = P.lw_m * (vmj.x - v0j.x) + P.lw_p * (vpj.x - v0j.x);
-            fb[i] = (v0i.x + ei) * Store<S>::kInvF;
-            fb[j] = (v0j.x + ej) * Store<S>::kInvF;
+            const float ei = P.lw_m * St::sub_f(rmi, v0i.x) + P.lw_p * St::sub_f(rpi, v0i.x);
+            const float ej = P.lw_m * St::sub_f(rmj, v0j.x) + P.lw_p * St::sub_f(rpj, v0j.x);
+            fb[i] = (v0i.x + ei) * sf;
+            fb[j] = (v0j.x + ej) * sf;
             df += ei + ej;
         }
     }
     const float2 m0 = __ldg(moment_plane(state) + c);
     phi_fx = (int)((unsigned int)__float_as_int(m0.y) + dphi);
     gb[0] = __int2float_rn((int)((unsigned int)phi_fx - (unsigned int)P.phi_ref_fx)) * kPhiFxInvF;
-    if (WITH_F) fb[0] = m0.x + df * Store<S>::kInvF;
+    if (WITH_F) fb[0] = m0.x + df * St::kInvF;
 }
 
 struct Macro {
@@ -166,7 +175,8 @@ struct Macro {
 };
 
 // phi, rho, u (Sec. 2.3, Eq. momentum): rho u = sum fbar_i e_i + rho G / 2.
-template <int Q, bool GEN>
+// U: the storage type whose units fb[i >= 1] are in (STORE_F32: population units).
+template <int Q, bool GEN, int U = STORE_F32>
 __device__ __forceinline__ void macro_flow(const Params& P, const float (&fb)[Q], const float (&gb)[Q], Macro& m) {
     m.Phi = gb[0];
     m.phi = P.phi_ref + m.Phi;
@@ -181,6 +191,11 @@ __device__ __forceinline__ void macro_flow(const Params& P, const float (&fb)[Q]
         if (Lat<Q>::cy(i) < 0) jy -= fb[i];
         if (Lat<Q>::cz(i) > 0) jz += fb[i];
         if (Lat<Q>::cz(i) < 0) jz -= fb[i];
+    }
+    if constexpr (Store<U>::kInvF != 1.0f) {  // exact power-of-two rescaling, kept out of any FMA
+        jx = __fmul_rn(jx, Store<U>::kInvF);
+        jy = __fmul_rn(jy, Store<U>::kInvF);
+        jz = __fmul_rn(jz, Store<U>::kInvF);
     }
     if (GEN) {
         m.rho = P.rho2 + P.drho * m.phi;
@@ -201,7 +216,7 @@ __device__ __forceinline__ void macro_flow(const Params& P, const float (&fb)[Q]
 // (Sec. 2.3, Eq. norm): K1 = sum g_i e_i - phi u, n = -K1/|K1|, S = 4 phi (1-phi)/delta n,
 // grad phi = (tau_phi cs^2 S - K1) / ((tau_phi + 1/2) cs^2). The shift t_i phi_ref has no
 // first moment, so the stored deviations give K1 directly.
-template <int Q>
+template <int Q, int U = STORE_F32>
 __device__ __forceinline__ void macro_interface_df(const Params& P, const float (&gb)[Q], Macro& m) {
     float kx = 0.f, ky = 0.f, kz = 0.f;
 #pragma unroll
@@ -212,6 +227,11 @@ __device__ __forceinline__ void macro_interface_df(const Params& P, const float 
         if (Lat<Q>::cy(i) < 0) ky -= gb[i];
         if (Lat<Q>::cz(i) > 0) kz += gb[i];
         if (Lat<Q>::cz(i) < 0) kz -= gb[i];
+    }
+    if constexpr (Store<U>::kInvG != 1.0f) {
+        kx = __fmul_rn(kx, Store<U>::kInvG);
+        ky = __fmul_rn(ky, Store<U>::kInvG);
+        kz = __fmul_rn(kz, Store<U>::kInvG);
     }
     kx -= m.phi * m.u[0];
     ky -= m.phi * m.u[1];
@@ -304,7 +324,9 @@ __device__ __forceinline__ float edot(int i, const float (&v)[3]) {
 // e (3 e.u, e.S), evaluated once.
 // Zeroth moments: the g collision conserves phi; sum_i f*_i = sum_i fbar_i + u . grad rho,
 // because sum_i F_i = u . grad rho and sum_i f^eq_i = p / cs^2.
-template <int Q, bool GEN>
+// U: the storage type whose units fb[i], gb[i] (i >= 1) are in; the weights t_i carry its
+// scales, so f^eq, F and g^eq come out in the same units.
+template <int Q, bool GEN, int U = STORE_F32>
 __device__ __forceinline__ void collide(const Params& P, const Macro& m, float (&fb)[Q], float (&gb)[Q]) {
     constexpr int D = Lat<Q>::D;
     const float u2 = m.u[0] * m.u[0] + m.u[1] * m.u[1] + m.u[2] * m.u[2];
@@ -326,7 +348,8 @@ __device__ __forceinline__ void collide(const Params& P, const Macro& m, float (
 #pragma unroll
     for (int k = 0; k < Lat<Q>::kPairs; ++k) {
         const int i = Lat<Q>::pair_first(k), j = Lat<Q>::pair_second(k);
-        const float t = Lat<Q>::w(i);
+        const float t = Lat<Q>::w(i) * Store<U>::kScaleF;
+        const float tg = Lat<Q>::w(i) * Store<U>::kScaleG;
         const float eu = edot<Q>(i, m.u);
         const float en = edot<Q>(i, m.n);
         const float es = edot<Q>(i, m.S);
@@ -347,8 +370,8 @@ __device__ __forceinline__ void collide(const Params& P, const Macro& m, float (
             fb[i] = fb[i] - omega_f * (fb[i] - fi);
             fb[j] = fb[j] - omega_f * (fb[j] - fj);
         }
-        const float ge = t * (m.Phi + m.phi * even);
-        const float go = t * (m.phi * odd + P.tau_phi * es);
+        const float ge = tg * (m.Phi + m.phi * even);
+        const float go = tg * (m.phi * odd + P.tau_phi * es);
         gb[i] = gb[i] - omega_g * (gb[i] - (ge + go));
         gb[j] = gb[j] - omega_g * (gb[j] - (ge - go));
     }
@@ -372,26 +395,27 @@ __device__ __forceinline__ void step_cell(const Params& P, const void* __restric
     // addresses and give the same bits, so the result does not depend on it.
     const bool at_wall = GEN && (ws.xlo || ws.xhi || ws.ylo || ws.yhi || ws.zlo || ws.zhi);
     if (GEN && __any_sync(__activemask(), at_wall))
-        pull<Q, true, S, true>(P, fg_in, c, nb, fb, gb, phi_fx, ws);
+        pull<Q, true, S, true, true>(P, fg_in, c, nb, fb, gb, phi_fx, ws);
     else
-        pull<Q, true, S, false>(P, fg_in, c, nb, fb, gb, phi_fx);
+        pull<Q, true, S, false, true>(P, fg_in, c, nb, fb, gb, phi_fx);
 
+    // fb[i], gb[i] (i >= 1) stay in storage units until they are stored
     Macro m;
-    macro_flow<Q, GEN>(P, fb, gb, m);
+    macro_flow<Q, GEN, S>(P, fb, gb, m);
     if (SCHEME == SCHEME_DF) {
-        macro_interface_df<Q>(P, gb, m);
+        macro_interface_df<Q, S>(P, gb, m);
     } else {
         float gx, gy, gz;
         fd_gradient<Q>(phi_fd, c, GEN ? mirror_at_walls(nb, ws) : nb, gx, gy, gz);
         macro_interface_fd(P, gx, gy, gz, m);
     }
     macro_pressure<GEN>(P, m);
-    collide<Q, GEN>(P, m, fb, gb);
+    collide<Q, GEN, S>(P, m, fb, gb);
 
     // streaming stores: the output is not re-read this step
     __stcs(moment_plane(fg_out) + c, make_float2(fb[0], __int_as_float(phi_fx)));
 #pragma unroll
-    for (int i = 1; i < Q; ++i) Store<S>::store(moving_plane<S>(fg_out, P.N, i) + c, fb[i], gb[i], P);
+    for (int i = 1; i < Q; ++i) Store<S>::store_raw(moving_plane<S>(fg_out, P.N, i) + c, fb[i], gb[i]);
 }
 
 }  // namespace lbm

@@ -23,31 +23,69 @@ namespace lbm {
 template <int S>
 struct Store;
 
-// load_raw returns the stored pair in storage units (scaled for FP16); kInvF / kInvG turn
-// storage units into population units. load() applies them. The Lax-Wendroff update is linear,
-// so it runs on raw values and the scale is applied once per population afterwards.
+// Stored values are in storage units (scaled for FP16); kInvF / kInvG turn storage units into
+// population units. load() applies them, store() applies kScaleF / kScaleG
+// before rounding, store_raw() takes values already in storage units. The time step keeps the
+// moving populations in storage units from load to store: propagation and collision are linear
+// in them, the scales are powers of two (exact in FP32), so only the moments need rescaling and
+// the results are the same bits as in population units.
+//
+// Raw pair access for the propagation: ld() returns the pair as loaded, cvt() converts it to
+// FP32, sub_f(r, c) / sub_g(r, c) return (FP32 of r's f or g) - c with one rounding. For the
+// 16-bit types these are the mixed-precision forms of sub (a 16-bit operand widened exactly to
+// FP32, then subtracted), so a neighbour's pair is never converted on its own.
+__device__ __forceinline__ void unpack16(unsigned int r, unsigned short& lo, unsigned short& hi) {
+    asm("mov.b32 {%0, %1}, %2;" : "=h"(lo), "=h"(hi) : "r"(r));
+}
+
 template <>
 struct Store<STORE_F32> {
     using T = float2;
+    using Raw = float2;
+    __device__ __forceinline__ static Raw ld(const T* p) { return __ldg(p); }
+    __device__ __forceinline__ static float2 cvt(Raw r) { return r; }
+    __device__ __forceinline__ static float sub_f(Raw r, float c) { return __fsub_rn(r.x, c); }
+    __device__ __forceinline__ static float sub_g(Raw r, float c) { return __fsub_rn(r.y, c); }
     static constexpr float kScaleF = 1.0f, kScaleG = 1.0f, kInvF = 1.0f, kInvG = 1.0f;
-    __device__ __forceinline__ static float2 load_raw(const T* p) { return __ldg(p); }
     __device__ __forceinline__ static float2 load(const T* p, const Params&) { return __ldg(p); }
     __device__ __forceinline__ static void store(T* p, float f, float g, const Params&) {
         __stcs(p, make_float2(f, g));
     }
+    __device__ __forceinline__ static void store_raw(T* p, float f, float g) { __stcs(p, make_float2(f, g)); }
 };
 
 template <>
 struct Store<STORE_F16> {
     using T = __half2;
+    using Raw = unsigned int;
+    __device__ __forceinline__ static Raw ld(const T* p) { return __ldg(reinterpret_cast<const unsigned int*>(p)); }
+    __device__ __forceinline__ static float2 cvt(Raw r) {
+        return __half22float2(*reinterpret_cast<const __half2*>(&r));
+    }
+    __device__ __forceinline__ static float sub_f(Raw r, float c) {
+        unsigned short lo, hi;
+        unpack16(r, lo, hi);
+        float d;
+        asm("sub.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(lo), "f"(c));
+        return d;
+    }
+    __device__ __forceinline__ static float sub_g(Raw r, float c) {
+        unsigned short lo, hi;
+        unpack16(r, lo, hi);
+        float d;
+        asm("sub.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(hi), "f"(c));
+        return d;
+    }
     static constexpr float kScaleF = 4096.0f, kScaleG = 1024.0f, kInvF = 1.0f / 4096.0f, kInvG = 1.0f / 1024.0f;
-    __device__ __forceinline__ static float2 load_raw(const T* p) { return __half22float2(__ldg(p)); }
     __device__ __forceinline__ static float2 load(const T* p, const Params&) {
         const float2 v = __half22float2(__ldg(p));
         return make_float2(v.x * kInvF, v.y * kInvG);
     }
     __device__ __forceinline__ static void store(T* p, float f, float g, const Params&) {
-        const __half2 h = __floats2half2_rn(f * kScaleF, g * kScaleG);
+        store_raw(p, f * kScaleF, g * kScaleG);
+    }
+    __device__ __forceinline__ static void store_raw(T* p, float f, float g) {
+        const __half2 h = __floats2half2_rn(f, g);
         __stcs(reinterpret_cast<unsigned int*>(p), *reinterpret_cast<const unsigned int*>(&h));
     }
 };
@@ -55,10 +93,29 @@ struct Store<STORE_F16> {
 template <>
 struct Store<STORE_BF16> {
     using T = __nv_bfloat162;
+    using Raw = unsigned int;
+    __device__ __forceinline__ static Raw ld(const T* p) { return __ldg(reinterpret_cast<const unsigned int*>(p)); }
+    __device__ __forceinline__ static float2 cvt(Raw r) {
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r));
+    }
+    __device__ __forceinline__ static float sub_f(Raw r, float c) {
+        unsigned short lo, hi;
+        unpack16(r, lo, hi);
+        float d;
+        asm("sub.rn.f32.bf16 %0, %1, %2;" : "=f"(d) : "h"(lo), "f"(c));
+        return d;
+    }
+    __device__ __forceinline__ static float sub_g(Raw r, float c) {
+        unsigned short lo, hi;
+        unpack16(r, lo, hi);
+        float d;
+        asm("sub.rn.f32.bf16 %0, %1, %2;" : "=f"(d) : "h"(hi), "f"(c));
+        return d;
+    }
     static constexpr float kScaleF = 1.0f, kScaleG = 1.0f, kInvF = 1.0f, kInvG = 1.0f;
-    __device__ __forceinline__ static float2 load_raw(const T* p) { return __bfloat1622float2(__ldg(p)); }
     __device__ __forceinline__ static float2 load(const T* p, const Params&) { return __bfloat1622float2(__ldg(p)); }
-    __device__ __forceinline__ static void store(T* p, float f, float g, const Params&) {
+    __device__ __forceinline__ static void store(T* p, float f, float g, const Params&) { store_raw(p, f, g); }
+    __device__ __forceinline__ static void store_raw(T* p, float f, float g) {
         const __nv_bfloat162 h = __floats2bfloat162_rn(f, g);
         __stcs(reinterpret_cast<unsigned int*>(p), *reinterpret_cast<const unsigned int*>(&h));
     }
