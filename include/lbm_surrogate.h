@@ -71,8 +71,9 @@ int lbm_coarse_fields(lbm_ctx *ctx, int factor, float *out);
 
 /* Replace the state by the one lbm_init_fields builds from coarse fields (device [5][...] as
  * above) upsampled trilinearly between coarse cell centres (periodic; clamped across walls),
- * with p0 the reference pressure of the storage. sum phi is then set back exactly to its
- * value before the call (the difference, in units of 2^-30, spread over the cells). */
+ * with p0 the reference pressure of the storage; the construction runs in FP32 in one pass, and
+ * the upsampled phi is clamped to [-1, 1.5]. sum phi is then set back exactly to its value
+ * before the call (the difference, in units of 2^-30, spread over the cells). */
 int lbm_restart_from_coarse(lbm_ctx *ctx, int factor, const float *coarse, double p0);
 
 typedef struct {
@@ -96,10 +97,16 @@ typedef struct {
  *      restart); reject if the ratio exceeds relax_tol: a prediction whose phi, u and p do not
  *      fit together relaxes fast;
  *   5. on rejection restore the starting state and advance it k steps with the LBM.
- * Synchronous. Needs 2x the state's device memory while it runs.
+ * Synchronous. Needs a workspace of one more state buffer plus four coarse field arrays: the
+ * first jump on a handle allocates it (or lbm_surrogate_reserve, beforehand) and the handle keeps
+ * it until lbm_destroy, so later jumps allocate nothing.
  */
 int lbm_surrogate_jump(lbm_ctx *ctx, lbm_net *net, int factor, const float mean_std[10], int k, int judge_steps,
                        double mass_tol, double relax_tol, lbm_jump_report *report);
+
+/* Allocate the workspace of lbm_surrogate_jump for this factor now (LBM_ENOMEM if it does not
+ * fit), so that the jumps themselves allocate nothing. Synchronous. */
+int lbm_surrogate_reserve(lbm_ctx *ctx, int factor);
 
 #ifdef __cplusplus
 }

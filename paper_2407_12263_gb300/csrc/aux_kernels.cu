@@ -256,6 +256,35 @@ mass_finish(const double* __restrict__ partials, int n, double* __restrict__ res
     }
 }
 
+// The exact sum of the fixed-point phi values of plane 0. The propagation only moves phi across
+// faces in integer amounts that cancel in pairs, so this equals the sum over the propagated
+// state that launch_mass reports in result[3], without reading the moving populations.
+__global__ void __launch_bounds__(kRedThreads)
+phi_fixed_sum_kernel(const float2* __restrict__ plane0, long long N, double* __restrict__ partials) {
+    long long s = 0;
+    for (long long c = (long long)blockIdx.x * kRedThreads + threadIdx.x; c < N; c += (long long)gridDim.x * kRedThreads)
+        s += __float_as_int(__ldg(plane0 + c).y);
+    double unused[2] = {0.0, 0.0};
+    block_sum(s, unused);
+    if (threadIdx.x == 0) partials[3 * blockIdx.x] = __longlong_as_double(s);
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+phi_fixed_finish(const double* __restrict__ partials, int n, double* __restrict__ result) {
+    long long s = 0;
+    for (int b = threadIdx.x; b < n; b += kRedThreads) s += __double_as_longlong(partials[3 * b]);
+    double unused[2] = {0.0, 0.0};
+    block_sum(s, unused);
+    if (threadIdx.x == 0) result[3] = __longlong_as_double(s);
+}
+
+cudaError_t launch_phi_fixed_sum(const Params& P, const void* fg, double* partials, int n_partials, double* result,
+                                 cudaStream_t s) {
+    phi_fixed_sum_kernel<<<n_partials, kRedThreads, 0, s>>>(moment_plane(fg), P.N, partials);
+    phi_fixed_finish<<<1, kRedThreads, 0, s>>>(partials, n_partials, result);
+    return cudaGetLastError();
+}
+
 int mass_partials_needed(const Params& P) {
     const long long blocks = (P.N + kRedThreads - 1) / kRedThreads;
     return (int)(blocks < 1024 ? blocks : 1024);

@@ -343,8 +343,12 @@ __device__ __forceinline__ void collide(const Params& P, const Macro& m, float (
         omega_f = 1.0f / (tau + 0.5f);
     }
     const float omega_g = P.omega_g;
+    // f* = (1 - w_f) fbar + w_f f^eq + (1 - w_f/2) F and g* = (1 - w_g) g + w_g g^eq: the same
+    // collisions, one multiply-add per population once the pair's parts are known.
+    const float a_f = 1.f - omega_f, c_f = 1.f - 0.5f * omega_f, a_g = 1.f - omega_g;
     const float u2h = 1.5f * u2;
     const float feq0 = m.P - 4.5f * pi0;  // P - 4.5 Pi_s term shared by every |e|^2 class
+    const float rho3 = 3.f * m.rho, phi3 = 3.f * m.phi, urG3 = 3.f * urG;
 #pragma unroll
     for (int k = 0; k < Lat<Q>::kPairs; ++k) {
         const int i = Lat<Q>::pair_first(k), j = Lat<Q>::pair_second(k);
@@ -353,27 +357,36 @@ __device__ __forceinline__ void collide(const Params& P, const Macro& m, float (
         const float eu = edot<Q>(i, m.u);
         const float en = edot<Q>(i, m.n);
         const float es = edot<Q>(i, m.S);
-        const float even = 4.5f * eu * eu - u2h;            // gam_i = even + odd, gam_j = even - odd
-        const float odd = 3.f * eu;
+        const float even = 4.5f * eu * eu - u2h;                   // gam_i = even + 3 eu, gam_j = even - 3 eu
         const float pis = sg * ((float)Lat<Q>::e2(i) - en * en);  // Pi_s term minus its |e|^2 = 0 part
-        const float fe = t * (feq0 + m.rho * even - 4.5f * pis);
-        const float fo = t * m.rho * odd;
-        const float fi = fe + fo, fj = fe - fo;             // f^eq_i, f^eq_j (shifted)
+        // f^eq_i = t (Xe + Xo), f^eq_j = t (Xe - Xo)
+        const float Xe = feq0 + m.rho * even - 4.5f * pis;
+        float Ae, Ao;  // w_f f^eq + (1 - w_f/2) F, even and odd parts
         if (GEN) {
+            // F_i = t (Ye + Yo), F_j = t (Ye - Yo), from e_j = -e_i in S_i and R_i:
+            //   Ye = 3 eu (e.grad rho + 3 e.rho G) - even u.grad rho - 3 u.rho G
+            //   Yo = even e.grad rho - 3 eu u.grad rho + 3 e.rho G
             const float egr = edot<Q>(i, gr);
             const float erG = edot<Q>(i, rG);
-            const float Fi = t * ((even + odd) * (egr - ugr) + 3.f * (erG - urG) + 9.f * eu * erG);
-            const float Fj = t * ((even - odd) * (-egr - ugr) + 3.f * (-erG - urG) + 9.f * eu * erG);
-            fb[i] = fb[i] - omega_f * (fb[i] - fi + 0.5f * Fi) + Fi;
-            fb[j] = fb[j] - omega_f * (fb[j] - fj + 0.5f * Fj) + Fj;
+            const float odd = 3.f * eu;
+            const float Ye = odd * (egr + 3.f * erG) - even * ugr - urG3;
+            const float Yo = even * egr - odd * ugr + 3.f * erG;
+            Ae = t * (omega_f * Xe + c_f * Ye);
+            Ao = t * (omega_f * (rho3 * eu) + c_f * Yo);
         } else {
-            fb[i] = fb[i] - omega_f * (fb[i] - fi);
-            fb[j] = fb[j] - omega_f * (fb[j] - fj);
+            const float tw = t * omega_f;  // uniform over the grid
+            Ae = tw * Xe;
+            Ao = (tw * rho3) * eu;
         }
-        const float ge = tg * (m.Phi + m.phi * even);
-        const float go = tg * (m.phi * odd + P.tau_phi * es);
-        gb[i] = gb[i] - omega_g * (gb[i] - (ge + go));
-        gb[j] = gb[j] - omega_g * (gb[j] - (ge - go));
+        fb[i] = a_f * fb[i] + (Ae + Ao);
+        fb[j] = a_f * fb[j] + (Ae - Ao);
+        // g^eq_i = tg (Phi + phi gam_i + tau_phi e_i.S): even part tg (Phi + phi even), odd part
+        // tg (3 phi eu + tau_phi e.S)
+        const float twg = tg * omega_g;
+        const float Be = twg * (m.Phi + m.phi * even);
+        const float Bo = twg * (phi3 * eu + P.tau_phi * es);
+        gb[i] = a_g * gb[i] + (Be + Bo);
+        gb[j] = a_g * gb[j] + (Be - Bo);
     }
     fb[0] = GEN ? m.Pbar + ugr : m.Pbar;  // plane 0 keeps phi_fx: the collision conserves phi
 }

@@ -57,6 +57,7 @@ void free_ctx(lbm_ctx* c) {
     cudaFree(c->partials);
     cudaFree(c->result);
     cudaFree(c->staging);
+    cudaFree(c->jump_ws);
     for (int k = 0; k < 2; ++k)
         if (c->graph_exec[k]) cudaGraphExecDestroy(c->graph_exec[k]);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -292,12 +293,12 @@ int lbm::ctx_mass_fixed(lbm_ctx* c, long long* sum) {
     int rc = check_ctx(c);
     if (rc) return rc;
     if (!c->initialised) return set_error(c, LBM_ESTATE, "no state: call lbm_init_phi first");
-    LBM_CUDA(c, lbm::launch_mass(c->P, c->fg[c->cur], c->partials, c->n_partials, c->result, c->stream));
+    LBM_CUDA(c, lbm::launch_phi_fixed_sum(c->P, c->fg[c->cur], c->partials, c->n_partials, c->result, c->stream));
     c->launches += 2;
-    double r[4];
-    LBM_CUDA(c, cudaMemcpyAsync(r, c->result, sizeof r, cudaMemcpyDeviceToHost, c->stream));
+    double r3;
+    LBM_CUDA(c, cudaMemcpyAsync(&r3, c->result + 3, sizeof r3, cudaMemcpyDeviceToHost, c->stream));
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));
-    std::memcpy(sum, &r[3], sizeof *sum);
+    std::memcpy(sum, &r3, sizeof *sum);
     return LBM_OK;
 }
 
@@ -308,19 +309,8 @@ int lbm::ctx_restart_from_coarse(lbm_ctx* c, int f, const float* coarse, double 
     P.w0d = p0 * 3.0;
     P.w0 = (float)P.w0d;
     drop_graphs(c);
-    const size_t nxy = (size_t)P.nxy;
-    const int nzs = slab_depth(c, 5, 2);
-    rc = ensure_staging(c, (size_t)(nzs + 2 + 4 * nzs) * nxy);
-    if (rc) return rc;
-    double* phis = c->staging;
-    double* us = phis + (size_t)(nzs + 2) * nxy;
-    double* ps = us + (size_t)3 * nzs * nxy;
-    for (int z0 = 0; z0 < P.nz; z0 += nzs) {
-        const int n = (z0 + nzs <= P.nz) ? nzs : P.nz - z0;
-        LBM_CUDA(c, lbm::launch_upsample_slab(P, coarse, f, z0, n, phis, us, ps, c->stream));
-        LBM_CUDA(c, lbm::launch_init(P, z0, n, phis, us, ps, p0, c->fg[c->cur], c->stream));
-        c->launches += 2;
-    }
+    LBM_CUDA(c, lbm::launch_restart(P, coarse, f, p0, c->fg[c->cur], c->stream));
+    c->launches += 1;
     c->initialised = true;
     c->version += 1;
     return LBM_OK;

@@ -28,6 +28,8 @@ struct lbm_ctx {
     int graph_steps;                  // steps per replayed CUDA graph (0 = none)
     cudaGraphExec_t graph_exec[2];    // graph of graph_steps steps starting from buffer 0 / 1
     bool batch_owned;      // a case of an lbm_batch: lbm_destroy leaves it to lbm_batch_destroy
+    void* jump_ws;         // surrogate jumps: a backup state, then four coarse field arrays
+    size_t jump_ws_bytes;  // (allocated by the first jump or lbm_surrogate_reserve, kept until destroy)
     long long version;     // bumped whenever the parameters or the whole state are replaced
     char err[512];
 };

@@ -70,6 +70,9 @@ cudaError_t launch_moments(const Params& P, int scheme, int z0, int nzs, const v
 cudaError_t launch_mass(const Params& P, const void* fg, double* partials, int n_partials,
                         double* result /* 4 doubles */, cudaStream_t s);
 int mass_partials_needed(const Params& P);
+// Only result[3] of launch_mass (the exact fixed-point sum of phi), from plane 0 alone.
+cudaError_t launch_phi_fixed_sum(const Params& P, const void* fg, double* partials, int n_partials,
+                                 double* result /* 4 doubles */, cudaStream_t s);
 
 // All Q populations of the slab [z0, z0 + nzs) between the device storage and FP64 staging
 // holding plain populations (Q planes of nzs * nxy values).

@@ -368,6 +368,41 @@ int lbm_restart_from_coarse(lbm_ctx* c, int f, const float* coarse, double p0) {
     return LBM_OK;
 }
 
+namespace {
+
+// Carves the jump's buffers out of the handle's workspace, growing it if it is too small.
+int jump_workspace(lbm_ctx* c, int f, void** backup, float* fields[4]) {
+    const long long nc = (long long)(c->P.nx / f) * (c->P.ny / f) * (c->P.nz / f);
+    const size_t align = 256;
+    const size_t sb = (c->fg_bytes + align - 1) / align * align;
+    const size_t fb = ((size_t)5 * nc * sizeof(float) + align - 1) / align * align;
+    const size_t need = sb + 4 * fb;
+    if (c->jump_ws_bytes < need) {
+        cudaFree(c->jump_ws);
+        c->jump_ws = nullptr;
+        c->jump_ws_bytes = 0;
+        cudaError_t e = cudaMalloc(&c->jump_ws, need);
+        if (e != cudaSuccess) return lbm::ctx_error(c, LBM_ENOMEM, cudaGetErrorString(e));
+        c->jump_ws_bytes = need;
+    }
+    char* base = static_cast<char*>(c->jump_ws);
+    *backup = base;
+    for (int i = 0; i < 4; ++i) fields[i] = reinterpret_cast<float*>(base + sb + i * fb);
+    return LBM_OK;
+}
+
+}  // namespace
+
+int lbm_surrogate_reserve(lbm_ctx* c, int f) {
+    int rc = lbm::ctx_check(c);
+    if (rc) return rc;
+    if (f < 1 || c->P.nx % f || c->P.ny % f || c->P.nz % f)
+        return lbm::ctx_error(c, LBM_EINVAL, "factor must divide nx, ny and nz");
+    void* backup;
+    float* fields[4];
+    return jump_workspace(c, f, &backup, fields);
+}
+
 int lbm_surrogate_jump(lbm_ctx* c, lbm_net* n, int f, const float mean_std[10], int k, int judge_steps, double mass_tol,
                        double relax_tol, lbm_jump_report* rep) {
     int rc = lbm::ctx_check(c);
@@ -381,24 +416,11 @@ int lbm_surrogate_jump(lbm_ctx* c, lbm_net* n, int f, const float mean_std[10], 
     std::memset(rep, 0, sizeof *rep);
     const int grid_c[3] = {c->P.nx / f, c->P.ny / f, c->P.nz / f};
     const long long nc = (long long)grid_c[0] * grid_c[1] * grid_c[2];
-    const size_t fbytes = (size_t)5 * nc * sizeof(float);
-    float *in = nullptr, *xin = nullptr, *yout = nullptr, *pred = nullptr;
-    void* backup = nullptr;
-    struct Frees {
-        float **a, **b, **cc, **d;
-        void** e;
-        ~Frees() {
-            cudaFree(*a);
-            cudaFree(*b);
-            cudaFree(*cc);
-            cudaFree(*d);
-            cudaFree(*e);
-        }
-    } frees{&in, &xin, &yout, &pred, &backup};
+    void* backup;
+    float* fields[4];
+    if ((rc = jump_workspace(c, f, &backup, fields))) return rc;
+    float *in = fields[0], *xin = fields[1], *yout = fields[2], *pred = fields[3];
     auto cu = [&](cudaError_t e) { return e == cudaSuccess ? LBM_OK : lbm::ctx_error(c, LBM_ECUDA, cudaGetErrorString(e)); };
-    if ((rc = cu(cudaMalloc(&in, fbytes))) || (rc = cu(cudaMalloc(&xin, fbytes))) || (rc = cu(cudaMalloc(&yout, fbytes))) ||
-        (rc = cu(cudaMalloc(&pred, fbytes))) || (rc = cu(cudaMalloc(&backup, c->fg_bytes))))
-        return rc;
     const int saved_cur = c->cur;
     const lbm::Params saved_P = c->P;
     if ((rc = cu(cudaMemcpyAsync(backup, c->fg[c->cur], c->fg_bytes, cudaMemcpyDeviceToDevice, c->stream)))) return rc;

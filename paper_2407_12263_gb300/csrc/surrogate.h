@@ -54,10 +54,10 @@ cudaError_t wgrad32_tc(const float* g, int cout, float g_scale, const void* h, i
 // Coarse fields [5][nz/f][ny/f][nx/f] (phi, u, v, w, p; means over f^3 cells of the macroscopic
 // fields of the difference-free scheme) of the propagated state fg.
 cudaError_t launch_coarsen(const Params& P, const void* fg, int factor, float* out, cudaStream_t s);
-// The staging of launch_init for the slab [z0, z0 + nzs) from coarse fields, trilinear between
-// coarse cell centres (periodic, clamped across walls): phi planes z0-1 .. z0+nzs, u, p.
-cudaError_t launch_upsample_slab(const Params& P, const float* coarse, int factor, int z0, int nzs, double* phis,
-                                 double* us, double* ps, cudaStream_t s);
+// The state launch_init builds (equilibrium plus the first-order non-equilibrium part of g) from
+// coarse fields upsampled trilinearly between coarse cell centres (periodic, clamped across
+// walls), in FP32 arithmetic and in one pass: no staging.
+cudaError_t launch_restart(const Params& P, const float* coarse, int factor, double p0, void* fg, cudaStream_t s);
 // Adds delta units (2^-30) of phi to the state, spread over the cells so that it sums exactly.
 cudaError_t launch_adjust_phi(const Params& P, void* fg, long long delta, cudaStream_t s);
 // (x - mean[c]) / std[c] per channel of [5][n] (dir = +1) or x std[c] + mean[c] (dir = -1).

@@ -1,7 +1,7 @@
 // surrogate_glue.cu -- field transfers between the lattice and the surrogate's coarse grid:
-// block means of the macroscopic fields, trilinear upsampling into the initialisation's
-// staging (the restart is then the same equilibrium-plus-non-equilibrium construction as the
-// initial state), and the exact correction of sum phi after a restart.
+// block means of the macroscopic fields, the restart from trilinearly upsampled coarse fields
+// (the same equilibrium-plus-non-equilibrium construction as the initial state, in FP32), and
+// the exact correction of sum phi after a restart.
 #include "cell.cuh"
 #include "surrogate.h"
 
@@ -59,63 +59,137 @@ cudaError_t launch_coarsen(const Params& P, const void* fg, int factor, float* o
     return cudaGetLastError();
 }
 
-// coarse index and weight of fine cell i along an axis of n fine cells (nc coarse ones)
-__device__ __forceinline__ void interp_axis(int i, int f, int nc, bool wall, int& i0, int& i1, double& t) {
-    const double xc = (i + 0.5) / f - 0.5;
-    int a = (int)floor(xc);
-    t = xc - a;
-    int b = a + 1;
+// Where fine coordinate i (of n = nc f cells) falls between coarse cell centres: the two coarse
+// indices and the weight of the second. Periodic, or clamped to the end centres across a wall.
+struct Axis {
+    int a, b;
+    float t;
+};
+
+__device__ __forceinline__ Axis interp_axis(int i, int f, int nc, bool wall) {
+    const float xc = ((float)i + 0.5f) / (float)f - 0.5f;
+    Axis r;
+    r.a = (int)floorf(xc);
+    r.t = xc - (float)r.a;
+    r.b = r.a + 1;
     if (wall) {
-        if (a < 0) { a = 0; t = 0.0; }
-        if (b > nc - 1) { b = nc - 1; t = (a == b) ? 0.0 : t; }
+        if (r.a < 0) {
+            r.a = 0;
+            r.t = 0.f;
+        }
+        if (r.b > nc - 1) {
+            r.b = nc - 1;
+            if (r.a == r.b) r.t = 0.f;
+        }
     } else {
-        a = (a % nc + nc) % nc;
-        b = (b % nc + nc) % nc;
+        r.a = (r.a % nc + nc) % nc;
+        r.b = (r.b % nc + nc) % nc;
     }
-    i0 = a;
-    i1 = b;
+    return r;
 }
 
-__device__ __forceinline__ double trilinear(const float* __restrict__ q, int ncx, int ncy, int x0, int x1, double tx,
-                                            int y0, int y1, double ty, int z0, int z1, double tz) {
-    auto at = [&](int z, int y, int x) { return (double)q[((long long)z * ncy + y) * ncx + x]; };
-    const double c00 = at(z0, y0, x0) * (1 - tx) + at(z0, y0, x1) * tx;
-    const double c01 = at(z0, y1, x0) * (1 - tx) + at(z0, y1, x1) * tx;
-    const double c10 = at(z1, y0, x0) * (1 - tx) + at(z1, y0, x1) * tx;
-    const double c11 = at(z1, y1, x0) * (1 - tx) + at(z1, y1, x1) * tx;
-    return (c00 * (1 - ty) + c01 * ty) * (1 - tz) + (c10 * (1 - ty) + c11 * ty) * tz;
+__device__ __forceinline__ float trilinear(const float* __restrict__ q, int ncx, int ncy, const Axis& X, const Axis& Y,
+                                           const Axis& Z) {
+    auto at = [&](int z, int y, int x) { return __ldg(q + ((long long)z * ncy + y) * ncx + x); };
+    auto lerp = [](float u, float v, float t) { return fmaf(t, v - u, u); };
+    const float c00 = lerp(at(Z.a, Y.a, X.a), at(Z.a, Y.a, X.b), X.t);
+    const float c01 = lerp(at(Z.a, Y.b, X.a), at(Z.a, Y.b, X.b), X.t);
+    const float c10 = lerp(at(Z.b, Y.a, X.a), at(Z.b, Y.a, X.b), X.t);
+    const float c11 = lerp(at(Z.b, Y.b, X.a), at(Z.b, Y.b, X.b), X.t);
+    return lerp(lerp(c00, c01, Y.t), lerp(c10, c11, Y.t), Z.t);
 }
 
-__global__ void upsample_kernel(const Params P, const float* __restrict__ coarse, int f, int z0, int nzs,
-                                double* __restrict__ phis, double* __restrict__ us, double* __restrict__ ps) {
+// The initial-state construction of init_kernel (equilibria of the upsampled phi, u, p plus the
+// first-order non-equilibrium part of g, grad phi from the isotropic central difference of the
+// upsampled phi) in FP32, written directly as deviations from the storage's reference levels.
+// phi is clamped to [-1, 1.5], the range lbm_init_fields accepts, so that its fixed-point value
+// stays in range whatever the prediction holds.
+template <int Q, int S>
+__global__ void restart_kernel(const Params P, const float* __restrict__ coarse, int f, float p0, void* __restrict__ fg) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int l = (int)blockIdx.z - 1;  // plane z0 + l, l = -1 .. nzs
+    const int z = blockIdx.z;
     if (x >= P.nx || y >= P.ny) return;
     const int ncx = P.nx / f, ncy = P.ny / f, ncz = P.nz / f;
     const long long nc = (long long)ncx * ncy * ncz;
-    int z = z0 + l;
-    if (P.walls & 4) z = min(max(z, 0), P.nz - 1);
-    else z = ((z % P.nz) + P.nz) % P.nz;
-    int x0, x1, y0, y1, zz0, zz1;
-    double tx, ty, tz;
-    interp_axis(x, f, ncx, P.walls & 1, x0, x1, tx);
-    interp_axis(y, f, ncy, P.walls & 2, y0, y1, ty);
-    interp_axis(z, f, ncz, P.walls & 4, zz0, zz1, tz);
-    const size_t nxy = (size_t)P.nxy;
-    const size_t cell = (size_t)y * P.nx + x;
-    phis[(size_t)(l + 1) * nxy + cell] = trilinear(coarse, ncx, ncy, x0, x1, tx, y0, y1, ty, zz0, zz1, tz);
-    if (l < 0 || l >= nzs) return;
-    const size_t slab = (size_t)nzs * nxy, lu = (size_t)l * nxy + cell;
-    for (int a = 0; a < 3; ++a)
-        us[a * slab + lu] = trilinear(coarse + (1 + a) * nc, ncx, ncy, x0, x1, tx, y0, y1, ty, zz0, zz1, tz);
-    ps[lu] = trilinear(coarse + 4 * nc, ncx, ncy, x0, x1, tx, y0, y1, ty, zz0, zz1, tz);
+    // the axes at x - 1, x, x + 1 (periodic images; across a wall the cell itself, so that the
+    // normal gradient vanishes there)
+    Axis ax[3], ay[3], az[3];
+#pragma unroll
+    for (int d = -1; d <= 1; ++d) {
+        int xx = x + d, yy = y + d, zz = z + d;
+        xx = (P.walls & 1) ? min(max(xx, 0), P.nx - 1) : (xx + P.nx) % P.nx;
+        yy = (P.walls & 2) ? min(max(yy, 0), P.ny - 1) : (yy + P.ny) % P.ny;
+        zz = (P.walls & 4) ? min(max(zz, 0), P.nz - 1) : (zz + P.nz) % P.nz;
+        ax[d + 1] = interp_axis(xx, f, ncx, P.walls & 1);
+        ay[d + 1] = interp_axis(yy, f, ncy, P.walls & 2);
+        az[d + 1] = interp_axis(zz, f, ncz, P.walls & 4);
+    }
+    auto phi_at = [&](int dx, int dy, int dz) {
+        return fminf(fmaxf(trilinear(coarse, ncx, ncy, ax[dx + 1], ay[dy + 1], az[dz + 1]), -1.0f), 1.5f);
+    };
+    const float phi = phi_at(0, 0, 0);
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const float v = Lat<Q>::w(i) * phi_at(Lat<Q>::cx(i), Lat<Q>::cy(i), Lat<Q>::cz(i));
+        gx += Lat<Q>::cx(i) * v;
+        gy += Lat<Q>::cy(i) * v;
+        gz += Lat<Q>::cz(i) * v;
+    }
+    gx *= 3.f;
+    gy *= 3.f;
+    gz *= 3.f;
+    const float u[3] = {trilinear(coarse + nc, ncx, ncy, ax[1], ay[1], az[1]),
+                        trilinear(coarse + 2 * nc, ncx, ncy, ax[1], ay[1], az[1]),
+                        trilinear(coarse + 3 * nc, ncx, ncy, ax[1], ay[1], az[1])};
+    const float pc = trilinear(coarse + 4 * nc, ncx, ncy, ax[1], ay[1], az[1]);
+    const float g2 = gx * gx + gy * gy + gz * gz;
+    const float gn = sqrtf(g2);
+    const float inv = (g2 > kNormalGuard) ? 1.0f / gn : 0.f;
+    const float n[3] = {gx * inv, gy * inv, gz * inv};
+    const float smag = P.four_over_delta * phi * (1.f - phi);
+    const float Sv[3] = {smag * n[0], smag * n[1], smag * n[2]};
+    const float rho = P.rho2 + P.drho * phi;
+    const float u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const float sg = P.sigma * gn;
+    const float trc3 = ((float)Lat<Q>::D - (n[0] * n[0] + n[1] * n[1] + n[2] * n[2])) * (1.0f / 3.0f);
+    const float dP = 3.f * (pc - p0);  // p / cs^2 - w0
+    const float Phi = phi - P.phi_ref;
+    const float tnq = P.tau_phi - 0.5f;
+    const long long c = ((long long)z * P.ny + y) * P.nx + x;
+    float fsum = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float t = Lat<Q>::w(i);
+        const float eu = Lat<Q>::cx(i) * u[0] + Lat<Q>::cy(i) * u[1] + Lat<Q>::cz(i) * u[2];
+        const float en = Lat<Q>::cx(i) * n[0] + Lat<Q>::cy(i) * n[1] + Lat<Q>::cz(i) * n[2];
+        const float es = Lat<Q>::cx(i) * Sv[0] + Lat<Q>::cy(i) * Sv[1] + Lat<Q>::cz(i) * Sv[2];
+        const float eg = Lat<Q>::cx(i) * gx + Lat<Q>::cy(i) * gy + Lat<Q>::cz(i) * gz;
+        const float gam = 3.f * eu + 4.5f * eu * eu - 1.5f * u2;
+        const float pis = sg * ((float)Lat<Q>::e2(i) - en * en - trc3);
+        const float fdev = t * (dP + rho * gam - 4.5f * pis);                        // f*_i - t_i w0
+        const float gdev = t * (Phi + phi * gam + P.tau_phi * es) - t * tnq * eg;  // g*_i - t_i phi_ref
+        fsum += fdev;
+        if (i > 0) Store<S>::store(moving_plane<S>(fg, P.N, i) + c, fdev, gdev, P);
+    }
+    // plane 0: sum_i f*_i - w0, and phi (= sum_i g*_i) as the integer phi * 2^30
+    moment_plane(fg)[c] = make_float2(fsum, __int_as_float(__float2int_rn(phi * 1073741824.0f)));
 }
 
-cudaError_t launch_upsample_slab(const Params& P, const float* coarse, int factor, int z0, int nzs, double* phis,
-                                 double* us, double* ps, cudaStream_t s) {
-    const dim3 block(32, 4), grid((P.nx + 31) / 32, (P.ny + 3) / 4, nzs + 2);
-    upsample_kernel<<<grid, block, 0, s>>>(P, coarse, factor, z0, nzs, phis, us, ps);
+cudaError_t launch_restart(const Params& P, const float* coarse, int factor, double p0, void* fg, cudaStream_t s) {
+    const dim3 block(32, 4), grid((P.nx + 31) / 32, (P.ny + 3) / 4, P.nz);
+#define LBM_RESTART(Q, S) restart_kernel<Q, S><<<grid, block, 0, s>>>(P, coarse, factor, (float)p0, fg)
+    if (P.Q == 9) {
+        if (P.storage == STORE_F16) LBM_RESTART(9, STORE_F16);
+        else if (P.storage == STORE_BF16) LBM_RESTART(9, STORE_BF16);
+        else LBM_RESTART(9, STORE_F32);
+    } else {
+        if (P.storage == STORE_F16) LBM_RESTART(19, STORE_F16);
+        else if (P.storage == STORE_BF16) LBM_RESTART(19, STORE_BF16);
+        else LBM_RESTART(19, STORE_F32);
+    }
+#undef LBM_RESTART
     return cudaGetLastError();
 }
 

@@ -102,6 +102,7 @@ SIGNATURES = [
     ("lbm_surrogate_jump", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
                                           ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                           ctypes.POINTER(lbm_jump_report)]),
+    ("lbm_surrogate_reserve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
 ]
 
 _lib = None
@@ -508,6 +509,10 @@ def lbm_coarse_fields(h, factor, out_ptr):
 
 def lbm_restart_from_coarse(h, factor, coarse_ptr, p0=1.0 / 3.0):
     _check(h, load().lbm_restart_from_coarse(h, int(factor), ctypes.c_void_p(coarse_ptr), float(p0)))
+
+
+def lbm_surrogate_reserve(h, factor):
+    _check(h, load().lbm_surrogate_reserve(h, int(factor)))
 
 
 def lbm_surrogate_jump(h, net, factor, mean_std, k, judge_steps, mass_tol, relax_tol):

@@ -92,6 +92,7 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.lbm_step(None, 1) == lbm.LBM_EINVAL
     assert lib.lbm_mass(None, None, None) == lbm.LBM_EINVAL
     assert lib.lbm_launch_count(None) == 0
+    assert lib.lbm_surrogate_reserve(None, 2) == lbm.LBM_EINVAL
     lib.lbm_destroy(None)
     out = ctypes.c_void_p()
     assert lib.lbm_create(ctypes.byref(out), None, 19, 0.8, 0.8, 0.02, 4.0, 1e-3, 1.0, 1.0, None, None) == lbm.LBM_EINVAL

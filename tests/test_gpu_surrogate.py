@@ -165,13 +165,18 @@ def test_wild_prediction_is_rejected_and_the_lbm_takes_over():
     g, twin = _tgv_lattice(c), _tgv_lattice(c)
     net = _net(True, 1)
     net.set_params(np.random.default_rng(0).normal(0, 1.0, net.param_count).astype(np.float32))
-    rep = lbm.lbm_surrogate_jump(g.h, net, 2, [0.5, 0, 0, 0, 1 / 3, 0.5, 0.04, 0.04, 0.04, 1e-4], 16, 4, 1e-3, 4.0)
-    assert not rep["accepted"]
-    twin.step(16)
-    fa, ga = g.get_pops()
-    fb, gb = twin.get_pops()
-    np.testing.assert_array_equal(fa, fb)
-    np.testing.assert_array_equal(ga, gb)
+    ms = [0.5, 0, 0, 0, 1 / 3, 0.5, 0.04, 0.04, 0.04, 1e-4]
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_surrogate_reserve(g.h, 3)  # 3 does not divide 16
+    # the second jump reuses the workspace the first one allocated
+    for _ in range(2):
+        rep = lbm.lbm_surrogate_jump(g.h, net, 2, ms, 16, 4, 1e-3, 4.0)
+        assert not rep["accepted"]
+        twin.step(16)
+        fa, ga = g.get_pops()
+        fb, gb = twin.get_pops()
+        np.testing.assert_array_equal(fa, fb)
+        np.testing.assert_array_equal(ga, gb)
 
 
 def test_trained_surrogate_beats_persistence_and_is_accepted():
