@@ -40,8 +40,67 @@ __global__ void coarsen_kernel(const Params P, const void* __restrict__ fg, int 
     for (int k = 0; k < 5; ++k) out[k * nc + l] = (float)(acc[k] * inv);
 }
 
+// The same block means for factors f that divide 32: lane l of a warp takes fine x = 32 b + l,
+// so a warp reads 32 consecutive cells of each plane, loops over the f x f rows of its coarse
+// cells and sums across each aligned group of f lanes (one coarse cell) with shuffles.
+template <int Q, int S, bool GEN>
+__global__ void coarsen_lanes_kernel(const Params P, const void* __restrict__ fg, int f, float* __restrict__ out) {
+    const int lane = threadIdx.x;
+    const int x = blockIdx.x * 32 + lane;
+    const int cy = blockIdx.y * blockDim.y + threadIdx.y;
+    const int cz = blockIdx.z;
+    const int ncx = P.nx / f, ncy = P.ny / f, ncz = P.nz / f;
+    if (cy >= ncy) return;  // whole warps leave together
+    const bool valid = x < P.nx;  // whole groups of f lanes are valid or not: f divides nx and 32
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (valid)
+        for (int dz = 0; dz < f; ++dz)
+            for (int dy = 0; dy < f; ++dy) {
+                const int y = cy * f + dy, z = cz * f + dz;
+                const Nbr nb = make_nbr(P, x, y, z);
+                const int c = (z * P.ny + y) * P.nx + x;
+                const WallSide ws = GEN ? make_wall_side(P, x, y, z) : WallSide{};
+                float fb[Q], gb[Q];
+                int phi_fx;
+                pull<Q, true, S, GEN>(P, fg, c, nb, fb, gb, phi_fx, ws);
+                Macro m;
+                macro_flow<Q, GEN>(P, fb, gb, m);
+                macro_interface_df<Q>(P, gb, m);
+                macro_pressure<GEN>(P, m);
+                acc[0] += (double)phi_fx / kPhiFx;
+                acc[1] += m.u[0];
+                acc[2] += m.u[1];
+                acc[3] += m.u[2];
+                acc[4] += (P.w0d + (double)m.P) / 3.0;
+            }
+    for (int o = f >> 1; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+    if (!valid || lane % f) return;
+    const double inv = 1.0 / ((double)f * f * f);
+    const long long nc = (long long)ncx * ncy * ncz, l = ((long long)cz * ncy + cy) * ncx + x / f;
+    for (int k = 0; k < 5; ++k) out[k * nc + l] = (float)(acc[k] * inv);
+}
+
 cudaError_t launch_coarsen(const Params& P, const void* fg, int factor, float* out, cudaStream_t s) {
     const int ncx = P.nx / factor, ncy = P.ny / factor, ncz = P.nz / factor;
+    if (factor <= 32 && 32 % factor == 0) {
+        const dim3 block(32, 4), grid((P.nx + 31) / 32, (ncy + 3) / 4, ncz);
+#define LBM_COARSEN_LANES(Q, S)                                                                   \
+    (P.general ? (coarsen_lanes_kernel<Q, S, true><<<grid, block, 0, s>>>(P, fg, factor, out), 0) \
+               : (coarsen_lanes_kernel<Q, S, false><<<grid, block, 0, s>>>(P, fg, factor, out), 0))
+        if (P.Q == 9) {
+            if (P.storage == STORE_F16) LBM_COARSEN_LANES(9, STORE_F16);
+            else if (P.storage == STORE_BF16) LBM_COARSEN_LANES(9, STORE_BF16);
+            else LBM_COARSEN_LANES(9, STORE_F32);
+        } else {
+            if (P.storage == STORE_F16) LBM_COARSEN_LANES(19, STORE_F16);
+            else if (P.storage == STORE_BF16) LBM_COARSEN_LANES(19, STORE_BF16);
+            else LBM_COARSEN_LANES(19, STORE_F32);
+        }
+#undef LBM_COARSEN_LANES
+        return cudaGetLastError();
+    }
     const dim3 block(32, 4), grid((ncx + 31) / 32, (ncy + 3) / 4, ncz);
 #define LBM_COARSEN(Q, S)                                                                   \
     (P.general ? (coarsen_kernel<Q, S, true><<<grid, block, 0, s>>>(P, fg, factor, out), 0) \

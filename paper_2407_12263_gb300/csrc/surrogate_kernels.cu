@@ -312,27 +312,32 @@ cudaError_t adam(float* p, const float* g, float* m, float* v, long long n, floa
 // The 32 -> 32 channel convolution on the fifth-generation tensor cores (tcgen05), FP16
 // operands, FP32 accumulation in tensor memory.
 //
-// Implicit GEMM: a tile of 128 output voxels (8 in x, 16 in y, one z plane) is the M = 128 side,
+// Implicit GEMM: a step of 128 output voxels (8 in x, 16 in y, one z plane) is the M = 128 side,
 // the 32 output channels the N = 32 side, and the reduction runs over 27 taps x 32 input
-// channels. The haloed input tile (10 x 18 x 3 voxels, 32 channels) sits in shared memory in
-// "chunk planes": element (haloed voxel h, channel k) at (k / 8) * PL + 16 h + 2 (k % 8). In the
+// channels. A haloed input plane (10 x 18 voxels, 32 channels) sits in shared memory in "chunk
+// planes": element (haloed voxel v, channel k) at (k / 8) * PLP + 16 v + 2 (k % 8). In the
 // canonical no-swizzle K-major operand layout (core matrices of 8 rows x 16 bytes), the rows of
 // an 8-voxel x-run are then 16 bytes apart and successive y-runs one haloed row (160 bytes)
 // apart, so the A operand of every tap is the same descriptor at a different start address.
 // The weights of all taps are a preformatted FP16 image (2 KB per tap) loaded once per CTA.
-// One thread issues the 54 MMAs (27 taps x 2 of K = 16) and commits them to an mbarrier; the
-// four warps then read their 32 rows of the accumulator with tcgen05.ld and write the output.
-// Waits are bounded: on a timeout the kernel raises *err, frees its tensor memory and returns.
+//
+// A CTA walks a column of steps along z (a chunk of z planes of one (x, y) tile) with the
+// haloed planes in a ring of four and two accumulators in tensor memory: one thread issues the
+// 54 MMAs of step z (27 taps x 2 of K = 16) and commits them to an mbarrier; meanwhile the
+// threads stage plane z + 2 into the slot step z - 1 read, and the four epilogue warps read the
+// accumulator of step z - 1 (tcgen05.ld) and write its output. Waits are bounded: on a timeout
+// the kernel raises *err, waits once more for its MMAs, frees its tensor memory and returns.
 // ---------------------------------------------------------------------------------------
 namespace tc {
 
-constexpr int TX = 8, TY = 16, HX = TX + 2, HY = TY + 2, HZ = 3;
-constexpr int HALO = HX * HY * HZ;           // 540 haloed voxels
-constexpr uint32_t PL = HALO * 16;           // bytes of one chunk plane (8 channels)
-constexpr uint32_t A_BYTES = 4 * PL;         // 32 channels
+constexpr int TX = 8, TY = 16, HX = TX + 2, HY = TY + 2;
+constexpr int HPLANE = HX * HY;               // 180 haloed voxels per z plane
+constexpr uint32_t PLP = HPLANE * 16;         // bytes of one chunk plane (8 channels) of a z plane
+constexpr uint32_t SLOT_BYTES = 4 * PLP;      // 32 channels: 11,520
+constexpr int CONV_THREADS = 256;
 constexpr uint32_t W_TAP = 2048;             // bytes of one tap's 32 x 32 FP16 weights
 constexpr uint32_t W_BYTES = 27 * W_TAP;
-constexpr uint32_t SMEM = A_BYTES + W_BYTES;
+constexpr uint32_t SMEM = 4 * SLOT_BYTES + W_BYTES;  // 101,376: two CTAs per SM
 constexpr long long kSpin = 1ll << 26;        // polls of an mbarrier before giving up
 
 // offset of weight (out n, in k) of a tap inside its 2 KB block: core matrix (k/8, n/8)
@@ -367,30 +372,53 @@ __device__ inline bool wait_parity(uint32_t mbar, uint32_t parity) {
     return false;
 }
 
+// One haloed z plane zz of the input into a ring slot, converted to FP16 and scaled (channels
+// >= cin are zero): a thread takes one haloed voxel, all 32 channels in flight, and writes 8
+// channels (16 bytes) at a time.
+template <typename TIN>
+__device__ __forceinline__ void conv_stage_plane(unsigned char* slot, const TIN* __restrict__ inb, int cin, float in_scale,
+                                                 long long vox, int zz, int y0, int x0, int H, int Wd) {
+    for (int v = threadIdx.x; v < HPLANE; v += CONV_THREADS) {
+        const int hx = v % HX, hy = v / HX;
+        const long long goff = ((long long)zz * H + wrap(y0 + hy - 1, H)) * Wd + wrap(x0 + hx - 1, Wd);
+        float f[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) f[c] = c < cin ? to_f(inb[(long long)c * vox + goff]) : 0.f;
+#pragma unroll
+        for (int c8 = 0; c8 < 4; ++c8) {
+            __half2 q[4];
+#pragma unroll
+            for (int j2 = 0; j2 < 4; ++j2) q[j2] = __floats2half2_rn(f[8 * c8 + 2 * j2] * in_scale, f[8 * c8 + 2 * j2 + 1] * in_scale);
+            *reinterpret_cast<uint4*>(slot + c8 * PLP + v * 16) = *reinterpret_cast<const uint4*>(q);
+        }
+    }
+}
+
 template <typename TIN, int MODE, typename TOUT>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(CONV_THREADS, 2)
 conv32_tc_kernel(const TIN* __restrict__ in, int cin, float in_scale, const __half* __restrict__ wimg,
                  const float* __restrict__ bias, TOUT* __restrict__ out, int cout, int D, int H, int Wd, int tiles_x,
-                 int tiles_y, int n_tiles, int* __restrict__ err) {
+                 int tiles_y, int zchunk, int n_chunks, int n_columns, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* sA = smem;
-    unsigned char* sW = smem + A_BYTES;
-    __shared__ __align__(8) unsigned long long mbar;
+    unsigned char* sA = smem;                   // ring of four haloed planes
+    unsigned char* sW = smem + 4 * SLOT_BYTES;  // weights of the 27 taps
+    __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int s_fail;
     const int t = threadIdx.x;
-    const uint32_t mbar_a = (uint32_t)__cvta_generic_to_shared(&mbar);
+    const uint32_t mbar0 = (uint32_t)__cvta_generic_to_shared(&mbar[0]);  // barrier k at mbar0 + 8 k
     if (t == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_a));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar0));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar0 + 8));
         s_fail = 0;
     }
-    if (t < 32) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(
+    if (t < 32) {  // two 32-column accumulators
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(
             (uint32_t)__cvta_generic_to_shared(&tmem_slot)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     // weights: the preformatted image, 16 bytes at a time
-    for (int i = t; i < (int)(W_BYTES / 16); i += 128)
+    for (int i = t; i < (int)(W_BYTES / 16); i += CONV_THREADS)
         reinterpret_cast<uint4*>(sW)[i] = __ldg(reinterpret_cast<const uint4*>(wimg) + i);
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -398,64 +426,19 @@ conv32_tc_kernel(const TIN* __restrict__ in, int cin, float in_scale, const __ha
     const uint32_t tmem = tmem_slot;
     const uint32_t a_addr = (uint32_t)__cvta_generic_to_shared(sA), w_addr = (uint32_t)__cvta_generic_to_shared(sW);
     const long long vox = (long long)D * H * Wd;
-    const int tiles_xy = tiles_x * tiles_y, tiles_per_b = tiles_xy * D;
     const float out_scale = 1.0f / in_scale;  // in_scale is a power of two: exact
-    uint32_t phase = 0;
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const int b = tile / tiles_per_b, r = tile - b * tiles_per_b;
-        const int z0 = r / tiles_xy, ty = (r - z0 * tiles_xy) / tiles_x, tx = r - z0 * tiles_xy - ty * tiles_x;
-        const int x0 = tx * TX, y0 = ty * TY;
-        const TIN* inb = in + (long long)b * cin * vox;
-        // stage the haloed tile, converted to FP16, in chunk planes (channels >= cin are zero):
-        // a thread takes one haloed voxel, all 32 channels in flight, and writes 8 channels (16
-        // bytes) at a time
-        for (int h = t; h < HALO; h += 128) {
-            const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
-            const long long goff =
-                ((long long)wrap(z0 + hz - 1, D) * H + wrap(y0 + hy - 1, H)) * Wd + wrap(x0 + hx - 1, Wd);
-            float v[32];
-#pragma unroll
-            for (int c = 0; c < 32; ++c) v[c] = c < cin ? to_f(inb[(long long)c * vox + goff]) : 0.f;
-#pragma unroll
-            for (int c8 = 0; c8 < 4; ++c8) {
-                __half2 q[4];
-#pragma unroll
-                for (int j2 = 0; j2 < 4; ++j2)
-                    q[j2] = __floats2half2_rn(v[8 * c8 + 2 * j2] * in_scale, v[8 * c8 + 2 * j2 + 1] * in_scale);
-                *reinterpret_cast<uint4*>(sA + c8 * PL + h * 16) = *reinterpret_cast<const uint4*>(q);
-            }
-        }
-        asm volatile("fence.proxy.async.shared::cta;");
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        if (t == 0) {
-            const uint32_t h0 = (uint32_t)((HY + 1) * HX + 1);  // haloed index of output voxel (0, 0, 0)
-            for (int tap = 0; tap < 27; ++tap) {
-                const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-                const int shift = (dz - 1) * HY * HX + (dy - 1) * HX + (dx - 1);
-                for (int kk = 0; kk < 2; ++kk) {
-                    const uint64_t ad = smem_desc(a_addr + (uint32_t)(2 * kk) * PL + (uint32_t)((int)h0 + shift) * 16, PL, HX * 16);
-                    const uint64_t bd = smem_desc(w_addr + (uint32_t)tap * W_TAP + (uint32_t)(2 * kk) * 512, 512, 128);
-                    const uint32_t acc = (tap | kk) ? 1u : 0u;
-                    asm volatile(
-                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
-                        "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
-                }
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_a));
-        }
-        const bool ok = wait_parity(mbar_a, phase);
-        phase ^= 1u;
-        if (!ok) {
-            s_fail = 1;
-            atomicExch(err, 1);
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        __syncthreads();
-        if (s_fail) break;
-        // the accumulator: warp w holds rows 32 w .. 32 w + 31 (row m = 8 ly + lx)
+    uint32_t phase = 0u, pending = 0u;        // per barrier k (bit k): the parity it waits for; a commit not waited for
+    auto drain = [&](int k) {
+        if (!((pending >> k) & 1u)) return true;
+        if (!wait_parity(mbar0 + 8u * (uint32_t)k, (phase >> k) & 1u)) return false;
+        phase ^= 1u << k;
+        pending &= ~(1u << k);
+        return true;
+    };
+    // the output of a finished step from accumulator k: warp w < 4 holds rows 32 w .. 32 w + 31
+    // (row m = 8 ly + lx)
+    auto epilogue = [&](int k, int b, int z, int x0, int y0) {
+        if (t >= 128) return;
         const int warp = t / 32;
         uint32_t v[32];
         asm volatile(
@@ -465,65 +448,227 @@ conv32_tc_kernel(const TIN* __restrict__ in, int cin, float in_scale, const __ha
               "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
               "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
               "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-            : "r"(tmem + ((uint32_t)(warp * 32) << 16)));
+            : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(k * 32)));
         asm volatile("tcgen05.wait::ld.sync.aligned;");
-        const int m = t, lx = m % TX, ly = m / TX;
+        const int lx = t % TX, ly = t / TX;
         const int x = x0 + lx, y = y0 + ly;
         if (x < Wd && y < H) {
-            const long long vv = ((long long)z0 * H + y) * Wd + x;
+            const long long vv = ((long long)z * H + y) * Wd + x;
             TOUT* ob = out + (long long)b * cout * vox;
 #pragma unroll
             for (int o = 0; o < 32; ++o) {
-                if (o >= cout) break;
-                float a = __uint_as_float(v[o]) * out_scale + (bias ? bias[o] : 0.f);
-                if (MODE == 1) a = fmaxf(a, 0.f);
-                ob[(long long)o * vox + vv] = from_f<TOUT>(a);
+                if (o < cout) {
+                    float a = __uint_as_float(v[o]) * out_scale + (bias ? __ldg(bias + o) : 0.f);
+                    if (MODE == 1) a = fmaxf(a, 0.f);
+                    ob[(long long)o * vox + vv] = from_f<TOUT>(a);
+                }
             }
         }
-        // every thread is done with the accumulator and the staged tile before the next MMAs
+    };
+    for (int col = blockIdx.x; col < n_columns && !s_fail; col += gridDim.x) {
+        int r = col;
+        const int zc = r % n_chunks;
+        r /= n_chunks;
+        const int tx = r % tiles_x;
+        r /= tiles_x;
+        const int ty = r % tiles_y;
+        const int b = r / tiles_y;
+        const int x0 = tx * TX, y0 = ty * TY;
+        const int z_begin = zc * zchunk, z_end = min(z_begin + zchunk, D);
+        const TIN* inb = in + (long long)b * cin * vox;
+        // prologue: planes z_begin - 1 .. z_begin + 1 in ring slots 0..2
+        for (int j = 0; j < 3; ++j)
+            conv_stage_plane(sA + j * SLOT_BYTES, inb, cin, in_scale, vox, wrap(z_begin - 1 + j, D), y0, x0, H, Wd);
+        for (int z = z_begin; z < z_end; ++z) {
+            const int zi = z - z_begin, k = zi & 1;  // accumulator and barrier of this step
+            asm volatile("fence.proxy.async.shared::cta;");
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (s_fail) break;
+            if (t == 0) {
+                for (int tap = 0; tap < 27; ++tap) {
+                    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+                    // haloed voxel of output (0, 0) shifted by (dx - 1, dy - 1), in plane z + dz - 1
+                    const uint32_t a0 = a_addr + (uint32_t)((zi + dz) & 3) * SLOT_BYTES + (uint32_t)(dy * HX + dx) * 16;
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                        const uint64_t ad = smem_desc(a0 + (uint32_t)(2 * kk) * PLP, PLP, HX * 16);
+                        const uint64_t bd = smem_desc(w_addr + (uint32_t)tap * W_TAP + (uint32_t)(2 * kk) * 512, 512, 128);
+                        const uint32_t acc = (tap | kk) ? 1u : 0u;
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem + (uint32_t)(k * 32)),
+                            "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar0 + 8u * (uint32_t)k));
+            }
+            pending |= 1u << k;
+            if (zi > 0) {
+                // step z - 1 is done: its output, then its ring slot takes plane z + 2
+                if (!drain(k ^ 1)) {
+                    s_fail = 1;
+                    atomicExch(err, 1);
+                } else {
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    epilogue(k ^ 1, b, z - 1, x0, y0);
+                }
+            }
+            if (z + 1 < z_end)
+                conv_stage_plane(sA + (uint32_t)((zi + 3) & 3) * SLOT_BYTES, inb, cin, in_scale, vox, wrap(z + 2, D), y0, x0, H, Wd);
+            // the epilogue's reads of accumulator k ^ 1 come before the next step's MMAs into it
+            asm volatile("tcgen05.fence::before_thread_sync;");
+        }
+        // the column's last step
+        const int kl = (z_end - 1 - z_begin) & 1;
+        if (!s_fail) {
+            if (!drain(kl)) {
+                s_fail = 1;
+                atomicExch(err, 1);
+            } else {
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                epilogue(kl, b, z_end - 1, x0, y0);
+            }
+        }
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
     }
+    // on a timeout, one more bounded wait for MMAs still in flight before the memory is freed
+    for (int kb = 0; kb < 2; ++kb) drain(kb);
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (t < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
+    if (t < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
 }
 
 // ---------------------------------------------------------------------------------------
 // Weight gradients on the tensor cores:
 //   gW[o][c][tap] = sum over voxels v of h[c][v + off(tap)] g[o][v],
 // a GEMM over the voxels for each of the 9 (dz, dy) pairs: D_(dz,dy)[m][o] with the M = 128 rows
-// m = 32 dx + c (dx = 0, 1, 2 and a fourth, zero, slot) and N = 32 columns o. A tile is 8 voxels
-// in x by 16 in y in one z plane (K = 128). The haloed rows of h (3 z-planes x 18 y-rows) are
-// staged as three x-shifted copies of each 8-voxel row side by side: element (row r, dx, c, lx)
-// at 2048 r + 512 dx + 16 c + 2 lx holds h[c][z0 + hz - 1][y0 + hy - 1][x0 + lx + dx - 1]. In the
-// K-major no-swizzle layout that is an operand with 128 bytes between groups of 8 rows (SBO) and
-// 2 KB between successive 8-voxel K chunks (LBO), the pair (dz, dy) selecting the start row. g is
-// staged the same way as the N x K operand (16 o + 2 lx within a 512-byte row). Nine 128 x 32
-// FP32 accumulators live in tensor memory (288 of 512 columns; one CTA per SM) for all the tiles
-// a CTA takes, and are added to gW at the end.
+// m = 32 dx + c (dx = 0, 1, 2 and a fourth, zero, slot) and N = 32 columns o. A step is 8 voxels
+// in x by 16 in y in one z plane (K = 128). A haloed row of h (18 y-rows per z plane) is staged
+// as three x-shifted copies of its 8-voxel run side by side: element (row r, dx, c, lx) at
+// 2048 r + 512 dx + 16 c + 2 lx holds h[c][z][y0 + r - 1][x0 + lx + dx - 1]. In the K-major
+// no-swizzle layout that is an operand with 128 bytes between groups of 8 rows (SBO) and 2 KB
+// between successive 8-voxel K chunks (LBO), the pair (dz, dy) selecting the plane and the start
+// row. g is staged the same way as the N x K operand (16 o + 2 lx within a 512-byte row).
+//
+// A CTA walks a column of steps along z (a chunk of z planes of one (x, y) tile), keeping the
+// haloed planes in a ring of four: step z reads planes z - 1, z, z + 1 while the 256 threads
+// stage plane z + 2 and g of step z + 1 (the plane and g buffers that step z - 1 read, waited
+// for on its mbarrier). Nine 128 x 32 FP32 accumulators live in tensor memory (288 of 512
+// columns; one CTA per SM) for all the columns a CTA takes, and are added to gW at the end.
 // ---------------------------------------------------------------------------------------
-constexpr int WG_TX = 8, WG_TY = 16, WG_ROWS = 3 * (WG_TY + 2);  // 54 haloed x-rows
-constexpr uint32_t WG_ROW_BYTES = 4 * 512;                       // 4 dx slots x 32 channels x 8 voxels
-constexpr uint32_t WG_H_BYTES = WG_ROWS * WG_ROW_BYTES;           // 110,592
-constexpr uint32_t WG_G_BYTES = WG_TY * 512;                      // 8,192
-constexpr uint32_t WG_SMEM = WG_H_BYTES + WG_G_BYTES;
+constexpr int WG_TX = 8, WG_TY = 16, WG_HY = WG_TY + 2;        // 18 haloed rows per plane
+constexpr int WG_THREADS = 256;
+constexpr int WG_ZCHUNK = 16;                                   // z planes per column
+constexpr uint32_t WG_ROW_BYTES = 4 * 512;                      // 4 dx slots x 32 channels x 8 voxels
+constexpr uint32_t WG_PLANE_BYTES = WG_HY * WG_ROW_BYTES;        // 36,864
+constexpr uint32_t WG_G_BYTES = WG_TY * 512;                     // 8,192
+constexpr uint32_t WG_SMEM = 4 * WG_PLANE_BYTES + 2 * WG_G_BYTES; // 163,840
+
+// Eight consecutive values of a row as floats. vec: the row start is 16-byte aligned and all
+// eight lie inside the row (no wrap).
+__device__ __forceinline__ void load8(const __half* p, bool vec, int x0, int Wd, float (&v)[8]) {
+    if (vec) {
+        const uint4 q = __ldg(reinterpret_cast<const uint4*>(p + x0));
+        const __half2* h2 = reinterpret_cast<const __half2*>(&q);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float2 f = __half22float2(h2[j]);
+            v[2 * j] = f.x;
+            v[2 * j + 1] = f.y;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = __half2float(p[wrap(x0 + j, Wd)]);
+    }
+}
+__device__ __forceinline__ void load8(const float* p, bool vec, int x0, int Wd, float (&v)[8]) {
+    if (vec) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(p + x0)), b = __ldg(reinterpret_cast<const float4*>(p + x0 + 4));
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = p[wrap(x0 + j, Wd)];
+    }
+}
+
+// Plane zz of h into a ring slot: a thread takes one (row, channel), loads its ten x-values
+// (x0 - 1 .. x0 + 8, periodic) and writes the three shifted 8-voxel windows, 16 bytes each.
+template <typename TH>
+__device__ __forceinline__ void wg_stage_plane(unsigned char* slot, const TH* __restrict__ hb, int cin, long long vox,
+                                               int zz, int y0, int x0, int H, int Wd, bool vec) {
+    for (int task = threadIdx.x; task < WG_HY * 32; task += WG_THREADS) {
+        const int r = task / 32, c = task % 32;
+        float v[WG_TX + 2];
+        if (c < cin) {
+            const TH* row = hb + (long long)c * vox + ((long long)zz * H + wrap(y0 + r - 1, H)) * Wd;
+            float m[8];
+            load8(row, vec, x0, Wd, m);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j + 1] = m[j];
+            v[0] = to_f(row[wrap(x0 - 1, Wd)]);
+            v[WG_TX + 1] = to_f(row[wrap(x0 + WG_TX, Wd)]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < WG_TX + 2; ++q) v[q] = 0.f;
+        }
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+            __half2 w2[4];
+#pragma unroll
+            for (int j2 = 0; j2 < 4; ++j2) w2[j2] = __floats2half2_rn(v[dx + 2 * j2], v[dx + 2 * j2 + 1]);
+            *reinterpret_cast<uint4*>(slot + r * WG_ROW_BYTES + dx * 512 + c * 16) = *reinterpret_cast<const uint4*>(w2);
+        }
+    }
+}
+
+// g of the step's own voxels (zero outside the grid and for o >= cout), scaled; one (row,
+// output channel) per thread, 8 voxels in one 16-byte store.
+__device__ __forceinline__ void wg_stage_g(unsigned char* buf, const float* __restrict__ gb, int cout, long long vox,
+                                           float g_scale, int z, int y0, int x0, int H, int Wd, bool vec) {
+    for (int task = threadIdx.x; task < WG_TY * 32; task += WG_THREADS) {
+        const int ly = task / 32, o = task % 32;
+        const int y = y0 + ly;
+        float v[8];
+        if (o < cout && y < H) {
+            const float* row = gb + (long long)o * vox + ((long long)z * H + y) * Wd;
+            if (vec) {
+                load8(row, true, x0, Wd, v);
+            } else {
+#pragma unroll
+                for (int lx = 0; lx < WG_TX; ++lx) v[lx] = (x0 + lx < Wd) ? row[x0 + lx] : 0.f;
+            }
+        } else {
+#pragma unroll
+            for (int lx = 0; lx < WG_TX; ++lx) v[lx] = 0.f;
+        }
+        __half2 w2[4];
+#pragma unroll
+        for (int j2 = 0; j2 < 4; ++j2) w2[j2] = __floats2half2_rn(v[2 * j2] * g_scale, v[2 * j2 + 1] * g_scale);
+        *reinterpret_cast<uint4*>(buf + ly * 512 + o * 16) = *reinterpret_cast<const uint4*>(w2);
+    }
+}
 
 template <typename TH>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(WG_THREADS, 1)
 wgrad32_tc_kernel(const float* __restrict__ g, int cout, float g_scale, const TH* __restrict__ h, int cin,
-                  float* __restrict__ gW, int D, int H, int Wd, int tiles_x, int tiles_y, int n_tiles, int* __restrict__ err) {
+                  float* __restrict__ gW, int D, int H, int Wd, int tiles_x, int tiles_y, int n_chunks, int n_columns,
+                  int vec_h, int vec_g, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* sH = smem;
-    unsigned char* sG = smem + WG_H_BYTES;
-    __shared__ __align__(8) unsigned long long mbar;
+    unsigned char* sH = smem;                       // ring of four haloed planes
+    unsigned char* sG = smem + 4 * WG_PLANE_BYTES;  // two g buffers
+    __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int s_fail;
     const int t = threadIdx.x;
-    const uint32_t mbar_a = (uint32_t)__cvta_generic_to_shared(&mbar);
+    const uint32_t mbar0 = (uint32_t)__cvta_generic_to_shared(&mbar[0]);  // barrier k at mbar0 + 8 k
     if (t == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_a));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar0));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar0 + 8));
         s_fail = 0;
     }
     if (t < 32) {
@@ -532,92 +677,92 @@ wgrad32_tc_kernel(const float* __restrict__ g, int cout, float g_scale, const TH
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     // the fourth dx slot of every row stays zero
-    for (int i = t; i < (int)(WG_H_BYTES / 16); i += 128) reinterpret_cast<uint4*>(sH)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = t; i < (int)(4 * WG_PLANE_BYTES / 16); i += WG_THREADS) reinterpret_cast<uint4*>(sH)[i] = make_uint4(0, 0, 0, 0);
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_slot;
     const uint32_t h_addr = (uint32_t)__cvta_generic_to_shared(sH), g_addr = (uint32_t)__cvta_generic_to_shared(sG);
     const long long vox = (long long)D * H * Wd;
-    const int tiles_xy = tiles_x * tiles_y, tiles_per_b = tiles_xy * D;
     constexpr uint32_t kIdescW = (1u << 4) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
-    uint32_t phase = 0;
+    uint32_t phase = 0u, pending = 0u;  // bit k: the parity barrier k waits for; a commit on it not yet waited for
     bool first = true;
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const int b = tile / tiles_per_b, r0 = tile - b * tiles_per_b;
-        const int z0 = r0 / tiles_xy, ty = (r0 - z0 * tiles_xy) / tiles_x, tx = r0 - z0 * tiles_xy - ty * tiles_x;
+    // waits for the MMAs committed on barrier k, if any; false on a timeout (they stay pending)
+    auto drain = [&](int k) {
+        if (!((pending >> k) & 1u)) return true;
+        if (!wait_parity(mbar0 + 8u * (uint32_t)k, (phase >> k) & 1u)) return false;
+        phase ^= 1u << k;
+        pending &= ~(1u << k);
+        return true;
+    };
+    const bool vh = vec_h != 0, vg = vec_g != 0;
+    for (int col = blockIdx.x; col < n_columns && !s_fail; col += gridDim.x) {
+        int r = col;
+        const int zc = r % n_chunks;
+        r /= n_chunks;
+        const int tx = r % tiles_x;
+        r /= tiles_x;
+        const int ty = r % tiles_y;
+        const int b = r / tiles_y;
         const int x0 = tx * WG_TX, y0 = ty * WG_TY;
-        // h: rows (hz, hy), three x-shifted copies: a thread takes one (row, channel), loads its
-        // ten x-values once and writes the three shifted 8-voxel windows, 16 bytes each
-        for (int pr2 = t; pr2 < WG_ROWS * 32; pr2 += 128) {
-            const int r = pr2 / 32, c = pr2 % 32;
-            const int hy = r % (WG_TY + 2), hz = r / (WG_TY + 2);
-            float v[WG_TX + 2];
-            if (c < cin) {
-                const long long base = ((long long)b * cin + c) * vox + ((long long)wrap(z0 + hz - 1, D) * H + wrap(y0 + hy - 1, H)) * Wd;
+        const int z_begin = zc * WG_ZCHUNK, z_end = min(z_begin + WG_ZCHUNK, D);
+        const TH* hb = h + (long long)b * cin * vox;
+        const float* gbat = g + (long long)b * cout * vox;
+        // prologue: planes z_begin - 1 .. z_begin + 1 (ring slots 0..2) and g of the first step
+        for (int j = 0; j < 3; ++j)
+            wg_stage_plane(sH + j * WG_PLANE_BYTES, hb, cin, vox, wrap(z_begin - 1 + j, D), y0, x0, H, Wd, vh);
+        wg_stage_g(sG, gbat, cout, vox, g_scale, z_begin, y0, x0, H, Wd, vg);
+        for (int z = z_begin; z < z_end; ++z) {
+            const int zi = z - z_begin;
+            asm volatile("fence.proxy.async.shared::cta;");
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (s_fail) break;
+            const int k = zi & 1;  // barrier and g buffer of this step
+            if (t == 0) {
+                for (int pr = 0; pr < 9; ++pr) {
+                    const int dz = pr / 3, dy = pr % 3;
+                    const uint32_t plane = h_addr + (uint32_t)((zi + dz) & 3) * WG_PLANE_BYTES + (uint32_t)dy * WG_ROW_BYTES;
 #pragma unroll
-                for (int q = 0; q < WG_TX + 2; ++q) v[q] = to_f(h[base + wrap(x0 + q - 1, Wd)]);
-            } else {
-#pragma unroll
-                for (int q = 0; q < WG_TX + 2; ++q) v[q] = 0.f;
-            }
-#pragma unroll
-            for (int dx = 0; dx < 3; ++dx) {
-                __half2 w2[4];
-#pragma unroll
-                for (int j2 = 0; j2 < 4; ++j2) w2[j2] = __floats2half2_rn(v[dx + 2 * j2], v[dx + 2 * j2 + 1]);
-                *reinterpret_cast<uint4*>(sH + r * WG_ROW_BYTES + dx * 512 + c * 16) = *reinterpret_cast<const uint4*>(w2);
-            }
-        }
-        // g: the tile's own voxels (zero outside the grid and for o >= cout), scaled; one
-        // (row, output channel) per thread, 8 voxels in one 16-byte store
-        for (int pr2 = t; pr2 < WG_TY * 32; pr2 += 128) {
-            const int ly = pr2 / 32, o = pr2 % 32;
-            const int y = y0 + ly;
-            float v[WG_TX];
-#pragma unroll
-            for (int lx = 0; lx < WG_TX; ++lx) {
-                const int x = x0 + lx;
-                v[lx] = (o < cout && x < Wd && y < H) ? g[((long long)b * cout + o) * vox + ((long long)z0 * H + y) * Wd + x] * g_scale : 0.f;
-            }
-            __half2 w2[4];
-#pragma unroll
-            for (int j2 = 0; j2 < 4; ++j2) w2[j2] = __floats2half2_rn(v[2 * j2], v[2 * j2 + 1]);
-            *reinterpret_cast<uint4*>(sG + ly * 512 + o * 16) = *reinterpret_cast<const uint4*>(w2);
-        }
-        asm volatile("fence.proxy.async.shared::cta;");
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        if (t == 0) {
-            for (int pr = 0; pr < 9; ++pr) {
-                const int dz = pr / 3, dy = pr % 3;
-                const uint32_t row0 = (uint32_t)(dz * (WG_TY + 2) + dy);
-                for (int kk = 0; kk < WG_TY / 2; ++kk) {  // two 8-voxel rows per MMA (K = 16)
-                    const uint64_t ad = tc::smem_desc(h_addr + (row0 + 2 * kk) * WG_ROW_BYTES, WG_ROW_BYTES, 128);
-                    const uint64_t bd = tc::smem_desc(g_addr + (uint32_t)(2 * kk) * 512, 512, 128);
-                    const uint32_t acc = (first && kk == 0) ? 0u : 1u;
-                    asm volatile(
-                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem + (uint32_t)(pr * 32)),
-                        "l"(ad), "l"(bd), "r"(kIdescW), "r"(acc));
+                    for (int kk = 0; kk < WG_TY / 2; ++kk) {  // two 8-voxel rows per MMA (K = 16)
+                        const uint64_t ad = smem_desc(plane + (uint32_t)(2 * kk) * WG_ROW_BYTES, WG_ROW_BYTES, 128);
+                        const uint64_t bd = smem_desc(g_addr + (uint32_t)k * WG_G_BYTES + (uint32_t)(2 * kk) * 512, 512, 128);
+                        const uint32_t acc = (first && kk == 0) ? 0u : 1u;
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem + (uint32_t)(pr * 32)),
+                            "l"(ad), "l"(bd), "r"(kIdescW), "r"(acc));
+                    }
                 }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar0 + 8u * (uint32_t)k));
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_a));
+            pending |= 1u << k;
+            first = false;
+            if (z + 1 < z_end) {
+                // the buffers of step z - 1 are free once its MMAs are done; stage into them
+                if (!drain(k ^ 1)) {
+                    s_fail = 1;
+                    atomicExch(err, 1);
+                }
+                wg_stage_plane(sH + (uint32_t)((zi + 3) & 3) * WG_PLANE_BYTES, hb, cin, vox, wrap(z + 2, D), y0, x0, H, Wd, vh);
+                wg_stage_g(sG + (uint32_t)(k ^ 1) * WG_G_BYTES, gbat, cout, vox, g_scale, z + 1, y0, x0, H, Wd, vg);
+            }
         }
-        first = false;
-        const bool ok = tc::wait_parity(mbar_a, phase);
-        phase ^= 1u;
-        if (!ok) {
-            s_fail = 1;
-            atomicExch(err, 1);
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;");
+        // the column's last MMAs read the ring: wait for them before the next prologue
+        for (int kb = 0; kb < 2; ++kb)
+            if (!drain(kb)) {
+                s_fail = 1;
+                atomicExch(err, 1);
+            }
         __syncthreads();
-        if (s_fail) break;
     }
-    // read the nine accumulators out: warp w holds rows 32 w .. 32 w + 31, i.e. dx = w, c = lane
-    if (!s_fail && !first) {
+    // on a timeout, one more bounded wait for MMAs still in flight before the memory is freed
+    for (int kb = 0; kb < 2; ++kb) drain(kb);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    __syncthreads();
+    // read the nine accumulators out: warp w < 4 holds rows 32 w .. 32 w + 31, i.e. dx = w, c = lane
+    if (!s_fail && !first && t < 128) {
         const int warp = t / 32, c = t % 32;
         const float inv = 1.0f / g_scale;
         for (int pr = 0; pr < 9; ++pr) {
@@ -633,7 +778,9 @@ wgrad32_tc_kernel(const float* __restrict__ g, int cout, float g_scale, const TH
             asm volatile("tcgen05.wait::ld.sync.aligned;");
             if (warp < 3 && c < cin) {
                 const int tap = 9 * (pr / 3) + 3 * (pr % 3) + warp;
-                for (int o = 0; o < cout; ++o) atomicAdd(&gW[((long long)o * cin + c) * 27 + tap], __uint_as_float(v[o]) * inv);
+#pragma unroll
+                for (int o = 0; o < 32; ++o)
+                    if (o < cout) atomicAdd(&gW[((long long)o * cin + c) * 27 + tap], __uint_as_float(v[o]) * inv);
             }
         }
     }
@@ -687,22 +834,26 @@ cudaError_t wgrad32_tc(const float* g, int cout, float g_scale, const void* h, i
                        int batch, int D, int H, int Wd, int* err, cudaStream_t s) {
     if (cin > 32 || cout > 32) return cudaErrorInvalidValue;
     const int tx = (Wd + tc::WG_TX - 1) / tc::WG_TX, ty = (H + tc::WG_TY - 1) / tc::WG_TY;
-    const int n_tiles = tx * ty * D * batch;
+    const int n_chunks = (D + tc::WG_ZCHUNK - 1) / tc::WG_ZCHUNK;
+    const int n_columns = tx * ty * n_chunks * batch;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int blocks = n_tiles < sms ? n_tiles : sms;  // 512 tensor-memory columns each: one per SM
+    const int blocks = n_columns < sms ? n_columns : sms;  // 512 tensor-memory columns each: one per SM
+    // 16-byte row loads where every 8-voxel run is aligned and inside its row
+    const int vec_h = (Wd % 8 == 0) && ((uintptr_t)h % 16 == 0);
+    const int vec_g = (Wd % 8 == 0) && ((uintptr_t)g % 16 == 0);
     cudaError_t e;
     if (h_fp16) {
         e = cudaFuncSetAttribute(tc::wgrad32_tc_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::WG_SMEM);
         if (e != cudaSuccess) return e;
-        tc::wgrad32_tc_kernel<__half><<<blocks, 128, tc::WG_SMEM, s>>>(g, cout, g_scale, (const __half*)h, cin, gW, D, H, Wd, tx, ty,
-                                                               n_tiles, err);
+        tc::wgrad32_tc_kernel<__half><<<blocks, tc::WG_THREADS, tc::WG_SMEM, s>>>(
+            g, cout, g_scale, (const __half*)h, cin, gW, D, H, Wd, tx, ty, n_chunks, n_columns, vec_h, vec_g, err);
     } else {
         e = cudaFuncSetAttribute(tc::wgrad32_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::WG_SMEM);
         if (e != cudaSuccess) return e;
-        tc::wgrad32_tc_kernel<float><<<blocks, 128, tc::WG_SMEM, s>>>(g, cout, g_scale, (const float*)h, cin, gW, D, H, Wd, tx, ty,
-                                                              n_tiles, err);
+        tc::wgrad32_tc_kernel<float><<<blocks, tc::WG_THREADS, tc::WG_SMEM, s>>>(
+            g, cout, g_scale, (const float*)h, cin, gW, D, H, Wd, tx, ty, n_chunks, n_columns, vec_h, vec_g, err);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -716,16 +867,19 @@ cudaError_t conv32_tc(const void* in, int in_fp16, int cin, float in_scale, cons
                       int out_fp16, int cout, int relu, int batch, int D, int H, int Wd, int* err, cudaStream_t s) {
     if (cin > 32 || cout > 32) return cudaErrorInvalidValue;
     const int tx = (Wd + tc::TX - 1) / tc::TX, ty = (H + tc::TY - 1) / tc::TY;
-    const int n_tiles = tx * ty * D * batch;
-    const int blocks = n_tiles < tc_blocks() ? n_tiles : tc_blocks();
+    // z chunks of 8 planes: 10 staged planes per 8 steps, and enough columns to fill the GPU
+    const int zchunk = D < 8 ? D : 8;
+    const int n_chunks = (D + zchunk - 1) / zchunk;
+    const int n_columns = tx * ty * n_chunks * batch;
+    const int blocks = n_columns < tc_blocks() ? n_columns : tc_blocks();
 #define LBM_TC(TIN, MODE, TOUT)                                                                                    \
     do {                                                                                                           \
         cudaError_t e_ = cudaFuncSetAttribute(tc::conv32_tc_kernel<TIN, MODE, TOUT>,                              \
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM);         \
         if (e_ != cudaSuccess) return e_;                                                                          \
-        tc::conv32_tc_kernel<TIN, MODE, TOUT><<<blocks, 128, tc::SMEM, s>>>((const TIN*)in, cin, in_scale, wimg, bias,     \
-                                                                            (TOUT*)out, cout, D, H, Wd, tx, ty,    \
-                                                                            n_tiles, err);                         \
+        tc::conv32_tc_kernel<TIN, MODE, TOUT><<<blocks, tc::CONV_THREADS, tc::SMEM, s>>>(                          \
+            (const TIN*)in, cin, in_scale, wimg, bias, (TOUT*)out, cout, D, H, Wd, tx, ty, zchunk, n_chunks,       \
+            n_columns, err);                                                                                       \
     } while (0)
     if (in_fp16 && out_fp16 && relu) LBM_TC(__half, 1, __half);
     else if (!in_fp16 && !out_fp16 && !relu) LBM_TC(float, 0, float);

@@ -76,14 +76,21 @@ def test_forward_matches_oracle(fp16, tol):
         assert np.abs(y[b] - want).max() <= tol * scale
 
 
-@pytest.mark.parametrize("fp16,tol,cw", [(False, 1e-5, None), (True, 2e-2, None), (False, 1e-5, (1, 30, 30, 30, 0.5))])
-def test_gradients_match_oracle(fp16, tol, cw):
+@pytest.mark.parametrize("fp16,tol,cw,grid", [
+    (False, 1e-5, None, (8, 8, 8)),
+    (True, 2e-2, None, (8, 8, 8)),
+    (False, 1e-5, (1, 30, 30, 30, 0.5), (8, 8, 8)),
+    # tensor-core paths: x not a multiple of 8 (element-wise staging), two y tiles, z in two
+    # chunks of the weight-gradient pipeline; and aligned rows over three z chunks
+    (True, 2e-2, None, (12, 20, 18)),
+    (True, 2e-2, None, (16, 16, 34)),
+])
+def test_gradients_match_oracle(fp16, tol, cw, grid):
     net, weights = _random_net(fp16, seed=5)
     if cw is not None:
         net.set_loss_weights(cw)
     rng = np.random.default_rng(12)
-    grid = (8, 8, 8)
-    x = rng.normal(0, 1, (2, 5, 8, 8, 8)).astype(np.float32)
+    x = rng.normal(0, 1, (2, 5) + grid[::-1]).astype(np.float32)
     t = (x + rng.normal(0, 0.3, x.shape)).astype(np.float32)
     xd, td = _dev(x), _dev(t)  # held: the library reads them after this line
     loss = net.gradients(xd.data_ptr(), td.data_ptr(), 2, grid)
