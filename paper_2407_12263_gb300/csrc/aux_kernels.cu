@@ -119,7 +119,7 @@ __global__ void moments_kernel(const Params P, int z0, const void* __restrict__ 
     Macro m;
     macro_flow<Q, GEN>(P, fb, gb, m);
     if (SCHEME == SCHEME_DF) {
-        macro_interface_df<Q>(P, gb, m);
+        macro_interface_df<Q>(P, m);
     } else {
         float gx, gy, gz;
         fd_gradient<Q>(phi_fd, c, GEN ? mirror_at_walls(nb, ws) : nb, gx, gy, gz);

@@ -133,7 +133,9 @@ __device__ __forceinline__ void pull(const Params& P, const void* __restrict__ s
     constexpr float sf = RAW ? 1.0f : St::kInvF, sg = RAW ? 1.0f : St::kInvG;
     float df = 0.f;                 // increment of sum f, storage units
     unsigned int dphi = 0u;         // increment of phi_fx (wraps; the true sum fits in 32 bits)
-    const float fa = P.flux_a * St::kInvG, fbk = P.flux_b * St::kInvG;
+    const float fa = P.flux_as, fbk = P.flux_bs;  // flux_a, flux_b times the storage's kInvG
+    const float2 lwm = make_float2(P.lw_m, P.lw_m), lwp = make_float2(P.lw_p, P.lw_p);
+    const float2 nfa = make_float2(-fa, -fa), fbk2 = make_float2(fbk, fbk);
 #pragma unroll
     for (int k = 0; k < Lat<Q>::kPairs; ++k) {
         const int i = Lat<Q>::pair_first(k), j = Lat<Q>::pair_second(k);
@@ -141,19 +143,22 @@ __device__ __forceinline__ void pull(const Params& P, const void* __restrict__ s
         load_link<Q, S, WALLS>(P, state, c, nb, ws, i, rmi, r0i, rpi);
         load_link<Q, S, WALLS>(P, state, c, nb, ws, j, rmj, r0j, rpj);
         const float2 v0i = St::cvt(r0i), v0j = St::cvt(r0j);
-        gb[i] = (v0i.y + (P.lw_m * St::sub_g(rmi, v0i.y) + P.lw_p * St::sub_g(rpi, v0i.y))) * sg;
-        gb[j] = (v0j.y + (P.lw_m * St::sub_g(rmj, v0j.y) + P.lw_p * St::sub_g(rpj, v0j.y))) * sg;
+        // the Lax-Wendroff corrections of (f_i, g_i) and (f_j, g_j), both members at once
+        // (packed FP32 arithmetic, each lane rounded as its scalar form would be)
+        const float2 ei = __ffma2_rn(lwm, St::sub2(rmi, v0i), __fmul2_rn(lwp, St::sub2(rpi, v0i)));
+        const float2 ej = __ffma2_rn(lwm, St::sub2(rmj, v0j), __fmul2_rn(lwp, St::sub2(rpj, v0j)));
+        const float2 bi = __fadd2_rn(v0i, ei), bj = __fadd2_rn(v0j, ej);
+        gb[i] = bi.y * sg;
+        gb[j] = bj.y * sg;
         // net outflow of phi across x + e_i/2 and across x - e_i/2 (= x + e_j/2):
         //   fa (g_i(x) - g_j(x + e_i)) + fbk (g_i(x + e_i) - g_j(x)), and the same with i, j swapped
-        const int out_i = __float2int_rn(__fmaf_rn(-fa, St::sub_g(rmj, v0i.y), __fmul_rn(fbk, St::sub_g(rpi, v0j.y))));
-        const int out_j = __float2int_rn(__fmaf_rn(-fa, St::sub_g(rmi, v0j.y), __fmul_rn(fbk, St::sub_g(rpj, v0i.y))));
-        dphi -= (unsigned int)out_i + (unsigned int)out_j;
+        const float2 out = __ffma2_rn(nfa, make_float2(St::sub_g(rmj, v0i.y), St::sub_g(rmi, v0j.y)),
+                                      __fmul2_rn(fbk2, make_float2(St::sub_g(rpi, v0j.y), St::sub_g(rpj, v0i.y))));
+        dphi -= (unsigned int)__float2int_rn(out.x) + (unsigned int)__float2int_rn(out.y);
         if (WITH_F) {
-            const float ei = P.lw_m * St::sub_f(rmi, v0i.x) + P.lw_p * St::sub_f(rpi, v0i.x);
-            const float ej = P.lw_m * St::sub_f(rmj, v0j.x) + P.lw_p * St::sub_f(rpj, v0j.x);
-            fb[i] = (v0i.x + ei) * sf;
-            fb[j] = (v0j.x + ej) * sf;
-            df += ei + ej;
+            fb[i] = bi.x * sf;
+            fb[j] = bj.x * sf;
+            df += ei.x + ej.x;
         }
     }
     const float2 m0 = __ldg(moment_plane(state) + c);
@@ -172,6 +177,7 @@ struct Macro {
     float Pbar;   // sum fbar - w0
     float P;      // p / cs^2 - w0 = sum fbar - w0 + u . grad rho / 2
     float gnorm;  // |grad phi|
+    float gsum[3];  // sum g_i e_i of the propagated g
 };
 
 // phi, rho, u (Sec. 2.3, Eq. momentum): rho u = sum fbar_i e_i + rho G / 2.
@@ -182,21 +188,29 @@ __device__ __forceinline__ void macro_flow(const Params& P, const float (&fb)[Q]
     m.phi = P.phi_ref + m.Phi;
     m.omphi = (1.f - P.phi_ref) - m.Phi;  // 1 - phi, exact on the phi_ref side
     m.Pbar = fb[0];
-    float jx = 0.f, jy = 0.f, jz = 0.f;
+    // first moments of f and g together, (sum f_i e_i, sum g_i e_i) per axis in packed FP32:
+    // opposite velocities enter as one difference
+    float2 s[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-        if (Lat<Q>::cx(i) > 0) jx += fb[i];
-        if (Lat<Q>::cx(i) < 0) jx -= fb[i];
-        if (Lat<Q>::cy(i) > 0) jy += fb[i];
-        if (Lat<Q>::cy(i) < 0) jy -= fb[i];
-        if (Lat<Q>::cz(i) > 0) jz += fb[i];
-        if (Lat<Q>::cz(i) < 0) jz -= fb[i];
+    for (int k = 0; k < Lat<Q>::kPairs; ++k) {
+        const int i = Lat<Q>::pair_first(k), j = Lat<Q>::pair_second(k);
+        const float2 d = fsub2_rn(make_float2(fb[i], gb[i]), make_float2(fb[j], gb[j]));  // e_i (f_i - f_j)
+        const int e[3] = {Lat<Q>::cx(i), Lat<Q>::cy(i), Lat<Q>::cz(i)};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (e[a] > 0) s[a] = __fadd2_rn(s[a], d);
+            if (e[a] < 0) s[a] = fsub2_rn(s[a], d);
+        }
     }
-    if constexpr (Store<U>::kInvF != 1.0f) {  // exact power-of-two rescaling, kept out of any FMA
-        jx = __fmul_rn(jx, Store<U>::kInvF);
-        jy = __fmul_rn(jy, Store<U>::kInvF);
-        jz = __fmul_rn(jz, Store<U>::kInvF);
+    if constexpr (Store<U>::kInvF != 1.0f || Store<U>::kInvG != 1.0f) {  // to population units: exact
+        const float2 inv = make_float2(Store<U>::kInvF, Store<U>::kInvG);  // powers of two
+#pragma unroll
+        for (int a = 0; a < 3; ++a) s[a] = __fmul2_rn(s[a], inv);
     }
+    float jx = s[0].x, jy = s[1].x, jz = s[2].x;
+    m.gsum[0] = s[0].y;
+    m.gsum[1] = s[1].y;
+    m.gsum[2] = s[2].y;
     if (GEN) {
         m.rho = P.rho2 + P.drho * m.phi;
         m.inv_rho = 1.0f / m.rho;
@@ -217,22 +231,8 @@ __device__ __forceinline__ void macro_flow(const Params& P, const float (&fb)[Q]
 // grad phi = (tau_phi cs^2 S - K1) / ((tau_phi + 1/2) cs^2). The shift t_i phi_ref has no
 // first moment, so the stored deviations give K1 directly.
 template <int Q, int U = STORE_F32>
-__device__ __forceinline__ void macro_interface_df(const Params& P, const float (&gb)[Q], Macro& m) {
-    float kx = 0.f, ky = 0.f, kz = 0.f;
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-        if (Lat<Q>::cx(i) > 0) kx += gb[i];
-        if (Lat<Q>::cx(i) < 0) kx -= gb[i];
-        if (Lat<Q>::cy(i) > 0) ky += gb[i];
-        if (Lat<Q>::cy(i) < 0) ky -= gb[i];
-        if (Lat<Q>::cz(i) > 0) kz += gb[i];
-        if (Lat<Q>::cz(i) < 0) kz -= gb[i];
-    }
-    if constexpr (Store<U>::kInvG != 1.0f) {
-        kx = __fmul_rn(kx, Store<U>::kInvG);
-        ky = __fmul_rn(ky, Store<U>::kInvG);
-        kz = __fmul_rn(kz, Store<U>::kInvG);
-    }
+__device__ __forceinline__ void macro_interface_df(const Params& P, Macro& m) {
+    float kx = m.gsum[0], ky = m.gsum[1], kz = m.gsum[2];  // sum g_i e_i from macro_flow
     kx -= m.phi * m.u[0];
     ky -= m.phi * m.u[1];
     kz -= m.phi * m.u[2];
@@ -344,24 +344,30 @@ __device__ __forceinline__ void collide(const Params& P, const Macro& m, float (
     }
     const float omega_g = P.omega_g;
     // f* = (1 - w_f) fbar + w_f f^eq + (1 - w_f/2) F and g* = (1 - w_g) g + w_g g^eq: the same
-    // collisions, one multiply-add per population once the pair's parts are known.
+    // collisions, one multiply-add per population once the pair's parts are known. f and g of
+    // a population travel together as the lanes of packed FP32 operations.
     const float a_f = 1.f - omega_f, c_f = 1.f - 0.5f * omega_f, a_g = 1.f - omega_g;
+    const float2 a_fg = make_float2(a_f, a_g);
     const float u2h = 1.5f * u2;
     const float feq0 = m.P - 4.5f * pi0;  // P - 4.5 Pi_s term shared by every |e|^2 class
     const float rho3 = 3.f * m.rho, phi3 = 3.f * m.phi, urG3 = 3.f * urG;
+    const float2 rho_phi = make_float2(m.rho, m.phi);
 #pragma unroll
     for (int k = 0; k < Lat<Q>::kPairs; ++k) {
         const int i = Lat<Q>::pair_first(k), j = Lat<Q>::pair_second(k);
         const float t = Lat<Q>::w(i) * Store<U>::kScaleF;
         const float tg = Lat<Q>::w(i) * Store<U>::kScaleG;
+        const float twg = tg * omega_g;
         const float eu = edot<Q>(i, m.u);
         const float en = edot<Q>(i, m.n);
         const float es = edot<Q>(i, m.S);
         const float even = 4.5f * eu * eu - u2h;                   // gam_i = even + 3 eu, gam_j = even - 3 eu
         const float pis = sg * ((float)Lat<Q>::e2(i) - en * en);  // Pi_s term minus its |e|^2 = 0 part
-        // f^eq_i = t (Xe + Xo), f^eq_j = t (Xe - Xo)
-        const float Xe = feq0 + m.rho * even - 4.5f * pis;
-        float Ae, Ao;  // w_f f^eq + (1 - w_f/2) F, even and odd parts
+        // even parts of the equilibria over t and tg: f^eq_i = t (Xe + Xo), f^eq_j = t (Xe - Xo),
+        //   Xe = P - 4.5 Pi_s term + rho even;  g^eq: Phi + phi even
+        const float2 Xe = __ffma2_rn(rho_phi, make_float2(even, even), make_float2(feq0 - 4.5f * pis, m.Phi));
+        // (w_f f^eq + (1 - w_f/2) F, w_g g^eq), split into parts even and odd in e
+        float2 Ae, Ao;
         if (GEN) {
             // F_i = t (Ye + Yo), F_j = t (Ye - Yo), from e_j = -e_i in S_i and R_i:
             //   Ye = 3 eu (e.grad rho + 3 e.rho G) - even u.grad rho - 3 u.rho G
@@ -371,22 +377,19 @@ __device__ __forceinline__ void collide(const Params& P, const Macro& m, float (
             const float odd = 3.f * eu;
             const float Ye = odd * (egr + 3.f * erG) - even * ugr - urG3;
             const float Yo = even * egr - odd * ugr + 3.f * erG;
-            Ae = t * (omega_f * Xe + c_f * Ye);
-            Ao = t * (omega_f * (rho3 * eu) + c_f * Yo);
+            Ae = __fmul2_rn(make_float2(t, twg), make_float2(omega_f * Xe.x + c_f * Ye, Xe.y));
+            Ao = __fmul2_rn(make_float2(t, twg), make_float2(omega_f * (rho3 * eu) + c_f * Yo, phi3 * eu + P.tau_phi * es));
         } else {
             const float tw = t * omega_f;  // uniform over the grid
-            Ae = tw * Xe;
-            Ao = (tw * rho3) * eu;
+            Ae = __fmul2_rn(make_float2(tw, twg), Xe);
+            Ao = __fmul2_rn(make_float2(tw * rho3, twg), make_float2(eu, phi3 * eu + P.tau_phi * es));
         }
-        fb[i] = a_f * fb[i] + (Ae + Ao);
-        fb[j] = a_f * fb[j] + (Ae - Ao);
-        // g^eq_i = tg (Phi + phi gam_i + tau_phi e_i.S): even part tg (Phi + phi even), odd part
-        // tg (3 phi eu + tau_phi e.S)
-        const float twg = tg * omega_g;
-        const float Be = twg * (m.Phi + m.phi * even);
-        const float Bo = twg * (phi3 * eu + P.tau_phi * es);
-        gb[i] = a_g * gb[i] + (Be + Bo);
-        gb[j] = a_g * gb[j] + (Be - Bo);
+        const float2 qi = __ffma2_rn(a_fg, make_float2(fb[i], gb[i]), __fadd2_rn(Ae, Ao));
+        const float2 qj = __ffma2_rn(a_fg, make_float2(fb[j], gb[j]), fsub2_rn(Ae, Ao));
+        fb[i] = qi.x;
+        gb[i] = qi.y;
+        fb[j] = qj.x;
+        gb[j] = qj.y;
     }
     fb[0] = GEN ? m.Pbar + ugr : m.Pbar;  // plane 0 keeps phi_fx: the collision conserves phi
 }
@@ -416,7 +419,7 @@ __device__ __forceinline__ void step_cell(const Params& P, const void* __restric
     Macro m;
     macro_flow<Q, GEN, S>(P, fb, gb, m);
     if (SCHEME == SCHEME_DF) {
-        macro_interface_df<Q, S>(P, gb, m);
+        macro_interface_df<Q, S>(P, m);
     } else {
         float gx, gy, gz;
         fd_gradient<Q>(phi_fd, c, GEN ? mirror_at_walls(nb, ws) : nb, gx, gy, gz);

@@ -113,8 +113,13 @@ int capture_graph(lbm_ctx* c, int start) {
     return LBM_OK;
 }
 
-// The storage of the moving pairs (the FP16 scaling is a compile-time constant of Store<S>).
-void apply_storage(Params& P, int storage) { P.storage = storage; }
+// The storage of the moving pairs (the FP16 scaling is a compile-time constant of Store<S>),
+// and the face-flux weights for g held in that storage's units.
+void apply_storage(Params& P, int storage) {
+    P.storage = storage;
+    P.flux_as = P.flux_a * lbm::storage_inv_g(storage);
+    P.flux_bs = P.flux_b * lbm::storage_inv_g(storage);
+}
 
 int check_ctx(lbm_ctx* c) {
     if (!c) return set_error(nullptr, LBM_EINVAL, "null handle");

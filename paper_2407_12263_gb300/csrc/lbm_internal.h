@@ -18,6 +18,7 @@ struct Params {
                            // population across the face between an upwind cell u and its
                            // downwind neighbour d is 2^-30 (flux_a g*(u) + flux_b g*(d)),
                            // flux_a = 2^30 lw_m, flux_b = -2^30 lw_p
+    float flux_as, flux_bs;  // flux_a, flux_b for g in the storage's units (set with the storage)
     float tau_phi;         // phase-field relaxation time
     float omega_g;         // 1 / (tau_phi + 1/2)           (Eq. c-n_c)
     float grad_s;          // tau_phi / (tau_phi + 1/2)      grad phi = grad_s S - grad_k K1
@@ -110,6 +111,7 @@ struct BatchLaunch {
     int pad_;
     LaunchCase cases[kMaxLaunchCases];
 };
+static_assert(sizeof(BatchLaunch) <= 32764, "a group launch's parameters must fit the kernel parameter space");
 
 // One step of every case of the group: grid (ntx * nty, n_cases, ntz), one tile per block.
 cudaError_t launch_batch_group(int Q, const BatchLaunch& L, cudaStream_t s);

@@ -19,16 +19,21 @@ namespace lbm {
 
 // Thread block: 128 threads, one cell per thread, x fastest. The host picks the shape: one
 // 128-cell row per block where rows are at least that long, else 32 x 4 (a warp spans 32
-// consecutive cells of a row either way). The register budget allows 4 blocks (16 warps) per
-// SM; the difference-free step needs ~122 registers and runs at that occupancy with every
-// (f, g) load of a cell in flight.
-#ifndef LBM_STEP_MINB
-#define LBM_STEP_MINB 4
-#endif
+// consecutive cells of a row either way). With FP32 storage the register budget allows 4
+// blocks (16 warps) per SM: the difference-free step needs ~122 registers and runs at that
+// occupancy with every (f, g) load of a cell in flight. A 16-bit cell moves half the bytes, so
+// the same bandwidth needs more cells in flight: the 16-bit steps are held to 96 registers for
+// 5 blocks (20 warps), which they fit without spilling.
 constexpr int kStepThreads = 128;
+constexpr int LBM_STEP_MINB = 4;
+
+template <int S>
+constexpr int step_min_blocks() {
+    return S == STORE_F32 ? LBM_STEP_MINB : 5;
+}
 
 template <int Q, int SCHEME, bool GEN, int S>
-__global__ void __launch_bounds__(kStepThreads, LBM_STEP_MINB)
+__global__ void __launch_bounds__(kStepThreads, (step_min_blocks<S>()))
 step_kernel(const Params P, const void* __restrict__ fg_in, void* __restrict__ fg_out,
             const float* __restrict__ phi_fd) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;

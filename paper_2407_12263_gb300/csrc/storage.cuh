@@ -31,9 +31,21 @@ struct Store;
 // the results are the same bits as in population units.
 //
 // Raw pair access for the propagation: ld() returns the pair as loaded, cvt() converts it to
-// FP32, sub_f(r, c) / sub_g(r, c) return (FP32 of r's f or g) - c with one rounding. For the
+// FP32, sub_f(r, c) / sub_g(r, c) return (FP32 of r's f or g) - c with one rounding, sub2 both
+// (for FP32 pairs one packed subtraction). For the
 // 16-bit types these are the mixed-precision forms of sub (a 16-bit operand widened exactly to
 // FP32, then subtracted), so a neighbour's pair is never converted on its own.
+// a - b lane by lane in one packed FP32 instruction, each lane rounded as a scalar subtraction
+__device__ __forceinline__ float2 fsub2_rn(float2 a, float2 b) {
+    unsigned long long pa, pb, d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(pa) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(pb) : "f"(b.x), "f"(b.y));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pa), "l"(pb));
+    float2 o;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(o.x), "=f"(o.y) : "l"(d));
+    return o;
+}
+
 __device__ __forceinline__ void unpack16(unsigned int r, unsigned short& lo, unsigned short& hi) {
     asm("mov.b32 {%0, %1}, %2;" : "=h"(lo), "=h"(hi) : "r"(r));
 }
@@ -46,6 +58,7 @@ struct Store<STORE_F32> {
     __device__ __forceinline__ static float2 cvt(Raw r) { return r; }
     __device__ __forceinline__ static float sub_f(Raw r, float c) { return __fsub_rn(r.x, c); }
     __device__ __forceinline__ static float sub_g(Raw r, float c) { return __fsub_rn(r.y, c); }
+    __device__ __forceinline__ static float2 sub2(Raw r, float2 c) { return fsub2_rn(r, c); }
     static constexpr float kScaleF = 1.0f, kScaleG = 1.0f, kInvF = 1.0f, kInvG = 1.0f;
     __device__ __forceinline__ static float2 load(const T* p, const Params&) { return __ldg(p); }
     __device__ __forceinline__ static void store(T* p, float f, float g, const Params&) {
@@ -76,6 +89,7 @@ struct Store<STORE_F16> {
         asm("sub.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(hi), "f"(c));
         return d;
     }
+    __device__ __forceinline__ static float2 sub2(Raw r, float2 c) { return make_float2(sub_f(r, c.x), sub_g(r, c.y)); }
     static constexpr float kScaleF = 4096.0f, kScaleG = 1024.0f, kInvF = 1.0f / 4096.0f, kInvG = 1.0f / 1024.0f;
     __device__ __forceinline__ static float2 load(const T* p, const Params&) {
         const float2 v = __half22float2(__ldg(p));
@@ -112,6 +126,7 @@ struct Store<STORE_BF16> {
         asm("sub.rn.f32.bf16 %0, %1, %2;" : "=f"(d) : "h"(hi), "f"(c));
         return d;
     }
+    __device__ __forceinline__ static float2 sub2(Raw r, float2 c) { return make_float2(sub_f(r, c.x), sub_g(r, c.y)); }
     static constexpr float kScaleF = 1.0f, kScaleG = 1.0f, kInvF = 1.0f, kInvG = 1.0f;
     __device__ __forceinline__ static float2 load(const T* p, const Params&) { return __bfloat1622float2(__ldg(p)); }
     __device__ __forceinline__ static void store(T* p, float f, float g, const Params&) { store_raw(p, f, g); }
@@ -120,6 +135,9 @@ struct Store<STORE_BF16> {
         __stcs(reinterpret_cast<unsigned int*>(p), *reinterpret_cast<const unsigned int*>(&h));
     }
 };
+
+// kInvG of a storage kind, for host code.
+inline float storage_inv_g(int storage) { return storage == STORE_F16 ? Store<STORE_F16>::kInvG : 1.0f; }
 
 // Fixed-point units of phi in plane 0.
 constexpr double kPhiFx = 1073741824.0;  // 2^30

@@ -27,7 +27,7 @@ __global__ void coarsen_kernel(const Params P, const void* __restrict__ fg, int 
                 pull<Q, true, S, GEN>(P, fg, c, nb, fb, gb, phi_fx, ws);
                 Macro m;
                 macro_flow<Q, GEN>(P, fb, gb, m);
-                macro_interface_df<Q>(P, gb, m);
+                macro_interface_df<Q>(P, m);
                 macro_pressure<GEN>(P, m);
                 acc[0] += (double)phi_fx / kPhiFx;
                 acc[1] += m.u[0];
@@ -65,7 +65,7 @@ __global__ void coarsen_lanes_kernel(const Params P, const void* __restrict__ fg
                 pull<Q, true, S, GEN>(P, fg, c, nb, fb, gb, phi_fx, ws);
                 Macro m;
                 macro_flow<Q, GEN>(P, fb, gb, m);
-                macro_interface_df<Q>(P, gb, m);
+                macro_interface_df<Q>(P, m);
                 macro_pressure<GEN>(P, m);
                 acc[0] += (double)phi_fx / kPhiFx;
                 acc[1] += m.u[0];

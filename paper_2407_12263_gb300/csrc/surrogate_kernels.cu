@@ -335,6 +335,8 @@ constexpr int HPLANE = HX * HY;               // 180 haloed voxels per z plane
 constexpr uint32_t PLP = HPLANE * 16;         // bytes of one chunk plane (8 channels) of a z plane
 constexpr uint32_t SLOT_BYTES = 4 * PLP;      // 32 channels: 11,520
 constexpr int CONV_THREADS = 256;
+constexpr int CONV_STAGERS = CONV_THREADS - 32;  // warps 0..6 stage; warp 7 issues the MMAs
+constexpr int kIssuer = CONV_THREADS - 32;
 constexpr uint32_t W_TAP = 2048;             // bytes of one tap's 32 x 32 FP16 weights
 constexpr uint32_t W_BYTES = 27 * W_TAP;
 constexpr uint32_t SMEM = 4 * SLOT_BYTES + W_BYTES;  // 101,376: two CTAs per SM
@@ -350,6 +352,20 @@ __device__ inline uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) 
 
 // kind::f16 instruction descriptor: FP32 D, FP16 A and B, both K-major, M = 128, N = 32
 constexpr uint32_t kIdesc = (1u << 4) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+// One MMA from descriptors given as 32-bit halves. A descriptor's start address sits in the
+// low 14 bits as address / 16 and every shared-memory address stays below 2^18 bytes, so an
+// operand at byte offset d from a described base is the same descriptor with d / 16 added to
+// its low half.
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint32_t a_lo, uint32_t a_hi, uint32_t b_lo, uint32_t b_hi,
+                                        uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t.reg .b64 ad, bd;\n\t"
+        "mov.b64 ad, {%1, %2};\n\tmov.b64 bd, {%3, %4};\n\t"
+        "setp.ne.b32 p, %6, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], ad, bd, %5, p;\n\t}\n" ::"r"(d_tmem),
+        "r"(a_lo), "r"(a_hi), "r"(b_lo), "r"(b_hi), "r"(kIdesc), "r"(accumulate));
+}
 
 // The FP16 weight image of a layer with cout, cin <= 32: zero where n >= cout or k >= cin.
 __global__ void weight_image_kernel(const float* __restrict__ W, int cout, int cin, __half* __restrict__ img) {
@@ -373,24 +389,33 @@ __device__ inline bool wait_parity(uint32_t mbar, uint32_t parity) {
 }
 
 // One haloed z plane zz of the input into a ring slot, converted to FP16 and scaled (channels
-// >= cin are zero): a thread takes one haloed voxel, all 32 channels in flight, and writes 8
-// channels (16 bytes) at a time.
+// >= cin are zero): a task is one haloed voxel and 8 channels (8 loads, one 16-byte store);
+// consecutive threads take consecutive voxels of a channel group, and a thread loads all its
+// tasks before it stores any, so that their loads are in flight together.
 template <typename TIN>
-__device__ __forceinline__ void conv_stage_plane(unsigned char* slot, const TIN* __restrict__ inb, int cin, float in_scale,
-                                                 long long vox, int zz, int y0, int x0, int H, int Wd) {
-    for (int v = threadIdx.x; v < HPLANE; v += CONV_THREADS) {
+__device__ __forceinline__ void conv_stage_plane(unsigned char* __restrict__ slot, const TIN* __restrict__ inb, int cin,
+                                                 float in_scale, long long vox, int zz, int y0, int x0, int H, int Wd) {
+    constexpr int kTasks = 4 * HPLANE, kPer = (kTasks + CONV_STAGERS - 1) / CONV_STAGERS;
+    float f[kPer][8];
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        const int task = threadIdx.x + i * CONV_STAGERS;
+        const int c8 = task / HPLANE, v = task - c8 * HPLANE;
         const int hx = v % HX, hy = v / HX;
-        const long long goff = ((long long)zz * H + wrap(y0 + hy - 1, H)) * Wd + wrap(x0 + hx - 1, Wd);
-        float f[32];
+        const bool in_range = task < kTasks;
+        const TIN* src = inb + (long long)(8 * c8) * vox + ((long long)zz * H + wrap(y0 + hy - 1, H)) * Wd + wrap(x0 + hx - 1, Wd);
 #pragma unroll
-        for (int c = 0; c < 32; ++c) f[c] = c < cin ? to_f(inb[(long long)c * vox + goff]) : 0.f;
+        for (int j = 0; j < 8; ++j) f[i][j] = (in_range && 8 * c8 + j < cin) ? to_f(src[(long long)j * vox]) : 0.f;
+    }
 #pragma unroll
-        for (int c8 = 0; c8 < 4; ++c8) {
-            __half2 q[4];
+    for (int i = 0; i < kPer; ++i) {
+        const int task = threadIdx.x + i * CONV_STAGERS;
+        if (task >= kTasks) break;
+        const int c8 = task / HPLANE, v = task - c8 * HPLANE;
+        __half2 q[4];
 #pragma unroll
-            for (int j2 = 0; j2 < 4; ++j2) q[j2] = __floats2half2_rn(f[8 * c8 + 2 * j2] * in_scale, f[8 * c8 + 2 * j2 + 1] * in_scale);
-            *reinterpret_cast<uint4*>(slot + c8 * PLP + v * 16) = *reinterpret_cast<const uint4*>(q);
-        }
+        for (int j2 = 0; j2 < 4; ++j2) q[j2] = __floats2half2_rn(f[i][2 * j2] * in_scale, f[i][2 * j2 + 1] * in_scale);
+        *reinterpret_cast<uint4*>(slot + c8 * PLP + v * 16) = *reinterpret_cast<const uint4*>(q);
     }
 }
 
@@ -405,6 +430,7 @@ conv32_tc_kernel(const TIN* __restrict__ in, int cin, float in_scale, const __ha
     __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int s_fail;
+    __shared__ float s_bias[32];
     const int t = threadIdx.x;
     const uint32_t mbar0 = (uint32_t)__cvta_generic_to_shared(&mbar[0]);  // barrier k at mbar0 + 8 k
     if (t == 0) {
@@ -412,6 +438,7 @@ conv32_tc_kernel(const TIN* __restrict__ in, int cin, float in_scale, const __ha
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar0 + 8));
         s_fail = 0;
     }
+    if (t < 32) s_bias[t] = (bias && t < cout) ? bias[t] : 0.f;
     if (t < 32) {  // two 32-column accumulators
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(
             (uint32_t)__cvta_generic_to_shared(&tmem_slot)));
@@ -425,6 +452,9 @@ conv32_tc_kernel(const TIN* __restrict__ in, int cin, float in_scale, const __ha
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_slot;
     const uint32_t a_addr = (uint32_t)__cvta_generic_to_shared(sA), w_addr = (uint32_t)__cvta_generic_to_shared(sW);
+    const uint64_t a_desc = smem_desc(a_addr, PLP, HX * 16), b_desc = smem_desc(w_addr, 512, 128);
+    const uint32_t a_lo0 = (uint32_t)a_desc, a_hi = (uint32_t)(a_desc >> 32);
+    const uint32_t b_lo0 = (uint32_t)b_desc, b_hi = (uint32_t)(b_desc >> 32);
     const long long vox = (long long)D * H * Wd;
     const float out_scale = 1.0f / in_scale;  // in_scale is a power of two: exact
     uint32_t phase = 0u, pending = 0u;        // per barrier k (bit k): the parity it waits for; a commit not waited for
@@ -458,7 +488,7 @@ conv32_tc_kernel(const TIN* __restrict__ in, int cin, float in_scale, const __ha
 #pragma unroll
             for (int o = 0; o < 32; ++o) {
                 if (o < cout) {
-                    float a = __uint_as_float(v[o]) * out_scale + (bias ? __ldg(bias + o) : 0.f);
+                    float a = __uint_as_float(v[o]) * out_scale + s_bias[o];
                     if (MODE == 1) a = fmaxf(a, 0.f);
                     ob[(long long)o * vox + vv] = from_f<TOUT>(a);
                 }
@@ -486,21 +516,17 @@ conv32_tc_kernel(const TIN* __restrict__ in, int cin, float in_scale, const __ha
             __syncthreads();
             asm volatile("tcgen05.fence::after_thread_sync;");
             if (s_fail) break;
-            if (t == 0) {
+            if (t == kIssuer) {
+                uint32_t alo[3];  // plane z + dz - 1 in its ring slot
+#pragma unroll
+                for (int dz = 0; dz < 3; ++dz) alo[dz] = a_lo0 + ((uint32_t)((zi + dz) & 3) * SLOT_BYTES >> 4);
+#pragma unroll
                 for (int tap = 0; tap < 27; ++tap) {
                     const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-                    // haloed voxel of output (0, 0) shifted by (dx - 1, dy - 1), in plane z + dz - 1
-                    const uint32_t a0 = a_addr + (uint32_t)((zi + dz) & 3) * SLOT_BYTES + (uint32_t)(dy * HX + dx) * 16;
 #pragma unroll
-                    for (int kk = 0; kk < 2; ++kk) {
-                        const uint64_t ad = smem_desc(a0 + (uint32_t)(2 * kk) * PLP, PLP, HX * 16);
-                        const uint64_t bd = smem_desc(w_addr + (uint32_t)tap * W_TAP + (uint32_t)(2 * kk) * 512, 512, 128);
-                        const uint32_t acc = (tap | kk) ? 1u : 0u;
-                        asm volatile(
-                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem + (uint32_t)(k * 32)),
-                            "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
-                    }
+                    for (int kk = 0; kk < 2; ++kk)  // haloed voxel of output (0, 0) shifted by (dx - 1, dy - 1)
+                        mma_f16(tmem + (uint32_t)(k * 32), alo[dz] + (((uint32_t)(dy * HX + dx) * 16 + (uint32_t)(2 * kk) * PLP) >> 4),
+                                a_hi, b_lo0 + (((uint32_t)tap * W_TAP + (uint32_t)(2 * kk) * 512) >> 4), b_hi, (tap | kk) ? 1u : 0u);
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar0 + 8u * (uint32_t)k));
             }
@@ -562,6 +588,7 @@ conv32_tc_kernel(const TIN* __restrict__ in, int cin, float in_scale, const __ha
 // ---------------------------------------------------------------------------------------
 constexpr int WG_TX = 8, WG_TY = 16, WG_HY = WG_TY + 2;        // 18 haloed rows per plane
 constexpr int WG_THREADS = 256;
+constexpr int WG_STAGERS = WG_THREADS - 32;  // warps 0..6 stage; warp 7 issues the MMAs
 constexpr int WG_ZCHUNK = 16;                                   // z planes per column
 constexpr uint32_t WG_ROW_BYTES = 4 * 512;                      // 4 dx slots x 32 channels x 8 voxels
 constexpr uint32_t WG_PLANE_BYTES = WG_HY * WG_ROW_BYTES;        // 36,864
@@ -596,59 +623,78 @@ __device__ __forceinline__ void load8(const float* p, bool vec, int x0, int Wd, 
     }
 }
 
-// Plane zz of h into a ring slot: a thread takes one (row, channel), loads its ten x-values
-// (x0 - 1 .. x0 + 8, periodic) and writes the three shifted 8-voxel windows, 16 bytes each.
+// Plane zz of h into a ring slot: a task is one (row, channel); its ten x-values (x0 - 1 ..
+// x0 + 8, periodic) give the three shifted 8-voxel windows, 16 bytes each. A thread loads all
+// its tasks before it stores any, so their loads are in flight together.
 template <typename TH>
-__device__ __forceinline__ void wg_stage_plane(unsigned char* slot, const TH* __restrict__ hb, int cin, long long vox,
-                                               int zz, int y0, int x0, int H, int Wd, bool vec) {
-    for (int task = threadIdx.x; task < WG_HY * 32; task += WG_THREADS) {
+__device__ __forceinline__ void wg_stage_plane(unsigned char* __restrict__ slot, const TH* __restrict__ hb, int cin,
+                                               long long vox, int zz, int y0, int x0, int H, int Wd, bool vec) {
+    constexpr int kTasks = WG_HY * 32, kPer = (kTasks + WG_STAGERS - 1) / WG_STAGERS;
+    float v[kPer][WG_TX + 2];
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        const int task = threadIdx.x + i * WG_STAGERS;
         const int r = task / 32, c = task % 32;
-        float v[WG_TX + 2];
-        if (c < cin) {
+        if (task < kTasks && c < cin) {
             const TH* row = hb + (long long)c * vox + ((long long)zz * H + wrap(y0 + r - 1, H)) * Wd;
             float m[8];
             load8(row, vec, x0, Wd, m);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) v[j + 1] = m[j];
-            v[0] = to_f(row[wrap(x0 - 1, Wd)]);
-            v[WG_TX + 1] = to_f(row[wrap(x0 + WG_TX, Wd)]);
+            for (int j = 0; j < 8; ++j) v[i][j + 1] = m[j];
+            v[i][0] = to_f(row[wrap(x0 - 1, Wd)]);
+            v[i][WG_TX + 1] = to_f(row[wrap(x0 + WG_TX, Wd)]);
         } else {
 #pragma unroll
-            for (int q = 0; q < WG_TX + 2; ++q) v[q] = 0.f;
+            for (int q = 0; q < WG_TX + 2; ++q) v[i][q] = 0.f;
         }
+    }
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        const int task = threadIdx.x + i * WG_STAGERS;
+        if (task >= kTasks) break;
+        const int r = task / 32, c = task % 32;
 #pragma unroll
         for (int dx = 0; dx < 3; ++dx) {
             __half2 w2[4];
 #pragma unroll
-            for (int j2 = 0; j2 < 4; ++j2) w2[j2] = __floats2half2_rn(v[dx + 2 * j2], v[dx + 2 * j2 + 1]);
+            for (int j2 = 0; j2 < 4; ++j2) w2[j2] = __floats2half2_rn(v[i][dx + 2 * j2], v[i][dx + 2 * j2 + 1]);
             *reinterpret_cast<uint4*>(slot + r * WG_ROW_BYTES + dx * 512 + c * 16) = *reinterpret_cast<const uint4*>(w2);
         }
     }
 }
 
-// g of the step's own voxels (zero outside the grid and for o >= cout), scaled; one (row,
-// output channel) per thread, 8 voxels in one 16-byte store.
-__device__ __forceinline__ void wg_stage_g(unsigned char* buf, const float* __restrict__ gb, int cout, long long vox,
-                                           float g_scale, int z, int y0, int x0, int H, int Wd, bool vec) {
-    for (int task = threadIdx.x; task < WG_TY * 32; task += WG_THREADS) {
+// g of the step's own voxels (zero outside the grid and for o >= cout), scaled; a task is one
+// (row, output channel), 8 voxels in one 16-byte store; loads first, as above.
+__device__ __forceinline__ void wg_stage_g(unsigned char* __restrict__ buf, const float* __restrict__ gb, int cout,
+                                           long long vox, float g_scale, int z, int y0, int x0, int H, int Wd, bool vec) {
+    constexpr int kTasks = WG_TY * 32, kPer = (kTasks + WG_STAGERS - 1) / WG_STAGERS;
+    float v[kPer][8];
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        const int task = threadIdx.x + i * WG_STAGERS;
         const int ly = task / 32, o = task % 32;
         const int y = y0 + ly;
-        float v[8];
-        if (o < cout && y < H) {
+        if (task < kTasks && o < cout && y < H) {
             const float* row = gb + (long long)o * vox + ((long long)z * H + y) * Wd;
             if (vec) {
-                load8(row, true, x0, Wd, v);
+                load8(row, true, x0, Wd, v[i]);
             } else {
 #pragma unroll
-                for (int lx = 0; lx < WG_TX; ++lx) v[lx] = (x0 + lx < Wd) ? row[x0 + lx] : 0.f;
+                for (int lx = 0; lx < WG_TX; ++lx) v[i][lx] = (x0 + lx < Wd) ? row[x0 + lx] : 0.f;
             }
         } else {
 #pragma unroll
-            for (int lx = 0; lx < WG_TX; ++lx) v[lx] = 0.f;
+            for (int lx = 0; lx < WG_TX; ++lx) v[i][lx] = 0.f;
         }
+    }
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        const int task = threadIdx.x + i * WG_STAGERS;
+        if (task >= kTasks) break;
+        const int ly = task / 32, o = task % 32;
         __half2 w2[4];
 #pragma unroll
-        for (int j2 = 0; j2 < 4; ++j2) w2[j2] = __floats2half2_rn(v[2 * j2] * g_scale, v[2 * j2 + 1] * g_scale);
+        for (int j2 = 0; j2 < 4; ++j2) w2[j2] = __floats2half2_rn(v[i][2 * j2] * g_scale, v[i][2 * j2 + 1] * g_scale);
         *reinterpret_cast<uint4*>(buf + ly * 512 + o * 16) = *reinterpret_cast<const uint4*>(w2);
     }
 }
@@ -683,8 +729,10 @@ wgrad32_tc_kernel(const float* __restrict__ g, int cout, float g_scale, const TH
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_slot;
     const uint32_t h_addr = (uint32_t)__cvta_generic_to_shared(sH), g_addr = (uint32_t)__cvta_generic_to_shared(sG);
+    const uint64_t h_desc = smem_desc(h_addr, WG_ROW_BYTES, 128), g_desc = smem_desc(g_addr, 512, 128);
+    const uint32_t h_lo0 = (uint32_t)h_desc, h_hi = (uint32_t)(h_desc >> 32);
+    const uint32_t g_lo0 = (uint32_t)g_desc, g_hi = (uint32_t)(g_desc >> 32);
     const long long vox = (long long)D * H * Wd;
-    constexpr uint32_t kIdescW = (1u << 4) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
     uint32_t phase = 0u, pending = 0u;  // bit k: the parity barrier k waits for; a commit on it not yet waited for
     bool first = true;
     // waits for the MMAs committed on barrier k, if any; false on a timeout (they stay pending)
@@ -720,20 +768,18 @@ wgrad32_tc_kernel(const float* __restrict__ g, int cout, float g_scale, const TH
             asm volatile("tcgen05.fence::after_thread_sync;");
             if (s_fail) break;
             const int k = zi & 1;  // barrier and g buffer of this step
-            if (t == 0) {
+            if (t == WG_STAGERS) {
+                uint32_t alo[3];  // plane z + dz - 1 in its ring slot
+#pragma unroll
+                for (int dz = 0; dz < 3; ++dz) alo[dz] = h_lo0 + ((uint32_t)((zi + dz) & 3) * WG_PLANE_BYTES >> 4);
+                const uint32_t glo = g_lo0 + ((uint32_t)k * WG_G_BYTES >> 4);
+#pragma unroll
                 for (int pr = 0; pr < 9; ++pr) {
                     const int dz = pr / 3, dy = pr % 3;
-                    const uint32_t plane = h_addr + (uint32_t)((zi + dz) & 3) * WG_PLANE_BYTES + (uint32_t)dy * WG_ROW_BYTES;
 #pragma unroll
-                    for (int kk = 0; kk < WG_TY / 2; ++kk) {  // two 8-voxel rows per MMA (K = 16)
-                        const uint64_t ad = smem_desc(plane + (uint32_t)(2 * kk) * WG_ROW_BYTES, WG_ROW_BYTES, 128);
-                        const uint64_t bd = smem_desc(g_addr + (uint32_t)k * WG_G_BYTES + (uint32_t)(2 * kk) * 512, 512, 128);
-                        const uint32_t acc = (first && kk == 0) ? 0u : 1u;
-                        asm volatile(
-                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem + (uint32_t)(pr * 32)),
-                            "l"(ad), "l"(bd), "r"(kIdescW), "r"(acc));
-                    }
+                    for (int kk = 0; kk < WG_TY / 2; ++kk)  // two 8-voxel rows per MMA (K = 16)
+                        mma_f16(tmem + (uint32_t)(pr * 32), alo[dz] + ((uint32_t)(dy + 2 * kk) * WG_ROW_BYTES >> 4), h_hi,
+                                glo + ((uint32_t)(2 * kk) * 512 >> 4), g_hi, (first && kk == 0) ? 0u : 1u);
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar0 + 8u * (uint32_t)k));
             }
