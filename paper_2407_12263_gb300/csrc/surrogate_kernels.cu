@@ -430,7 +430,7 @@ conv32_tc_kernel(const TIN* __restrict__ in, int cin, float in_scale, const __ha
     __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int s_fail;
-    __shared__ float s_bias[32];
+    __shared__ __align__(16) float s_bias[32];
     const int t = threadIdx.x;
     const uint32_t mbar0 = (uint32_t)__cvta_generic_to_shared(&mbar[0]);  // barrier k at mbar0 + 8 k
     if (t == 0) {
@@ -483,14 +483,22 @@ conv32_tc_kernel(const TIN* __restrict__ in, int cin, float in_scale, const __ha
         const int lx = t % TX, ly = t / TX;
         const int x = x0 + lx, y = y0 + ly;
         if (x < Wd && y < H) {
-            const long long vv = ((long long)z * H + y) * Wd + x;
-            TOUT* ob = out + (long long)b * cout * vox;
+            // channel o of this voxel at p + o vox; the biases come four at a time
+            TOUT* p = out + (long long)b * cout * vox + ((long long)z * H + y) * Wd + x;
+            const float4* b4 = reinterpret_cast<const float4*>(s_bias);
 #pragma unroll
-            for (int o = 0; o < 32; ++o) {
-                if (o < cout) {
-                    float a = __uint_as_float(v[o]) * out_scale + s_bias[o];
-                    if (MODE == 1) a = fmaxf(a, 0.f);
-                    ob[(long long)o * vox + vv] = from_f<TOUT>(a);
+            for (int o4 = 0; o4 < 8; ++o4) {
+                const float4 bq = b4[o4];
+                const float bias4[4] = {bq.x, bq.y, bq.z, bq.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int o = 4 * o4 + q;
+                    if (o < cout) {
+                        float a = fmaf(__uint_as_float(v[o]), out_scale, bias4[q]);
+                        if (MODE == 1) a = fmaxf(a, 0.f);
+                        *p = from_f<TOUT>(a);
+                        p += vox;
+                    }
                 }
             }
         }
