@@ -589,9 +589,9 @@ conv32_tc_kernel(const TIN* __restrict__ in, int cin, float in_scale, const __ha
 // row. g is staged the same way as the N x K operand (16 o + 2 lx within a 512-byte row).
 //
 // A CTA walks a column of steps along z (a chunk of z planes of one (x, y) tile), keeping the
-// haloed planes in a ring of four: step z reads planes z - 1, z, z + 1 while the 256 threads
-// stage plane z + 2 and g of step z + 1 (the plane and g buffers that step z - 1 read, waited
-// for on its mbarrier). Nine 128 x 32 FP32 accumulators live in tensor memory (288 of 512
+// haloed planes in a ring of four: step z reads planes z - 1, z, z + 1 while seven warps write
+// plane z + 2 and g of step z + 1 into the plane and g buffers that step z - 1 read (waited for
+// on its mbarrier), from registers loaded during step z - 1, and issue the loads for step z + 1. Nine 128 x 32 FP32 accumulators live in tensor memory (288 of 512
 // columns; one CTA per SM) for all the columns a CTA takes, and are added to gW at the end.
 // ---------------------------------------------------------------------------------------
 constexpr int WG_TX = 8, WG_TY = 16, WG_HY = WG_TY + 2;        // 18 haloed rows per plane
@@ -631,78 +631,153 @@ __device__ __forceinline__ void load8(const float* p, bool vec, int x0, int Wd, 
     }
 }
 
-// Plane zz of h into a ring slot: a task is one (row, channel); its ten x-values (x0 - 1 ..
-// x0 + 8, periodic) give the three shifted 8-voxel windows, 16 bytes each. A thread loads all
-// its tasks before it stores any, so their loads are in flight together.
+// A haloed row of h as loaded: the 8 values x0 .. x0 + 7 and the halo values x0 - 1 and
+// x0 + 8 (periodic), kept in the storage type until they are written to shared memory.
 template <typename TH>
-__device__ __forceinline__ void wg_stage_plane(unsigned char* __restrict__ slot, const TH* __restrict__ hb, int cin,
-                                               long long vox, int zz, int y0, int x0, int H, int Wd, bool vec) {
-    constexpr int kTasks = WG_HY * 32, kPer = (kTasks + WG_STAGERS - 1) / WG_STAGERS;
-    float v[kPer][WG_TX + 2];
-#pragma unroll
-    for (int i = 0; i < kPer; ++i) {
-        const int task = threadIdx.x + i * WG_STAGERS;
-        const int r = task / 32, c = task % 32;
-        if (task < kTasks && c < cin) {
-            const TH* row = hb + (long long)c * vox + ((long long)zz * H + wrap(y0 + r - 1, H)) * Wd;
-            float m[8];
-            load8(row, vec, x0, Wd, m);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) v[i][j + 1] = m[j];
-            v[i][0] = to_f(row[wrap(x0 - 1, Wd)]);
-            v[i][WG_TX + 1] = to_f(row[wrap(x0 + WG_TX, Wd)]);
+struct HRow;
+template <>
+struct HRow<__half> {
+    uint4 m;
+    __half l, r;
+    __device__ __forceinline__ void load(const __half* __restrict__ row, bool vec, int x0, int Wd) {
+        if (vec) {
+            m = __ldg(reinterpret_cast<const uint4*>(row + x0));
         } else {
+            __half2 q[4];
 #pragma unroll
-            for (int q = 0; q < WG_TX + 2; ++q) v[i][q] = 0.f;
+            for (int j = 0; j < 4; ++j) q[j] = __halves2half2(row[wrap(x0 + 2 * j, Wd)], row[wrap(x0 + 2 * j + 1, Wd)]);
+            m = *reinterpret_cast<const uint4*>(q);
         }
+        l = row[wrap(x0 - 1, Wd)];
+        r = row[wrap(x0 + WG_TX, Wd)];
     }
+    __device__ __forceinline__ void zero() {
+        m = make_uint4(0, 0, 0, 0);
+        l = r = __float2half_rn(0.f);
+    }
+    __device__ __forceinline__ void get(float (&v)[WG_TX + 2]) const {
+        const __half2* h2 = reinterpret_cast<const __half2*>(&m);
 #pragma unroll
-    for (int i = 0; i < kPer; ++i) {
+        for (int j = 0; j < 4; ++j) {
+            const float2 f = __half22float2(h2[j]);
+            v[1 + 2 * j] = f.x;
+            v[2 + 2 * j] = f.y;
+        }
+        v[0] = __half2float(l);
+        v[WG_TX + 1] = __half2float(r);
+    }
+};
+template <>
+struct HRow<float> {
+    float4 a, b;
+    float l, r;
+    __device__ __forceinline__ void load(const float* __restrict__ row, bool vec, int x0, int Wd) {
+        if (vec) {
+            a = __ldg(reinterpret_cast<const float4*>(row + x0));
+            b = __ldg(reinterpret_cast<const float4*>(row + x0 + 4));
+        } else {
+            a = make_float4(row[wrap(x0, Wd)], row[wrap(x0 + 1, Wd)], row[wrap(x0 + 2, Wd)], row[wrap(x0 + 3, Wd)]);
+            b = make_float4(row[wrap(x0 + 4, Wd)], row[wrap(x0 + 5, Wd)], row[wrap(x0 + 6, Wd)], row[wrap(x0 + 7, Wd)]);
+        }
+        l = row[wrap(x0 - 1, Wd)];
+        r = row[wrap(x0 + WG_TX, Wd)];
+    }
+    __device__ __forceinline__ void zero() {
+        a = b = make_float4(0.f, 0.f, 0.f, 0.f);
+        l = r = 0.f;
+    }
+    __device__ __forceinline__ void get(float (&v)[WG_TX + 2]) const {
+        v[0] = l;
+        v[1] = a.x; v[2] = a.y; v[3] = a.z; v[4] = a.w;
+        v[5] = b.x; v[6] = b.y; v[7] = b.z; v[8] = b.w;
+        v[WG_TX + 1] = r;
+    }
+};
+
+// A thread's share of one haloed plane of h (tasks are (row, channel)) and of one step of g
+// (tasks are (row, output channel), 8 voxels each), as loaded. Loading and writing to shared
+// memory are separate so that the loads of the plane a step will need can be issued a whole
+// step ahead.
+constexpr int WG_H_TASKS = WG_HY * 32, WG_H_PER = (WG_H_TASKS + WG_STAGERS - 1) / WG_STAGERS;
+constexpr int WG_G_TASKS = WG_TY * 32, WG_G_PER = (WG_G_TASKS + WG_STAGERS - 1) / WG_STAGERS;
+
+template <typename TH>
+struct WgStage {
+    HRow<TH> h[WG_H_PER];
+    float4 ga[WG_G_PER], gb[WG_G_PER];
+};
+
+template <typename TH>
+__device__ __forceinline__ void wg_load_plane(WgStage<TH>& st, const TH* __restrict__ hb, int cin, long long vox, int zz,
+                                              int y0, int x0, int H, int Wd, bool vec) {
+#pragma unroll
+    for (int i = 0; i < WG_H_PER; ++i) {
         const int task = threadIdx.x + i * WG_STAGERS;
-        if (task >= kTasks) break;
         const int r = task / 32, c = task % 32;
+        if (task < WG_H_TASKS && c < cin)
+            st.h[i].load(hb + (long long)c * vox + ((long long)zz * H + wrap(y0 + r - 1, H)) * Wd, vec, x0, Wd);
+        else
+            st.h[i].zero();
+    }
+}
+
+// The three x-shifted 8-voxel windows of every loaded row, 16 bytes each.
+template <typename TH>
+__device__ __forceinline__ void wg_store_plane(unsigned char* __restrict__ slot, const WgStage<TH>& st) {
+#pragma unroll
+    for (int i = 0; i < WG_H_PER; ++i) {
+        const int task = threadIdx.x + i * WG_STAGERS;
+        if (task >= WG_H_TASKS) break;
+        const int r = task / 32, c = task % 32;
+        float v[WG_TX + 2];
+        st.h[i].get(v);
 #pragma unroll
         for (int dx = 0; dx < 3; ++dx) {
             __half2 w2[4];
 #pragma unroll
-            for (int j2 = 0; j2 < 4; ++j2) w2[j2] = __floats2half2_rn(v[i][dx + 2 * j2], v[i][dx + 2 * j2 + 1]);
+            for (int j2 = 0; j2 < 4; ++j2) w2[j2] = __floats2half2_rn(v[dx + 2 * j2], v[dx + 2 * j2 + 1]);
             *reinterpret_cast<uint4*>(slot + r * WG_ROW_BYTES + dx * 512 + c * 16) = *reinterpret_cast<const uint4*>(w2);
         }
     }
 }
 
-// g of the step's own voxels (zero outside the grid and for o >= cout), scaled; a task is one
-// (row, output channel), 8 voxels in one 16-byte store; loads first, as above.
-__device__ __forceinline__ void wg_stage_g(unsigned char* __restrict__ buf, const float* __restrict__ gb, int cout,
-                                           long long vox, float g_scale, int z, int y0, int x0, int H, int Wd, bool vec) {
-    constexpr int kTasks = WG_TY * 32, kPer = (kTasks + WG_STAGERS - 1) / WG_STAGERS;
-    float v[kPer][8];
+// g of one step's own voxels: zero outside the grid and for o >= cout.
+template <typename TH>
+__device__ __forceinline__ void wg_load_g(WgStage<TH>& st, const float* __restrict__ gb, int cout, long long vox, int z,
+                                          int y0, int x0, int H, int Wd, bool vec) {
 #pragma unroll
-    for (int i = 0; i < kPer; ++i) {
+    for (int i = 0; i < WG_G_PER; ++i) {
         const int task = threadIdx.x + i * WG_STAGERS;
         const int ly = task / 32, o = task % 32;
         const int y = y0 + ly;
-        if (task < kTasks && o < cout && y < H) {
-            const float* row = gb + (long long)o * vox + ((long long)z * H + y) * Wd;
+        st.ga[i] = st.gb[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (task < WG_G_TASKS && o < cout && y < H) {
+            const float* row = gb + (long long)o * vox + ((long long)z * H + y) * Wd + x0;
             if (vec) {
-                load8(row, true, x0, Wd, v[i]);
+                st.ga[i] = __ldg(reinterpret_cast<const float4*>(row));
+                st.gb[i] = __ldg(reinterpret_cast<const float4*>(row + 4));
             } else {
+                float v[8];
 #pragma unroll
-                for (int lx = 0; lx < WG_TX; ++lx) v[i][lx] = (x0 + lx < Wd) ? row[x0 + lx] : 0.f;
+                for (int lx = 0; lx < WG_TX; ++lx) v[lx] = (x0 + lx < Wd) ? row[lx] : 0.f;
+                st.ga[i] = make_float4(v[0], v[1], v[2], v[3]);
+                st.gb[i] = make_float4(v[4], v[5], v[6], v[7]);
             }
-        } else {
-#pragma unroll
-            for (int lx = 0; lx < WG_TX; ++lx) v[i][lx] = 0.f;
         }
     }
+}
+
+// g scaled and rounded to FP16, one (row, output channel) per 16-byte store.
+template <typename TH>
+__device__ __forceinline__ void wg_store_g(unsigned char* __restrict__ buf, const WgStage<TH>& st, float g_scale) {
 #pragma unroll
-    for (int i = 0; i < kPer; ++i) {
+    for (int i = 0; i < WG_G_PER; ++i) {
         const int task = threadIdx.x + i * WG_STAGERS;
-        if (task >= kTasks) break;
+        if (task >= WG_G_TASKS) break;
         const int ly = task / 32, o = task % 32;
-        __half2 w2[4];
-#pragma unroll
-        for (int j2 = 0; j2 < 4; ++j2) w2[j2] = __floats2half2_rn(v[i][2 * j2] * g_scale, v[i][2 * j2 + 1] * g_scale);
+        const float4 a = st.ga[i], b = st.gb[i];
+        const __half2 w2[4] = {__floats2half2_rn(a.x * g_scale, a.y * g_scale), __floats2half2_rn(a.z * g_scale, a.w * g_scale),
+                               __floats2half2_rn(b.x * g_scale, b.y * g_scale), __floats2half2_rn(b.z * g_scale, b.w * g_scale)};
         *reinterpret_cast<uint4*>(buf + ly * 512 + o * 16) = *reinterpret_cast<const uint4*>(w2);
     }
 }
@@ -765,9 +840,18 @@ wgrad32_tc_kernel(const float* __restrict__ g, int cout, float g_scale, const TH
         const TH* hb = h + (long long)b * cin * vox;
         const float* gbat = g + (long long)b * cout * vox;
         // prologue: planes z_begin - 1 .. z_begin + 1 (ring slots 0..2) and g of the first step
-        for (int j = 0; j < 3; ++j)
-            wg_stage_plane(sH + j * WG_PLANE_BYTES, hb, cin, vox, wrap(z_begin - 1 + j, D), y0, x0, H, Wd, vh);
-        wg_stage_g(sG, gbat, cout, vox, g_scale, z_begin, y0, x0, H, Wd, vg);
+        // in shared memory, and the loads of what the first step stages already in flight
+        WgStage<TH> st;
+        for (int j = 0; j < 3; ++j) {
+            wg_load_plane(st, hb, cin, vox, wrap(z_begin - 1 + j, D), y0, x0, H, Wd, vh);
+            wg_store_plane(sH + j * WG_PLANE_BYTES, st);
+        }
+        wg_load_g(st, gbat, cout, vox, z_begin, y0, x0, H, Wd, vg);
+        wg_store_g(sG, st, g_scale);
+        if (z_begin + 1 < z_end) {
+            wg_load_plane(st, hb, cin, vox, wrap(z_begin + 2, D), y0, x0, H, Wd, vh);
+            wg_load_g(st, gbat, cout, vox, z_begin + 1, y0, x0, H, Wd, vg);
+        }
         for (int z = z_begin; z < z_end; ++z) {
             const int zi = z - z_begin;
             asm volatile("fence.proxy.async.shared::cta;");
@@ -799,8 +883,13 @@ wgrad32_tc_kernel(const float* __restrict__ g, int cout, float g_scale, const TH
                     s_fail = 1;
                     atomicExch(err, 1);
                 }
-                wg_stage_plane(sH + (uint32_t)((zi + 3) & 3) * WG_PLANE_BYTES, hb, cin, vox, wrap(z + 2, D), y0, x0, H, Wd, vh);
-                wg_stage_g(sG + (uint32_t)(k ^ 1) * WG_G_BYTES, gbat, cout, vox, g_scale, z + 1, y0, x0, H, Wd, vg);
+                // plane z + 2 and g of step z + 1, loaded during the previous step
+                wg_store_plane(sH + (uint32_t)((zi + 3) & 3) * WG_PLANE_BYTES, st);
+                wg_store_g(sG + (uint32_t)(k ^ 1) * WG_G_BYTES, st, g_scale);
+                if (z + 2 < z_end) {  // and the loads of what step z + 1 stages
+                    wg_load_plane(st, hb, cin, vox, wrap(z + 3, D), y0, x0, H, Wd, vh);
+                    wg_load_g(st, gbat, cout, vox, z + 2, y0, x0, H, Wd, vg);
+                }
             }
         }
         // the column's last MMAs read the ring: wait for them before the next prologue
