@@ -54,6 +54,7 @@ template <>
 struct Store<STORE_F32> {
     using T = float2;
     using Raw = float2;
+    static constexpr bool kUnsignedIndex = true;  // neighbour addresses from unsigned cell indices
     __device__ __forceinline__ static Raw ld(const T* p) { return __ldg(p); }
     __device__ __forceinline__ static float2 cvt(Raw r) { return r; }
     __device__ __forceinline__ static float sub_f(Raw r, float c) { return __fsub_rn(r.x, c); }
@@ -71,6 +72,7 @@ template <>
 struct Store<STORE_F16> {
     using T = __half2;
     using Raw = unsigned int;
+    static constexpr bool kUnsignedIndex = false;
     __device__ __forceinline__ static Raw ld(const T* p) { return __ldg(reinterpret_cast<const unsigned int*>(p)); }
     __device__ __forceinline__ static float2 cvt(Raw r) {
         return __half22float2(*reinterpret_cast<const __half2*>(&r));
@@ -108,6 +110,7 @@ template <>
 struct Store<STORE_BF16> {
     using T = __nv_bfloat162;
     using Raw = unsigned int;
+    static constexpr bool kUnsignedIndex = true;
     __device__ __forceinline__ static Raw ld(const T* p) { return __ldg(reinterpret_cast<const unsigned int*>(p)); }
     __device__ __forceinline__ static float2 cvt(Raw r) {
         return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r));
