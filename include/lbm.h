@@ -264,7 +264,9 @@ lbm_ctx *lbm_batch_case(lbm_batch *b, int k);
  * LBM_STORAGE_AUTO and holds no state yet, each storage as well. The fastest form (and storage)
  * is kept for the class. Trial launches read each case's current state and write only its
  * other buffer, so the state is unchanged; cases without state are timed on the uniform rest
- * state. Synchronous. Without it every case runs in group launches of rows of x. */
+ * state. Synchronous. Without it a case with nx a multiple of 32 and at least 2^15 cells runs in
+ * dedicated launches and the others in group launches of tiles 2^a x 8 x 128/(2^a 8) (2^a the
+ * largest power of two up to 32 that divides nx, at least 8; 2D: 2^a x 128/2^a x 1). */
 int lbm_batch_tune(lbm_batch *b, int trial_steps);
 
 /* Tile shape (cells in x, y, z) of case k's group launch, its storage, and 1 if the case runs

@@ -371,13 +371,17 @@ int lbm_batch_create(lbm_batch** out, int n_cases, const lbm_case* cases, const 
                                  cs.rho_ratio, cs.mu_ratio, cs.body_force, &co, LBM_STORAGE_FP32);
         if (rc) return fail(berr(b, rc, "case %d: %s", k, lbm_last_error(nullptr)));
         b->cases[k]->batch_owned = true;
-        // default tile: rows of up to 128 cells in x, then y, then z
+        // Default form, the choice the tuner made for most classes on GB300: a case whose rows
+        // fill whole warps (nx a multiple of 32, at least 2^15 cells) runs in dedicated launches;
+        // the others in group launches whose tile is 2^a cells wide, 2^a the largest power of two
+        // up to 32 that divides nx (at least 8), then 8 in y (2D: all the rest), then z.
         const lbm::Params& P = b->cases[k]->P;
-        int txs = next_pow2_shift(P.nx);
-        if (txs > 7) txs = 7;
-        int tys = next_pow2_shift(P.ny);
-        if (tys > 7 - txs) tys = 7 - txs;
-        if (P.nz == 1) tys = 7 - txs;  // 2D: the tile stays in the plane
+        b->dedicated[k] = (P.nx % 32 == 0 && P.N >= 32768) ? 1 : 0;
+        int txs = 3;
+        while (txs < 5 && P.nx % (1 << (txs + 1)) == 0) ++txs;
+        if (txs > next_pow2_shift(P.nx)) txs = next_pow2_shift(P.nx);
+        int tys = (P.nz == 1) ? 7 - txs : (7 - txs < 3 ? 7 - txs : 3);
+        if (P.nz > 1 && tys > next_pow2_shift(P.ny)) tys = next_pow2_shift(P.ny);
         b->tx_shift[k] = txs;
         b->ty_shift[k] = tys;
     }

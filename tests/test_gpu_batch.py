@@ -34,7 +34,8 @@ def _mixed_cases():
              dict(grid=(16, 16, 16), storage=lbm.LBM_STORAGE_FP16, walls=7, rho_ratio=2.0, body_force=(0, 0, -1e-5)),
              dict(grid=(48, 48, 24), tau_f=0.3, sigma=5e-3),
              dict(grid=(12, 40, 8), storage=lbm.LBM_STORAGE_BF16, walls=3, mu_ratio=4.0),
-             dict(grid=(9, 7, 5), courant=1.0)]
+             dict(grid=(9, 7, 5), courant=1.0),
+             dict(grid=(32, 32, 32), sigma=2e-3)]  # rows of whole warps: dedicated launches by default
     out = []
     for s in specs:
         c = dict(base)
@@ -106,6 +107,20 @@ def test_batch_follows_steps_of_a_single_case():
     _assert_same(batch, singles)
 
 
+def test_default_forms():
+    """Without tuning: dedicated launches for rows of whole warps (nx a multiple of 32, at least
+    2^15 cells), group launches of tiles 2^a x 8 x 128/(8 2^a) otherwise."""
+    cases = _mixed_cases()
+    batch = _make_batch(cases)
+    for k, c in enumerate(cases):
+        tile, storage, dedicated = batch.config(k)
+        nx = c["grid"][0]
+        assert dedicated == (nx % 32 == 0 and np.prod(c["grid"]) >= 32768)
+        assert tile[0] * tile[1] * tile[2] == 128
+        if nx >= 8:
+            assert nx % tile[0] == 0 or tile[0] == 8
+
+
 def test_tuner_keeps_the_state_and_picks_valid_tiles():
     cases = _mixed_cases()
     batch, singles = _init_pair(cases)
@@ -131,7 +146,7 @@ def test_forms_set_by_hand_give_the_same_bits(dedicated):
     graph-replayed: still the bits of the single handles."""
     cases = _mixed_cases()
     batch, singles = _init_pair(cases, graph_steps=4)
-    shapes = [(8, 4, 4), (16, 1, 8), (8, 16, 1), (32, 4, 1), (8, 2, 8), (16, 8, 1)]
+    shapes = [(8, 4, 4), (16, 1, 8), (8, 16, 1), (32, 4, 1), (8, 2, 8), (16, 8, 1), (8, 8, 2)]
     for k in range(len(cases)):
         batch.set_config(k, shapes[k], dedicated)
         assert batch.config(k)[0] == shapes[k] and batch.config(k)[2] == dedicated
