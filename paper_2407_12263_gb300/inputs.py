@@ -25,17 +25,37 @@ WORKLOADS = {
 }
 
 
+def lattice_parameters(L0, U, Re, rho_ratio=1.0, mu_ratio=1.0, Ca=None, We=None, D=None, Cn=None, xi=4.0,
+                       Pe=None, M=0.02, g=(0.0, 0.0, 0.0)):
+    """The arguments of lbm_create (lattice units, dx = dt = 1) from the dimensionless groups of
+    a two-phase flow with reference length L0 and velocity U (cells, cells per step).
+
+    Fluid 1 (phi = 1) is the reference: rho1 = rho_ratio (fluid 2 has rho2 = 1) and
+    eta1 = mu_ratio eta2, with
+      Re = rho1 U L0 / eta1                 ->  eta1, and tau_f = eta2 / (rho2 cs^2);
+      Ca = eta1 U / sigma, or We = rho1 U^2 D / sigma (D defaults to L0)  ->  sigma;
+      Cn = xi / L0 (or xi given)            ->  xi;
+      Pe = U L0 / M (or M given)            ->  M, the mobility (M = tau_phi cs^2);
+    g is the body force (acceleration) vector. Exactly one of Ca and We must be given."""
+    if (Ca is None) == (We is None):
+        raise ValueError("give exactly one of Ca and We")
+    rho1 = float(rho_ratio)
+    eta1 = rho1 * U * L0 / Re
+    eta2 = eta1 / mu_ratio
+    sigma = eta1 * U / Ca if Ca is not None else rho1 * U * U * (L0 if D is None else D) / We
+    return dict(tau_f=eta2 / CS2, tau_g=0.8, M=(U * L0 / Pe) if Pe is not None else M,
+                xi=(Cn * L0) if Cn is not None else xi, sigma=sigma, rho_ratio=rho1, mu_ratio=float(mu_ratio),
+                body_force=tuple(float(v) for v in g))
+
+
 def _rayleigh_taylor(grid, Re=256.0, At=0.5, U=0.04, Ca=1.0, xi=4.0, M=0.02, steps=3600):
     """Single-mode Rayleigh-Taylor box (heavy fluid 1 on top, walls in z): lattice parameters
     from the dimensionless groups. Width W = nx, U = sqrt(g W), Re = rho1 U W / eta1,
     At = (rho1 - rho2)/(rho1 + rho2), Ca = eta1 U / sigma, viscosity ratio 1."""
     W = grid[0]
     rho1 = (1.0 + At) / (1.0 - At)          # rho2 = 1
-    g = U * U / W
-    eta1 = rho1 * U * W / Re
-    return dict(Q=19, grid=grid, xi=xi, sigma=eta1 * U / Ca, tau_f=eta1 / (1.0 / 3.0), tau_g=0.8, M=M,
-                rho_ratio=rho1, mu_ratio=1.0, body_force=(0.0, 0.0, -g), walls=4, amplitude=0.05 * W,
-                steps=steps, time_scale=W / U)
+    params = lattice_parameters(W, U, Re, rho_ratio=rho1, Ca=Ca, xi=xi, M=M, g=(0.0, 0.0, -U * U / W))
+    return dict(Q=19, grid=grid, **params, walls=4, amplitude=0.05 * W, steps=steps, time_scale=W / U)
 
 
 def cell_coords(grid):
@@ -93,10 +113,8 @@ def _taylor_green(n, Re=1000.0, We=20.0, u0=0.04, xi=4.0, M=0.02):
     of radius n/8 at the centre (phi = 0 inside), density and viscosity ratio 1,
     Re = rho0 u0 L0 / eta, We = rho0 u0^2 D / sigma (D = n/4), tau_f = eta / (rho0 cs^2)."""
     R = n / 8.0
-    eta = u0 * n / Re
-    return dict(Q=19, grid=(n, n, n), R=R, xi=xi, sigma=u0 * u0 * 2 * R / We, tau_f=3.0 * eta, tau_g=0.8, M=M,
-                rho_ratio=1.0, mu_ratio=1.0, body_force=(0.0, 0.0, 0.0), u0=u0, steps=int(n / u0),
-                time_scale=n / u0)
+    params = lattice_parameters(n, u0, Re, We=We, D=2 * R, xi=xi, M=M)
+    return dict(Q=19, grid=(n, n, n), R=R, **params, u0=u0, steps=int(n / u0), time_scale=n / u0)
 
 
 # Taylor-Green breakup: 256^3, u0 = 0.04, Re = 1000, R = 32, We = 20 (16-bit storage in the
