@@ -239,6 +239,21 @@ def test_zero_steps_and_state_errors():
     assert e.value.status == lbm.LBM_EINVAL
 
 
+def test_grid_beyond_device_memory_is_enomem():
+    """The largest grids the index range allows (nx ny nz < 2^31) do not fit the device in FP32
+    (two 152 B/cell state buffers of 1.64e9 cells, 498 GB): creation fails with LBM_ENOMEM, frees
+    what it allocated, and the device stays usable."""
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.Lattice((1280, 1280, 1000), 19, 0.8, 0.8, 0.02, 4.0, 1e-3)
+    assert e.value.status == lbm.LBM_ENOMEM
+    grid = (12, 10, 8)
+    g = lbm.Lattice(grid, 19, 0.8, 0.8, 0.02, 4.0, 1e-3)
+    g.init_phi(I.droplet_phi(grid, 3.0, 4.0))
+    s0 = g.mass()[0]
+    g.step(5)
+    assert g.mass()[0] == s0
+
+
 @pytest.mark.parametrize("bad", [1.6, -1.1, float("nan"), float("inf")])
 def test_phi_outside_fixed_point_range_rejected(bad):
     """phi is held as phi * 2^30 in 32 bits: initial phi and restored sum g outside [-1, 1.5]
