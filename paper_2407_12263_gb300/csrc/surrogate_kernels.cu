@@ -388,34 +388,111 @@ __device__ inline bool wait_parity(uint32_t mbar, uint32_t parity) {
     return false;
 }
 
-// One haloed z plane zz of the input into a ring slot, converted to FP16 and scaled (channels
-// >= cin are zero): a task is one haloed voxel and 8 channels (8 loads, one 16-byte store);
-// consecutive threads take consecutive voxels of a channel group, and a thread loads all its
-// tasks before it stores any, so that their loads are in flight together.
-template <typename TIN>
-__device__ __forceinline__ void conv_stage_plane(unsigned char* __restrict__ slot, const TIN* __restrict__ inb, int cin,
-                                                 float in_scale, long long vox, int zz, int y0, int x0, int H, int Wd) {
-    constexpr int kTasks = 4 * HPLANE, kPer = (kTasks + CONV_STAGERS - 1) / CONV_STAGERS;
-    float f[kPer][8];
+// A haloed row of one channel as loaded: the 8 values x0 .. x0 + 7 and the halo values x0 - 1
+// and x0 + 8 (periodic), kept in the storage type until they are written to shared memory.
+// vec: the row start is 16-byte aligned and x0 .. x0 + 7 lie inside the row.
+constexpr int kRunX = 8;
+template <typename TH>
+struct HRow;
+template <>
+struct HRow<__half> {
+    uint4 m;
+    __half l, r;
+    __device__ __forceinline__ void load(const __half* __restrict__ row, bool vec, int x0, int Wd) {
+        if (vec) {
+            m = __ldg(reinterpret_cast<const uint4*>(row + x0));
+        } else {
+            __half2 q[4];
 #pragma unroll
-    for (int i = 0; i < kPer; ++i) {
-        const int task = threadIdx.x + i * CONV_STAGERS;
-        const int c8 = task / HPLANE, v = task - c8 * HPLANE;
-        const int hx = v % HX, hy = v / HX;
-        const bool in_range = task < kTasks;
-        const TIN* src = inb + (long long)(8 * c8) * vox + ((long long)zz * H + wrap(y0 + hy - 1, H)) * Wd + wrap(x0 + hx - 1, Wd);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) f[i][j] = (in_range && 8 * c8 + j < cin) ? to_f(src[(long long)j * vox]) : 0.f;
+            for (int j = 0; j < 4; ++j) q[j] = __halves2half2(row[wrap(x0 + 2 * j, Wd)], row[wrap(x0 + 2 * j + 1, Wd)]);
+            m = *reinterpret_cast<const uint4*>(q);
+        }
+        l = row[wrap(x0 - 1, Wd)];
+        r = row[wrap(x0 + kRunX, Wd)];
     }
+    __device__ __forceinline__ void zero() {
+        m = make_uint4(0, 0, 0, 0);
+        l = r = __float2half_rn(0.f);
+    }
+    __device__ __forceinline__ void get(float (&v)[kRunX + 2]) const {
+        const __half2* h2 = reinterpret_cast<const __half2*>(&m);
 #pragma unroll
-    for (int i = 0; i < kPer; ++i) {
+        for (int j = 0; j < 4; ++j) {
+            const float2 f = __half22float2(h2[j]);
+            v[1 + 2 * j] = f.x;
+            v[2 + 2 * j] = f.y;
+        }
+        v[0] = __half2float(l);
+        v[kRunX + 1] = __half2float(r);
+    }
+};
+template <>
+struct HRow<float> {
+    float4 a, b;
+    float l, r;
+    __device__ __forceinline__ void load(const float* __restrict__ row, bool vec, int x0, int Wd) {
+        if (vec) {
+            a = __ldg(reinterpret_cast<const float4*>(row + x0));
+            b = __ldg(reinterpret_cast<const float4*>(row + x0 + 4));
+        } else {
+            a = make_float4(row[wrap(x0, Wd)], row[wrap(x0 + 1, Wd)], row[wrap(x0 + 2, Wd)], row[wrap(x0 + 3, Wd)]);
+            b = make_float4(row[wrap(x0 + 4, Wd)], row[wrap(x0 + 5, Wd)], row[wrap(x0 + 6, Wd)], row[wrap(x0 + 7, Wd)]);
+        }
+        l = row[wrap(x0 - 1, Wd)];
+        r = row[wrap(x0 + kRunX, Wd)];
+    }
+    __device__ __forceinline__ void zero() {
+        a = b = make_float4(0.f, 0.f, 0.f, 0.f);
+        l = r = 0.f;
+    }
+    __device__ __forceinline__ void get(float (&v)[kRunX + 2]) const {
+        v[0] = l;
+        v[1] = a.x; v[2] = a.y; v[3] = a.z; v[4] = a.w;
+        v[5] = b.x; v[6] = b.y; v[7] = b.z; v[8] = b.w;
+        v[kRunX + 1] = r;
+    }
+};
+
+// One haloed z plane of the input, a thread's share as loaded: tasks are (row, channel), ten
+// x-values each. Warps 0..6 stage; the MMA warp takes no tasks.
+constexpr int CV_TASKS = HY * 32, CV_PER = (CV_TASKS + CONV_STAGERS - 1) / CONV_STAGERS;
+
+template <typename TIN>
+struct ConvStage {
+    HRow<TIN> h[CV_PER];
+};
+
+template <typename TIN>
+__device__ __forceinline__ void conv_load_plane(ConvStage<TIN>& st, const TIN* __restrict__ inb, int cin, long long vox,
+                                                int zz, int y0, int x0, int H, int Wd, bool vec) {
+    if (threadIdx.x >= CONV_STAGERS) return;
+#pragma unroll
+    for (int i = 0; i < CV_PER; ++i) {
         const int task = threadIdx.x + i * CONV_STAGERS;
-        if (task >= kTasks) break;
-        const int c8 = task / HPLANE, v = task - c8 * HPLANE;
-        __half2 q[4];
+        const int r = task / 32, c = task % 32;
+        if (task < CV_TASKS && c < cin)
+            st.h[i].load(inb + (long long)c * vox + ((long long)zz * H + wrap(y0 + r - 1, H)) * Wd, vec, x0, Wd);
+        else
+            st.h[i].zero();
+    }
+}
+
+// The loaded rows into a ring slot in chunk planes, converted to FP16 and scaled: element
+// (haloed voxel v = HX r + hx, channel c) at (c / 8) PLP + 16 v + 2 (c % 8). Channels >= cin
+// are zero.
+template <typename TIN>
+__device__ __forceinline__ void conv_store_plane(unsigned char* __restrict__ slot, const ConvStage<TIN>& st, float in_scale) {
+    if (threadIdx.x >= CONV_STAGERS) return;
 #pragma unroll
-        for (int j2 = 0; j2 < 4; ++j2) q[j2] = __floats2half2_rn(f[i][2 * j2] * in_scale, f[i][2 * j2 + 1] * in_scale);
-        *reinterpret_cast<uint4*>(slot + c8 * PLP + v * 16) = *reinterpret_cast<const uint4*>(q);
+    for (int i = 0; i < CV_PER; ++i) {
+        const int task = threadIdx.x + i * CONV_STAGERS;
+        if (task >= CV_TASKS) break;
+        const int r = task / 32, c = task % 32;
+        float v[kRunX + 2];
+        st.h[i].get(v);
+        unsigned char* base = slot + (c >> 3) * PLP + (c & 7) * 2 + r * HX * 16;
+#pragma unroll
+        for (int hx = 0; hx < HX; ++hx) *reinterpret_cast<__half*>(base + hx * 16) = __float2half_rn(v[hx] * in_scale);
     }
 }
 
@@ -423,7 +500,7 @@ template <typename TIN, int MODE, typename TOUT>
 __global__ void __launch_bounds__(CONV_THREADS, 2)
 conv32_tc_kernel(const TIN* __restrict__ in, int cin, float in_scale, const __half* __restrict__ wimg,
                  const float* __restrict__ bias, TOUT* __restrict__ out, int cout, int D, int H, int Wd, int tiles_x,
-                 int tiles_y, int zchunk, int n_chunks, int n_columns, int* __restrict__ err) {
+                 int tiles_y, int zchunk, int n_chunks, int n_columns, int vec_in, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem;                   // ring of four haloed planes
     unsigned char* sW = smem + 4 * SLOT_BYTES;  // weights of the 27 taps
@@ -457,6 +534,7 @@ conv32_tc_kernel(const TIN* __restrict__ in, int cin, float in_scale, const __ha
     const uint32_t b_lo0 = (uint32_t)b_desc, b_hi = (uint32_t)(b_desc >> 32);
     const long long vox = (long long)D * H * Wd;
     const float out_scale = 1.0f / in_scale;  // in_scale is a power of two: exact
+    const bool vin = vec_in != 0;
     uint32_t phase = 0u, pending = 0u;        // per barrier k (bit k): the parity it waits for; a commit not waited for
     auto drain = [&](int k) {
         if (!((pending >> k) & 1u)) return true;
@@ -514,9 +592,14 @@ conv32_tc_kernel(const TIN* __restrict__ in, int cin, float in_scale, const __ha
         const int x0 = tx * TX, y0 = ty * TY;
         const int z_begin = zc * zchunk, z_end = min(z_begin + zchunk, D);
         const TIN* inb = in + (long long)b * cin * vox;
-        // prologue: planes z_begin - 1 .. z_begin + 1 in ring slots 0..2
-        for (int j = 0; j < 3; ++j)
-            conv_stage_plane(sA + j * SLOT_BYTES, inb, cin, in_scale, vox, wrap(z_begin - 1 + j, D), y0, x0, H, Wd);
+        // prologue: planes z_begin - 1 .. z_begin + 1 in ring slots 0..2, and the loads of the
+        // plane the first step stages in flight
+        ConvStage<TIN> st;
+        for (int j = 0; j < 3; ++j) {
+            conv_load_plane(st, inb, cin, vox, wrap(z_begin - 1 + j, D), y0, x0, H, Wd, vin);
+            conv_store_plane(sA + j * SLOT_BYTES, st, in_scale);
+        }
+        if (z_begin + 1 < z_end) conv_load_plane(st, inb, cin, vox, wrap(z_begin + 2, D), y0, x0, H, Wd, vin);
         for (int z = z_begin; z < z_end; ++z) {
             const int zi = z - z_begin, k = zi & 1;  // accumulator and barrier of this step
             asm volatile("fence.proxy.async.shared::cta;");
@@ -549,8 +632,10 @@ conv32_tc_kernel(const TIN* __restrict__ in, int cin, float in_scale, const __ha
                     epilogue(k ^ 1, b, z - 1, x0, y0);
                 }
             }
-            if (z + 1 < z_end)
-                conv_stage_plane(sA + (uint32_t)((zi + 3) & 3) * SLOT_BYTES, inb, cin, in_scale, vox, wrap(z + 2, D), y0, x0, H, Wd);
+            if (z + 1 < z_end) {  // plane z + 2, loaded during the previous step, and the next loads
+                conv_store_plane(sA + (uint32_t)((zi + 3) & 3) * SLOT_BYTES, st, in_scale);
+                if (z + 2 < z_end) conv_load_plane(st, inb, cin, vox, wrap(z + 3, D), y0, x0, H, Wd, vin);
+            }
             // the epilogue's reads of accumulator k ^ 1 come before the next step's MMAs into it
             asm volatile("tcgen05.fence::before_thread_sync;");
         }
@@ -603,97 +688,6 @@ constexpr uint32_t WG_PLANE_BYTES = WG_HY * WG_ROW_BYTES;        // 36,864
 constexpr uint32_t WG_G_BYTES = WG_TY * 512;                     // 8,192
 constexpr uint32_t WG_SMEM = 4 * WG_PLANE_BYTES + 2 * WG_G_BYTES; // 163,840
 
-// Eight consecutive values of a row as floats. vec: the row start is 16-byte aligned and all
-// eight lie inside the row (no wrap).
-__device__ __forceinline__ void load8(const __half* p, bool vec, int x0, int Wd, float (&v)[8]) {
-    if (vec) {
-        const uint4 q = __ldg(reinterpret_cast<const uint4*>(p + x0));
-        const __half2* h2 = reinterpret_cast<const __half2*>(&q);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float2 f = __half22float2(h2[j]);
-            v[2 * j] = f.x;
-            v[2 * j + 1] = f.y;
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = __half2float(p[wrap(x0 + j, Wd)]);
-    }
-}
-__device__ __forceinline__ void load8(const float* p, bool vec, int x0, int Wd, float (&v)[8]) {
-    if (vec) {
-        const float4 a = __ldg(reinterpret_cast<const float4*>(p + x0)), b = __ldg(reinterpret_cast<const float4*>(p + x0 + 4));
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-    } else {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = p[wrap(x0 + j, Wd)];
-    }
-}
-
-// A haloed row of h as loaded: the 8 values x0 .. x0 + 7 and the halo values x0 - 1 and
-// x0 + 8 (periodic), kept in the storage type until they are written to shared memory.
-template <typename TH>
-struct HRow;
-template <>
-struct HRow<__half> {
-    uint4 m;
-    __half l, r;
-    __device__ __forceinline__ void load(const __half* __restrict__ row, bool vec, int x0, int Wd) {
-        if (vec) {
-            m = __ldg(reinterpret_cast<const uint4*>(row + x0));
-        } else {
-            __half2 q[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) q[j] = __halves2half2(row[wrap(x0 + 2 * j, Wd)], row[wrap(x0 + 2 * j + 1, Wd)]);
-            m = *reinterpret_cast<const uint4*>(q);
-        }
-        l = row[wrap(x0 - 1, Wd)];
-        r = row[wrap(x0 + WG_TX, Wd)];
-    }
-    __device__ __forceinline__ void zero() {
-        m = make_uint4(0, 0, 0, 0);
-        l = r = __float2half_rn(0.f);
-    }
-    __device__ __forceinline__ void get(float (&v)[WG_TX + 2]) const {
-        const __half2* h2 = reinterpret_cast<const __half2*>(&m);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float2 f = __half22float2(h2[j]);
-            v[1 + 2 * j] = f.x;
-            v[2 + 2 * j] = f.y;
-        }
-        v[0] = __half2float(l);
-        v[WG_TX + 1] = __half2float(r);
-    }
-};
-template <>
-struct HRow<float> {
-    float4 a, b;
-    float l, r;
-    __device__ __forceinline__ void load(const float* __restrict__ row, bool vec, int x0, int Wd) {
-        if (vec) {
-            a = __ldg(reinterpret_cast<const float4*>(row + x0));
-            b = __ldg(reinterpret_cast<const float4*>(row + x0 + 4));
-        } else {
-            a = make_float4(row[wrap(x0, Wd)], row[wrap(x0 + 1, Wd)], row[wrap(x0 + 2, Wd)], row[wrap(x0 + 3, Wd)]);
-            b = make_float4(row[wrap(x0 + 4, Wd)], row[wrap(x0 + 5, Wd)], row[wrap(x0 + 6, Wd)], row[wrap(x0 + 7, Wd)]);
-        }
-        l = row[wrap(x0 - 1, Wd)];
-        r = row[wrap(x0 + WG_TX, Wd)];
-    }
-    __device__ __forceinline__ void zero() {
-        a = b = make_float4(0.f, 0.f, 0.f, 0.f);
-        l = r = 0.f;
-    }
-    __device__ __forceinline__ void get(float (&v)[WG_TX + 2]) const {
-        v[0] = l;
-        v[1] = a.x; v[2] = a.y; v[3] = a.z; v[4] = a.w;
-        v[5] = b.x; v[6] = b.y; v[7] = b.z; v[8] = b.w;
-        v[WG_TX + 1] = r;
-    }
-};
-
 // A thread's share of one haloed plane of h (tasks are (row, channel)) and of one step of g
 // (tasks are (row, output channel), 8 voxels each), as loaded. Loading and writing to shared
 // memory are separate so that the loads of the plane a step will need can be issued a whole
@@ -710,6 +704,7 @@ struct WgStage {
 template <typename TH>
 __device__ __forceinline__ void wg_load_plane(WgStage<TH>& st, const TH* __restrict__ hb, int cin, long long vox, int zz,
                                               int y0, int x0, int H, int Wd, bool vec) {
+    if (threadIdx.x >= WG_STAGERS) return;  // the MMA warp takes no tasks
 #pragma unroll
     for (int i = 0; i < WG_H_PER; ++i) {
         const int task = threadIdx.x + i * WG_STAGERS;
@@ -724,6 +719,7 @@ __device__ __forceinline__ void wg_load_plane(WgStage<TH>& st, const TH* __restr
 // The three x-shifted 8-voxel windows of every loaded row, 16 bytes each.
 template <typename TH>
 __device__ __forceinline__ void wg_store_plane(unsigned char* __restrict__ slot, const WgStage<TH>& st) {
+    if (threadIdx.x >= WG_STAGERS) return;
 #pragma unroll
     for (int i = 0; i < WG_H_PER; ++i) {
         const int task = threadIdx.x + i * WG_STAGERS;
@@ -745,6 +741,7 @@ __device__ __forceinline__ void wg_store_plane(unsigned char* __restrict__ slot,
 template <typename TH>
 __device__ __forceinline__ void wg_load_g(WgStage<TH>& st, const float* __restrict__ gb, int cout, long long vox, int z,
                                           int y0, int x0, int H, int Wd, bool vec) {
+    if (threadIdx.x >= WG_STAGERS) return;
 #pragma unroll
     for (int i = 0; i < WG_G_PER; ++i) {
         const int task = threadIdx.x + i * WG_STAGERS;
@@ -770,6 +767,7 @@ __device__ __forceinline__ void wg_load_g(WgStage<TH>& st, const float* __restri
 // g scaled and rounded to FP16, one (row, output channel) per 16-byte store.
 template <typename TH>
 __device__ __forceinline__ void wg_store_g(unsigned char* __restrict__ buf, const WgStage<TH>& st, float g_scale) {
+    if (threadIdx.x >= WG_STAGERS) return;
 #pragma unroll
     for (int i = 0; i < WG_G_PER; ++i) {
         const int task = threadIdx.x + i * WG_STAGERS;
@@ -1015,6 +1013,8 @@ cudaError_t conv32_tc(const void* in, int in_fp16, int cin, float in_scale, cons
     const int n_chunks = (D + zchunk - 1) / zchunk;
     const int n_columns = tx * ty * n_chunks * batch;
     const int blocks = n_columns < tc_blocks() ? n_columns : tc_blocks();
+    // 16-byte row loads where every 8-voxel run is aligned and inside its row
+    const int vec_in = (Wd % 8 == 0) && ((uintptr_t)in % 16 == 0);
 #define LBM_TC(TIN, MODE, TOUT)                                                                                    \
     do {                                                                                                           \
         cudaError_t e_ = cudaFuncSetAttribute(tc::conv32_tc_kernel<TIN, MODE, TOUT>,                              \
@@ -1022,7 +1022,7 @@ cudaError_t conv32_tc(const void* in, int in_fp16, int cin, float in_scale, cons
         if (e_ != cudaSuccess) return e_;                                                                          \
         tc::conv32_tc_kernel<TIN, MODE, TOUT><<<blocks, tc::CONV_THREADS, tc::SMEM, s>>>(                          \
             (const TIN*)in, cin, in_scale, wimg, bias, (TOUT*)out, cout, D, H, Wd, tx, ty, zchunk, n_chunks,       \
-            n_columns, err);                                                                                       \
+            n_columns, vec_in, err);                                                                               \
     } while (0)
     if (in_fp16 && out_fp16 && relu) LBM_TC(__half, 1, __half);
     else if (!in_fp16 && !out_fp16 && !relu) LBM_TC(float, 0, float);
