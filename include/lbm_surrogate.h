@@ -11,10 +11,10 @@
  * Four periodic 3x3x3 convolutions, 5 -> 32 -> 32 -> 32 -> 5 channels, ReLU after the first
  * three; the prediction is input + output (a residual step). Convolutions accumulate in FP32;
  * activations between layers are stored in FP16 (or FP32, for gradient checks). With FP16
- * activations the 32 -> 32 layers and their adjoints run on the tensor cores (tcgen05, FP16
- * operands, FP32 accumulation in tensor memory); the rest, and everything in FP32 mode, on the
- * CUDA cores. A tensor-core wait that times out makes the next synchronising call return
- * LBM_ETIMEOUT. Weights are
+ * activations every layer (channels zero-padded to 32), its adjoint and its weight gradients
+ * run on the tensor cores (tcgen05, FP16 operands, FP32 accumulation in tensor memory); in
+ * FP32 mode everything runs on the CUDA cores. A tensor-core wait that times out makes the
+ * next synchronising call return LBM_ETIMEOUT. Weights are
  * FP32 ([Cout][Cin][27] then bias [Cout] per layer, tap = 9 dz + 3 dy + dx for the input offset
  * (dz-1, dy-1, dx-1)). Training minimises the (channel-weighted) mean squared error with Adam
  * (0.9, 0.999, 1e-8).

@@ -323,10 +323,11 @@ cudaError_t adam(float* p, const float* g, float* m, float* v, long long n, floa
 //
 // A CTA walks a column of steps along z (a chunk of z planes of one (x, y) tile) with the
 // haloed planes in a ring of four and two accumulators in tensor memory: one thread issues the
-// 54 MMAs of step z (27 taps x 2 of K = 16) and commits them to an mbarrier; meanwhile the
-// threads stage plane z + 2 into the slot step z - 1 read, and the four epilogue warps read the
-// accumulator of step z - 1 (tcgen05.ld) and write its output. Waits are bounded: on a timeout
-// the kernel raises *err, waits once more for its MMAs, frees its tensor memory and returns.
+// 54 MMAs of step z (27 taps x 2 of K = 16) and commits them to an mbarrier; meanwhile four
+// warps read the accumulator of step z - 1 (tcgen05.ld) and write its output, and seven warps
+// write plane z + 2 (loaded during step z - 1) into the slot step z - 1 read and issue the
+// loads of plane z + 3. Waits are bounded: on a timeout the kernel raises *err, waits once more
+// for its MMAs, frees its tensor memory and returns.
 // ---------------------------------------------------------------------------------------
 namespace tc {
 
