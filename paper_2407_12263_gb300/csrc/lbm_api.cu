@@ -35,6 +35,9 @@ int set_error(lbm_ctx* ctx, int code, const char* fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(buf, 512, fmt, ap);
     va_end(ap);
+    // a failed allocation is reported here, synchronously, and is not sticky: clear it, or the
+    // next launch's error check would report it again
+    if (code == LBM_ENOMEM) (void)cudaGetLastError();
     return code;
 }
 

@@ -53,6 +53,9 @@ int nerr(lbm_net* n, int code, const char* fmt, ...) {
     va_start(ap, fmt);
     std::vsnprintf(dst, 512, fmt, ap);
     va_end(ap);
+    // a failed allocation is reported here, synchronously, and is not sticky: clear it, or the
+    // next launch's error check would report it again
+    if (code == LBM_ENOMEM) (void)cudaGetLastError();
     return code;
 }
 

@@ -183,3 +183,23 @@ def test_invalid_wall_masks_rejected():
         with pytest.raises(lbm.LBMError) as e:
             lbm.lbm_create(grid, Q, 0.8, 0.8, 0.02, 4.0, 1e-3, opts=o)
         assert e.value.status == lbm.LBM_EINVAL
+
+
+def test_full_size_rayleigh_taylor_parity():
+    """The 128 x 128 x 512 workload (walls in z, At = 0.5, Re = 256, Ca = 1) at full size, in the
+    launch configuration the benchmark times: every cell after 10 steps against the oracle with
+    the FP32 bounds, and sum phi unchanged over 200 more steps."""
+    w = I.WORKLOADS["rayleigh_taylor_128x128x512"]
+    params = dict(tau_f=w["tau_f"], tau_g=w["tau_g"], M=w["M"], xi=w["xi"], sigma=w["sigma"],
+                  rho_ratio=w["rho_ratio"], mu_ratio=w["mu_ratio"], body_force=w["body_force"])
+    phi0 = I.rayleigh_taylor_phi(w["grid"], w["amplitude"], w["xi"])
+    gpu = lbm.Lattice(w["grid"], 19, walls=w["walls"], **params)
+    ref = O.Oracle(19, w["grid"], walls=w["walls"], **params)
+    gpu.init_phi(phi0)
+    ref.init_phi(phi0)
+    s0 = gpu.mass()[0]
+    gpu.step(10)
+    ref.step(10)
+    _check(gpu, ref)
+    gpu.step(200)
+    assert gpu.mass()[0] == s0
