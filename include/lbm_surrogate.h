@@ -94,8 +94,9 @@ typedef struct {
  *   4. run judge_steps LBM steps and compare how far phi moves per step with the rate the
  *      prediction implies (|phi_after - phi_restart| / judge_steps against
  *      |phi_pred - phi_before| / k, coarse, L1, phi_restart the coarse phi right after the
- *      restart); reject if the ratio exceeds relax_tol: a prediction whose phi, u and p do not
- *      fit together relaxes fast;
+ *      restart; phi_restart and phi_after are block means of the state's own phi when factor
+ *      divides 32); reject if the ratio exceeds relax_tol: a prediction whose phi, u and p do
+ *      not fit together relaxes fast;
  *   5. on rejection restore the starting state and advance it k steps with the LBM.
  * Synchronous. Needs a workspace of one more state buffer plus four coarse field arrays: the
  * first jump on a handle allocates it (or lbm_surrogate_reserve, beforehand) and the handle keeps

@@ -453,13 +453,19 @@ int lbm_surrogate_jump(lbm_ctx* c, lbm_net* n, int f, const float mean_std[10], 
     if (accept) {
         if ((rc = lbm_restart_from_coarse(c, f, pred, saved_P.w0d / 3.0))) return rc;
         // phi right after the restart (it differs from the prediction by the smoothing of
-        // upsampling and block means, which is not motion) and judge_steps steps later
+        // upsampling and block means, which is not motion) and judge_steps steps later: block
+        // means of the state's own phi (plane 0), where the factor allows, else of the
+        // propagated state's moments
+        auto coarse_phi = [&]() {
+            if (f <= 32 && 32 % f == 0) return cu(lbm::launch_coarse_phi(c->P, c->fg[c->cur], f, in, c->stream));
+            return lbm_coarse_fields(c, f, in);
+        };
         std::vector<float> h_r((size_t)nc), h_after((size_t)nc);
-        if ((rc = lbm_coarse_fields(c, f, in))) return rc;
+        if ((rc = coarse_phi())) return rc;
         if ((rc = cu(cudaStreamSynchronize(c->stream)))) return rc;
         if ((rc = cu(cudaMemcpy(h_r.data(), in, (size_t)nc * sizeof(float), cudaMemcpyDeviceToHost)))) return rc;
         if ((rc = lbm_step(c, judge_steps))) return rc;
-        if ((rc = lbm_coarse_fields(c, f, in))) return rc;
+        if ((rc = coarse_phi())) return rc;
         if ((rc = cu(cudaStreamSynchronize(c->stream)))) return rc;
         if ((rc = cu(cudaMemcpy(h_after.data(), in, (size_t)nc * sizeof(float), cudaMemcpyDeviceToHost)))) return rc;
         double relax = 0.0;

@@ -54,6 +54,9 @@ cudaError_t wgrad32_tc(const float* g, int cout, float g_scale, const void* h, i
 // Coarse fields [5][nz/f][ny/f][nx/f] (phi, u, v, w, p; means over f^3 cells of the macroscopic
 // fields of the difference-free scheme) of the propagated state fg.
 cudaError_t launch_coarsen(const Params& P, const void* fg, int factor, float* out, cudaStream_t s);
+// Block means of the state's own phi (plane 0, before propagation) into out [nz/f][ny/f][nx/f];
+// factor must divide 32 (cudaErrorInvalidValue otherwise).
+cudaError_t launch_coarse_phi(const Params& P, const void* fg, int factor, float* out, cudaStream_t s);
 // The state launch_init builds (equilibrium plus the first-order non-equilibrium part of g) from
 // coarse fields upsampled trilinearly between coarse cell centres (periodic, clamped across
 // walls), in FP32 arithmetic and in one pass: no staging.

@@ -118,6 +118,34 @@ cudaError_t launch_coarsen(const Params& P, const void* fg, int factor, float* o
     return cudaGetLastError();
 }
 
+// Block means over f^3 cells of the state's own phi, the fixed-point value of plane 0 (no
+// propagation: 8 bytes read per cell). Lane l of a warp takes fine x = 32 b + l; f divides 32,
+// and each aligned group of f lanes is summed with shuffles.
+__global__ void coarse_phi_kernel(const float2* __restrict__ plane0, int nx, int ny, int nz, int f, float* __restrict__ out) {
+    const int lane = threadIdx.x;
+    const int x = blockIdx.x * 32 + lane;
+    const int cy = blockIdx.y * blockDim.y + threadIdx.y;
+    const int cz = blockIdx.z;
+    const int ncx = nx / f, ncy = ny / f;
+    if (cy >= ncy) return;  // whole warps leave together
+    const bool valid = x < nx;
+    long long acc = 0;
+    if (valid)
+        for (int dz = 0; dz < f; ++dz)
+            for (int dy = 0; dy < f; ++dy)
+                acc += __float_as_int(__ldg(plane0 + ((long long)(cz * f + dz) * ny + (cy * f + dy)) * nx + x).y);
+    for (int o = f >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (!valid || lane % f) return;
+    out[((long long)cz * ncy + cy) * ncx + x / f] = (float)((double)acc / (kPhiFx * (double)f * f * f));
+}
+
+cudaError_t launch_coarse_phi(const Params& P, const void* fg, int factor, float* out, cudaStream_t s) {
+    if (factor > 32 || 32 % factor) return cudaErrorInvalidValue;
+    const dim3 block(32, 4), grid((P.nx + 31) / 32, (P.ny / factor + 3) / 4, P.nz / factor);
+    coarse_phi_kernel<<<grid, block, 0, s>>>(moment_plane(fg), P.nx, P.ny, P.nz, factor, out);
+    return cudaGetLastError();
+}
+
 // Where fine coordinate i (of n = nc f cells) falls between coarse cell centres: the two coarse
 // indices and the weight of the second. Periodic, or clamped to the end centres across a wall.
 struct Axis {
