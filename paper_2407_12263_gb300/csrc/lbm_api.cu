@@ -317,8 +317,10 @@ int lbm::ctx_restart_from_coarse(lbm_ctx* c, int f, const float* coarse, double 
     P.w0d = p0 * 3.0;
     P.w0 = (float)P.w0d;
     drop_graphs(c);
-    LBM_CUDA(c, lbm::launch_restart(P, coarse, f, p0, c->fg[c->cur], c->stream));
-    c->launches += 1;
+    rc = ensure_staging(c, ((size_t)P.N + 1) / 2);  // N floats of upsampled phi
+    if (rc) return rc;
+    LBM_CUDA(c, lbm::launch_restart(P, coarse, f, p0, reinterpret_cast<float*>(c->staging), c->fg[c->cur], c->stream));
+    c->launches += 2;
     c->initialised = true;
     c->version += 1;
     return LBM_OK;

@@ -59,8 +59,10 @@ cudaError_t launch_coarsen(const Params& P, const void* fg, int factor, float* o
 cudaError_t launch_coarse_phi(const Params& P, const void* fg, int factor, float* out, cudaStream_t s);
 // The state launch_init builds (equilibrium plus the first-order non-equilibrium part of g) from
 // coarse fields upsampled trilinearly between coarse cell centres (periodic, clamped across
-// walls), in FP32 arithmetic and in one pass: no staging.
-cudaError_t launch_restart(const Params& P, const float* coarse, int factor, double p0, void* fg, cudaStream_t s);
+// walls), in FP32 arithmetic: the upsampled phi of every cell into phi_fine (N floats), then the
+// populations.
+cudaError_t launch_restart(const Params& P, const float* coarse, int factor, double p0, float* phi_fine, void* fg,
+                           cudaStream_t s);
 // Adds delta units (2^-30) of phi to the state, spread over the cells so that it sums exactly.
 cudaError_t launch_adjust_phi(const Params& P, void* fg, long long delta, cudaStream_t s);
 // (x - mean[c]) / std[c] per channel of [5][n] (dir = +1) or x std[c] + mean[c] (dir = -1).

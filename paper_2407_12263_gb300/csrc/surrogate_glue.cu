@@ -188,32 +188,41 @@ __device__ __forceinline__ float trilinear(const float* __restrict__ q, int ncx,
 
 // The initial-state construction of init_kernel (equilibria of the upsampled phi, u, p plus the
 // first-order non-equilibrium part of g, grad phi from the isotropic central difference of the
-// upsampled phi) in FP32, written directly as deviations from the storage's reference levels.
-// phi is clamped to [-1, 1.5], the range lbm_init_fields accepts, so that its fixed-point value
-// stays in range whatever the prediction holds.
+// upsampled phi, which phi_fine_kernel writes first) in FP32, written directly as deviations
+// from the storage's reference levels. phi is clamped to [-1, 1.5], the range lbm_init_fields
+// accepts, so that its fixed-point value stays in range whatever the prediction holds.
+// The upsampled phi of every cell (clamped as below), the first pass of the restart.
+__global__ void phi_fine_kernel(const Params P, const float* __restrict__ coarse, int f, float* __restrict__ phi) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= P.nx || y >= P.ny) return;
+    const int ncx = P.nx / f, ncy = P.ny / f, ncz = P.nz / f;
+    const float v = trilinear(coarse, ncx, ncy, interp_axis(x, f, ncx, P.walls & 1), interp_axis(y, f, ncy, P.walls & 2),
+                              interp_axis(z, f, ncz, P.walls & 4));
+    phi[((long long)z * P.ny + y) * P.nx + x] = fminf(fmaxf(v, -1.0f), 1.5f);
+}
+
 template <int Q, int S>
-__global__ void restart_kernel(const Params P, const float* __restrict__ coarse, int f, float p0, void* __restrict__ fg) {
+__global__ void restart_kernel(const Params P, const float* __restrict__ coarse, const float* __restrict__ phi_fine, int f,
+                               float p0, void* __restrict__ fg) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= P.nx || y >= P.ny) return;
     const int ncx = P.nx / f, ncy = P.ny / f, ncz = P.nz / f;
     const long long nc = (long long)ncx * ncy * ncz;
-    // the axes at x - 1, x, x + 1 (periodic images; across a wall the cell itself, so that the
-    // normal gradient vanishes there)
-    Axis ax[3], ay[3], az[3];
+    // neighbour rows and columns: periodic images, or across a wall the cell itself (so that
+    // the normal gradient vanishes there)
+    int xs[3], ys[3], zs[3];
 #pragma unroll
     for (int d = -1; d <= 1; ++d) {
-        int xx = x + d, yy = y + d, zz = z + d;
-        xx = (P.walls & 1) ? min(max(xx, 0), P.nx - 1) : (xx + P.nx) % P.nx;
-        yy = (P.walls & 2) ? min(max(yy, 0), P.ny - 1) : (yy + P.ny) % P.ny;
-        zz = (P.walls & 4) ? min(max(zz, 0), P.nz - 1) : (zz + P.nz) % P.nz;
-        ax[d + 1] = interp_axis(xx, f, ncx, P.walls & 1);
-        ay[d + 1] = interp_axis(yy, f, ncy, P.walls & 2);
-        az[d + 1] = interp_axis(zz, f, ncz, P.walls & 4);
+        xs[d + 1] = (P.walls & 1) ? min(max(x + d, 0), P.nx - 1) : (x + d + P.nx) % P.nx;
+        ys[d + 1] = (P.walls & 2) ? min(max(y + d, 0), P.ny - 1) : (y + d + P.ny) % P.ny;
+        zs[d + 1] = (P.walls & 4) ? min(max(z + d, 0), P.nz - 1) : (z + d + P.nz) % P.nz;
     }
     auto phi_at = [&](int dx, int dy, int dz) {
-        return fminf(fmaxf(trilinear(coarse, ncx, ncy, ax[dx + 1], ay[dy + 1], az[dz + 1]), -1.0f), 1.5f);
+        return __ldg(phi_fine + ((long long)zs[dz + 1] * P.ny + ys[dy + 1]) * P.nx + xs[dx + 1]);
     };
     const float phi = phi_at(0, 0, 0);
     float gx = 0.f, gy = 0.f, gz = 0.f;
@@ -227,10 +236,11 @@ __global__ void restart_kernel(const Params P, const float* __restrict__ coarse,
     gx *= 3.f;
     gy *= 3.f;
     gz *= 3.f;
-    const float u[3] = {trilinear(coarse + nc, ncx, ncy, ax[1], ay[1], az[1]),
-                        trilinear(coarse + 2 * nc, ncx, ncy, ax[1], ay[1], az[1]),
-                        trilinear(coarse + 3 * nc, ncx, ncy, ax[1], ay[1], az[1])};
-    const float pc = trilinear(coarse + 4 * nc, ncx, ncy, ax[1], ay[1], az[1]);
+    const Axis ax = interp_axis(x, f, ncx, P.walls & 1), ay = interp_axis(y, f, ncy, P.walls & 2),
+               az = interp_axis(z, f, ncz, P.walls & 4);
+    const float u[3] = {trilinear(coarse + nc, ncx, ncy, ax, ay, az), trilinear(coarse + 2 * nc, ncx, ncy, ax, ay, az),
+                        trilinear(coarse + 3 * nc, ncx, ncy, ax, ay, az)};
+    const float pc = trilinear(coarse + 4 * nc, ncx, ncy, ax, ay, az);
     const float g2 = gx * gx + gy * gy + gz * gz;
     const float gn = sqrtf(g2);
     const float inv = (g2 > kNormalGuard) ? 1.0f / gn : 0.f;
@@ -264,9 +274,11 @@ __global__ void restart_kernel(const Params P, const float* __restrict__ coarse,
     moment_plane(fg)[c] = make_float2(fsum, __int_as_float(__float2int_rn(phi * 1073741824.0f)));
 }
 
-cudaError_t launch_restart(const Params& P, const float* coarse, int factor, double p0, void* fg, cudaStream_t s) {
+cudaError_t launch_restart(const Params& P, const float* coarse, int factor, double p0, float* phi_fine, void* fg,
+                           cudaStream_t s) {
     const dim3 block(32, 4), grid((P.nx + 31) / 32, (P.ny + 3) / 4, P.nz);
-#define LBM_RESTART(Q, S) restart_kernel<Q, S><<<grid, block, 0, s>>>(P, coarse, factor, (float)p0, fg)
+    phi_fine_kernel<<<grid, block, 0, s>>>(P, coarse, factor, phi_fine);
+#define LBM_RESTART(Q, S) restart_kernel<Q, S><<<grid, block, 0, s>>>(P, coarse, phi_fine, factor, (float)p0, fg)
     if (P.Q == 9) {
         if (P.storage == STORE_F16) LBM_RESTART(9, STORE_F16);
         else if (P.storage == STORE_BF16) LBM_RESTART(9, STORE_BF16);
