@@ -961,15 +961,12 @@ cudaError_t weight_image(const float* W, int cout, int cin, __half* img, cudaStr
 
 size_t weight_image_bytes() { return tc::W_BYTES; }
 
+// Two persistent CTAs per SM of the current device.
 static int tc_blocks() {
-    static int blocks = 0;
-    if (!blocks) {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        blocks = 2 * (sms > 0 ? sms : 1);
-    }
-    return blocks;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return 2 * (sms > 0 ? sms : 1);
 }
 
 cudaError_t wgrad32_tc(const float* g, int cout, float g_scale, const void* h, int h_fp16, int cin, float* gW, float* gb,
