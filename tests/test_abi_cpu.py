@@ -36,6 +36,26 @@ def test_every_declared_symbol_is_exported(lib):
     assert {s[0] for s in lbm.SIGNATURES} >= set(names)
 
 
+def _declared_arity():
+    """Number of parameters of every lbm_* prototype in include/*.h (comments stripped)."""
+    out = {}
+    for h in (ROOT / "include").glob("*.h"):
+        text = re.sub(r"/\*.*?\*/", "", h.read_text(), flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[a-z_ ]+\**\s*\**(lbm_\w+)\s*\(([^;{]*?)\)\s*;", text, flags=re.M | re.S):
+            params = m.group(2).strip()
+            out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_argument_counts_match_the_headers():
+    """Every signature the ctypes binding declares takes as many arguments as the C prototype."""
+    arity = _declared_arity()
+    assert len(arity) >= 14
+    for name, _, argtypes in lbm.SIGNATURES:
+        assert name in arity, name
+        assert len(argtypes) == arity[name], (name, len(argtypes), arity[name])
+
+
 def test_library_is_built_for_sm_103a():
     assert "arch=compute_103a,code=sm_103a" in " ".join(cuda_build.ARCH)
     assert lbm.library_path().exists()
