@@ -47,6 +47,27 @@ def _declared_arity():
     return out
 
 
+def _declared_return_types():
+    out = {}
+    for h in (ROOT / "include").glob("*.h"):
+        text = re.sub(r"/\*.*?\*/", "", h.read_text(), flags=re.S)
+        for m in re.finditer(r"^\s*((?:const\s+)?[a-z_ ]+?\s*\**)\s*(lbm_\w+)\s*\(", text, flags=re.M):
+            out[m.group(2)] = " ".join(m.group(1).replace("*", " * ").split())
+    return out
+
+
+def test_binding_return_types_match_the_headers():
+    want = {"int": ctypes.c_int, "void": None, "const char *": ctypes.c_char_p, "long long": ctypes.c_longlong,
+            "double": ctypes.c_double}
+    declared = _declared_return_types()
+    for name, restype, _ in lbm.SIGNATURES:
+        c_type = declared[name]
+        if c_type.endswith("*") and c_type != "const char *":
+            assert restype is ctypes.c_void_p, (name, c_type, restype)  # a handle
+        else:
+            assert restype is want[c_type], (name, c_type, restype)
+
+
 def test_binding_argument_counts_match_the_headers():
     """Every signature the ctypes binding declares takes as many arguments as the C prototype."""
     arity = _declared_arity()
