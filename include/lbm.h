@@ -181,10 +181,17 @@ int lbm_lattice_tables(int lattice, int *d, int *e, double *w);
  *             Q planes [Q][nz][ny][nx], x fastest, plane 0 the rest population, in the
  *             velocity order above. Read only.
  *   lattice   LBM_D2Q9 or LBM_D3Q19; grid[3] as for lbm_create.
+ *   walls     the mask of walled axes, as lbm_opts.walls (0 = fully periodic). Where the
+ *             propagation stencil of a cell crosses a wall it reads the opposite population of
+ *             the same cell (half-way bounce-back), as the time step does.
  *   courant   Lax-Wendroff Courant number, 0 < c <= 1. rho_ratio > 0 as for lbm_create.
- *   result    device pointer to 3 doubles, written with: sum phi and sum rho phi over the
- *             propagated state (the quantities of lbm_mass), then the count of non-finite
- *             values among the stored populations.
+ *   result    device pointer to 3 doubles, written with: sum phi and sum rho phi (the mass
+ *             m = sum rho phi of Sec. 3.3) over the propagated state, then the count of
+ *             non-finite values among the stored populations. phi of each cell is the FP32
+ *             sum of its propagated g_i, accumulated in FP64. It is therefore not the exact
+ *             fixed-point sum lbm_mass reports for a handle, which the time step conserves bit
+ *             for bit: for the same state the two agree to about 1e-7 relative (FP32 rounding
+ *             of each cell's phi).
  *   stream    cudaStream_t to launch on (NULL = the default stream). Asynchronous: result is
  *             ready when the stream reaches this point.
  * Scratch. The per-block partial sums live in a static device array that every GPU loading
@@ -194,10 +201,11 @@ int lbm_lattice_tables(int lattice, int *d, int *e, double *w);
  * write their slots before the call's final sum reads them, so nothing needs clearing between
  * calls, but calls that overlap on the GPU (two streams, two threads) race on it and must be
  * serialised by the caller.
- * The first call on each device looks up the array's device address; make that first call
- * before any stream capture. Returns LBM_ECUDA if the lookup or the launch fails.
+ * Each call looks up the array's device address in the current context, so the entry point
+ * stays valid after a device reset. Returns LBM_ECUDA if the lookup or a launch fails; an
+ * error left on the thread by earlier work is neither reported nor cleared by this call.
  */
-int lbm_mass_noalloc(const float *g, int lattice, const int grid[3], double courant,
+int lbm_mass_noalloc(const float *g, int lattice, const int grid[3], int walls, double courant,
                      double rho_ratio, double *result, void *stream);
 
 /* Message of the last failure (see the error notes above); never NULL. */

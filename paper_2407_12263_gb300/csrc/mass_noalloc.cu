@@ -14,7 +14,6 @@
 
 #include <climits>
 #include <cmath>
-#include <mutex>
 
 #include "../../include/lbm.h"
 #include "cell.cuh"
@@ -27,27 +26,6 @@ constexpr int kNoallocMaxBlocks = 2048;  // partial triples the static scratch h
 
 // One FP64 triple (sum phi, sum rho phi, non-finite count) per block of the last call.
 static __device__ __align__(256) double g_noalloc_partials[3 * kNoallocMaxBlocks];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mutex;
-double* g_scratch_ptr[kMaxDevices] = {};
-
-// Address of the scratch array on the current device, resolved once per device.
-cudaError_t scratch_on_current_device(double** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = static_cast<double*>(p);
-    }
-    *out = g_scratch_ptr[dev];
-    return cudaSuccess;
-}
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -76,6 +54,8 @@ __device__ __forceinline__ void block_sum3_d(double (&v)[3], double* out) {
 
 // Block b covers z-layer b / bpl, rows [r0, r1) of it; it writes its triple to partials[b].
 // phi = sum_i of the Lax-Wendroff-propagated g_i (plane 0, the rest population, does not move).
+// Where a stencil point x -+ e_i lies beyond a wall, it reads the opposite population of this
+// cell (half-way bounce-back), as the time step does.
 template <int Q>
 __global__ void __launch_bounds__(kNoallocThreads)
 mass_noalloc_kernel(const Params P, const float* __restrict__ g, int blocks_per_layer, double* __restrict__ partials) {
@@ -89,14 +69,16 @@ mass_noalloc_kernel(const Params P, const float* __restrict__ g, int blocks_per_
         const int y = r0 + k / P.nx, x = k % P.nx;
         const int c = (z * P.ny + y) * P.nx + x;
         const Nbr nb = make_nbr(P, x, y, z);
+        const WallSide ws = make_wall_side(P, x, y, z);
         float phi = __ldg(g + c);
         int bad = !isfinite(phi);
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
             const float* gq = g + i * N;
+            const float* back = g + Lat<Q>::opp(i) * N + c;
             const float g0 = __ldg(gq + c);
-            const float gm = __ldg(gq + c + link_offset<Q>(nb, i, -1));
-            const float gp = __ldg(gq + c + link_offset<Q>(nb, i, +1));
+            const float gm = __ldg(crosses_wall<Q>(ws, i, -1) ? back : gq + c + link_offset<Q>(nb, i, -1));
+            const float gp = __ldg(crosses_wall<Q>(ws, i, +1) ? back : gq + c + link_offset<Q>(nb, i, +1));
             phi += g0 + (P.lw_m * (gm - g0) + P.lw_p * (gp - g0));
             bad += !isfinite(g0);
         }
@@ -119,8 +101,8 @@ mass_noalloc_finish(const double* __restrict__ partials, int n, double* __restri
 }  // namespace
 }  // namespace lbm
 
-extern "C" int lbm_mass_noalloc(const float* g, int lattice, const int grid[3], double courant, double rho_ratio,
-                                double* result, void* stream) {
+extern "C" int lbm_mass_noalloc(const float* g, int lattice, const int grid[3], int walls, double courant,
+                                double rho_ratio, double* result, void* stream) {
     if (!g || !grid || !result) return LBM_EINVAL;
     if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19) return LBM_EINVAL;
     const int nx = grid[0], ny = grid[1], nz = grid[2];
@@ -129,10 +111,18 @@ extern "C" int lbm_mass_noalloc(const float* g, int lattice, const int grid[3], 
     // The static scratch holds kNoallocMaxBlocks partial triples and each z-layer takes at least
     // one block, so grids deeper than that are rejected.
     if (nz > lbm::kNoallocMaxBlocks) return LBM_EINVAL;
+    if (walls < 0 || walls > 7 || (lattice == LBM_D2Q9 && (walls & 4))) return LBM_EINVAL;
     if (!(courant > 0 && courant <= 1) || !(rho_ratio > 0) || !std::isfinite(rho_ratio)) return LBM_EINVAL;
 
-    double* partials = nullptr;
-    if (lbm::scratch_on_current_device(&partials) != cudaSuccess) return LBM_ECUDA;
+    // The array's device address in the current context, looked up on every call: host code
+    // only knows a host-side stand-in for the symbol, and the address changes if the caller
+    // resets the device and a new context loads the module.
+    void* scratch = nullptr;
+    if (cudaGetSymbolAddress(&scratch, lbm::g_noalloc_partials) != cudaSuccess) {
+        (void)cudaGetLastError();  // this call's own failure, reported by the return code
+        return LBM_ECUDA;
+    }
+    double* partials = static_cast<double*>(scratch);
 
     lbm::Params P = {};
     P.Q = lattice;
@@ -141,6 +131,7 @@ extern "C" int lbm_mass_noalloc(const float* g, int lattice, const int grid[3], 
     P.nz = nz;
     P.nxy = nx * ny;
     P.N = (long long)nx * ny * nz;
+    P.walls = walls;
     P.lw_m = (float)(0.5 * courant * (1.0 + courant));
     P.lw_p = (float)(-0.5 * courant * (1.0 - courant));
     P.rho2_d = 1.0;
@@ -148,12 +139,23 @@ extern "C" int lbm_mass_noalloc(const float* g, int lattice, const int grid[3], 
     int bpl = lbm::kNoallocMaxBlocks / nz;
     if (bpl > ny) bpl = ny;
     if (bpl < 1) bpl = 1;
-    const int blocks = nz * bpl;
+    int blocks = nz * bpl;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (lattice == LBM_D2Q9)
-        lbm::mass_noalloc_kernel<9><<<blocks, lbm::kNoallocThreads, 0, s>>>(P, g, bpl, partials);
-    else
-        lbm::mass_noalloc_kernel<19><<<blocks, lbm::kNoallocThreads, 0, s>>>(P, g, bpl, partials);
-    lbm::mass_noalloc_finish<<<1, lbm::kNoallocThreads, 0, s>>>(partials, blocks, result);
-    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
+
+    // Launched through cudaLaunchKernel so that each launch's own status is checked: an error
+    // that earlier, unrelated work left on this thread is neither blamed on this call nor
+    // cleared by it.
+    const void* kernel = (lattice == LBM_D2Q9) ? (const void*)lbm::mass_noalloc_kernel<9>
+                                               : (const void*)lbm::mass_noalloc_kernel<19>;
+    void* args1[] = {&P, (void*)&g, &bpl, &partials};
+    cudaError_t e = cudaLaunchKernel(kernel, dim3(blocks), dim3(lbm::kNoallocThreads), args1, 0, s);
+    if (e == cudaSuccess) {
+        void* args2[] = {&partials, &blocks, &result};
+        e = cudaLaunchKernel((const void*)lbm::mass_noalloc_finish, dim3(1), dim3(lbm::kNoallocThreads), args2, 0, s);
+    }
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return LBM_ECUDA;
+    }
+    return LBM_OK;
 }

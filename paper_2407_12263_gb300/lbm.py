@@ -69,8 +69,8 @@ SIGNATURES = [
     ("lbm_launch_count", ctypes.c_longlong, [ctypes.c_void_p]),
     ("lbm_tau_phi", ctypes.c_double, [ctypes.c_void_p]),
     ("lbm_lattice_tables", ctypes.c_int, [ctypes.c_int, _ip, _ip, _dp]),
-    ("lbm_mass_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _ip, ctypes.c_double, ctypes.c_double,
-                                        ctypes.c_void_p, ctypes.c_void_p]),
+    ("lbm_mass_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _ip, ctypes.c_int, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
     ("lbm_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("lbm_destroy", None, [ctypes.c_void_p]),
     ("lbm_batch_default_opts", None, [ctypes.POINTER(lbm_batch_opts)]),
@@ -213,12 +213,12 @@ def lbm_lattice_tables(lattice):
     return d.value, e.reshape(lattice, 3).astype(np.int64), w
 
 
-def lbm_mass_noalloc(g_device_ptr, lattice, grid, courant, rho_ratio, result_device_ptr, stream=None) -> int:
+def lbm_mass_noalloc(g_device_ptr, lattice, grid, walls, courant, rho_ratio, result_device_ptr, stream=None) -> int:
     """Mass sums of plain FP32 device populations into a caller-owned device triple, without
     any device allocation (raw device pointers in; returns the lbm status)."""
     gr = (ctypes.c_int * 3)(*[int(v) for v in grid])
-    return int(load().lbm_mass_noalloc(ctypes.c_void_p(g_device_ptr), int(lattice), gr, courant, rho_ratio,
-                                       ctypes.c_void_p(result_device_ptr), stream))
+    return int(load().lbm_mass_noalloc(ctypes.c_void_p(g_device_ptr), int(lattice), gr, int(walls), courant,
+                                       rho_ratio, ctypes.c_void_p(result_device_ptr), stream))
 
 
 def lbm_last_error(h=None) -> str:
