@@ -455,7 +455,7 @@ def run_surrogate(lbm, torch, stream, args, world):
     # judge: 8 LBM steps; reject a mass error above 1% or phi relaxing more than 6x faster than the
     # prediction implies (trained networks measure 3.1-3.8 here from run to run: the weight
     # gradients' atomic sums make training non-deterministic at round-off)
-    rep = lbm.lbm_surrogate_jump(jumper.h, net, f, ms, k, 8, 1e-2, 6.0)
+    rep = lbm.lbm_surrogate_jump(jumper.h, net, f, ms, k, 8, 1e-2, 6.0, 1.0)
     t_jump = rep["seconds"]
     xt = coarse(truth, f)
     # the prediction itself, for its error (the jumper now holds it advanced by the judge's steps)

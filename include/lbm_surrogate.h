@@ -81,7 +81,12 @@ typedef struct {
                            0: it holds the LBM's own k steps from the starting state */
     double mass_error;  /* |sum phi of the prediction - sum phi before| / sum phi before */
     double relax_ratio; /* how fast the LBM moves phi right after the restart, relative to the
-                           rate the prediction implies (1 = consistent) */
+                           rate the prediction implies (1 = consistent); 0 if not judged */
+    double interface_shift; /* mean displacement of the interface from the starting state to the
+                               prediction, in cells: f sum |phi_pred - phi_start| / sum |grad phi_start|
+                               over the coarse cells (central differences in coarse cells) */
+    double interface_limit; /* the largest shift accepted: interface_tol * k * the largest speed
+                               |u| of the starting and the predicted coarse fields */
     double seconds_surrogate; /* host wall time of the jump, judge included */
 } lbm_jump_report;
 
@@ -89,7 +94,11 @@ typedef struct {
  * Fast-forward k steps with the surrogate, judged by the LBM:
  *   1. coarsen the state by `factor`, normalise with mean_std (5 means, then 5 stds), predict,
  *      denormalise;
- *   2. reject if the prediction's sum phi is off by more than mass_tol (relative);
+ *   2. reject if the prediction's sum phi is off by more than mass_tol (relative), or if its
+ *      interface moved farther than the flow can carry it: interface_shift > interface_limit
+ *      (see lbm_jump_report). The phi = 1/2 surface of the conservative phase field moves with
+ *      the fluid, because the sharpening flux vanishes on the equilibrium profile (Sec. 2.3), so
+ *      in k steps no part of it moves farther than max |u| k; interface_tol = 1 is that bound;
  *   3. restart the lattice from the prediction with sum phi held exactly;
  *   4. run judge_steps LBM steps and compare how far phi moves per step with the rate the
  *      prediction implies (|phi_after - phi_restart| / judge_steps against
@@ -103,7 +112,7 @@ typedef struct {
  * it until lbm_destroy, so later jumps allocate nothing.
  */
 int lbm_surrogate_jump(lbm_ctx *ctx, lbm_net *net, int factor, const float mean_std[10], int k, int judge_steps,
-                       double mass_tol, double relax_tol, lbm_jump_report *report);
+                       double mass_tol, double relax_tol, double interface_tol, lbm_jump_report *report);
 
 /* Allocate the workspace of lbm_surrogate_jump for this factor now (LBM_ENOMEM if it does not
  * fit), so that the jumps themselves allocate nothing. Synchronous. */

@@ -169,6 +169,7 @@ class Oracle:
         if lib.oracle_set_walls(self._h, int(walls)) != 0:
             raise ValueError(f"invalid wall mask {walls}")
         self.tau_phi = float(lib.oracle_tau_phi(self._h))
+        self.walls = int(walls)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -216,6 +217,15 @@ class Oracle:
         f = np.ascontiguousarray(f, dtype=np.float64).reshape((self.Q,) + self.shape)
         g = np.ascontiguousarray(g, dtype=np.float64).reshape((self.Q,) + self.shape)
         _load().oracle_set_pops(self._h, _ptr(f), _ptr(g))
+
+    def restart_from_coarse(self, coarse, factor, p0=CS2):
+        """Replace the state by the restart from coarse fields (the surrogate's hand-over to the
+        lattice; no counterpart in the paper). See ``oracle.restart``: trilinear upsampling of
+        (phi, u, v, w, p), phi clamped to [-1, 1.5], the initial-state construction of reading R9
+        (``init_phi`` with the pressure field), then sum phi set back to its value before."""
+        from . import restart as _restart
+
+        _restart.restart_from_coarse(self, coarse, factor, p0)
 
     def macroscopic_cell(self, fbar, g, fd_grad=None):
         out = np.zeros(21)

@@ -373,13 +373,14 @@ int lbm_restart_from_coarse(lbm_ctx* c, int f, const float* coarse, double p0) {
 
 namespace {
 
-// Carves the jump's buffers out of the handle's workspace, growing it if it is too small.
-int jump_workspace(lbm_ctx* c, int f, void** backup, float* fields[4]) {
+// Carves the jump's buffers out of the handle's workspace, growing it if it is too small: a
+// backup state, four coarse field arrays and the judge's four FP64 measures.
+int jump_workspace(lbm_ctx* c, int f, void** backup, float* fields[4], double** measures) {
     const long long nc = (long long)(c->P.nx / f) * (c->P.ny / f) * (c->P.nz / f);
     const size_t align = 256;
     const size_t sb = (c->fg_bytes + align - 1) / align * align;
     const size_t fb = ((size_t)5 * nc * sizeof(float) + align - 1) / align * align;
-    const size_t need = sb + 4 * fb;
+    const size_t need = sb + 4 * fb + align;
     if (c->jump_ws_bytes < need) {
         cudaFree(c->jump_ws);
         c->jump_ws = nullptr;
@@ -391,6 +392,7 @@ int jump_workspace(lbm_ctx* c, int f, void** backup, float* fields[4]) {
     char* base = static_cast<char*>(c->jump_ws);
     *backup = base;
     for (int i = 0; i < 4; ++i) fields[i] = reinterpret_cast<float*>(base + sb + i * fb);
+    *measures = reinterpret_cast<double*>(base + sb + 4 * fb);
     return LBM_OK;
 }
 
@@ -403,14 +405,16 @@ int lbm_surrogate_reserve(lbm_ctx* c, int f) {
         return lbm::ctx_error(c, LBM_EINVAL, "factor must divide nx, ny and nz");
     void* backup;
     float* fields[4];
-    return jump_workspace(c, f, &backup, fields);
+    double* measures;
+    return jump_workspace(c, f, &backup, fields, &measures);
 }
 
 int lbm_surrogate_jump(lbm_ctx* c, lbm_net* n, int f, const float mean_std[10], int k, int judge_steps, double mass_tol,
-                       double relax_tol, lbm_jump_report* rep) {
+                       double relax_tol, double interface_tol, lbm_jump_report* rep) {
     int rc = lbm::ctx_check(c);
     if (rc) return rc;
-    if (!n || !mean_std || !rep || k < 1 || judge_steps < 1 || !(mass_tol >= 0) || !(relax_tol > 0))
+    if (!n || !mean_std || !rep || k < 1 || judge_steps < 1 || !(mass_tol >= 0) || !(relax_tol > 0) ||
+        !(interface_tol >= 0) || std::isnan(relax_tol))
         return lbm::ctx_error(c, LBM_EINVAL, "need a network, mean_std, a report, k >= 1, judge_steps >= 1 and tolerances");
     if (f < 1 || c->P.nx % f || c->P.ny % f || c->P.nz % f)
         return lbm::ctx_error(c, LBM_EINVAL, "factor must divide nx, ny and nz");
@@ -421,7 +425,8 @@ int lbm_surrogate_jump(lbm_ctx* c, lbm_net* n, int f, const float mean_std[10], 
     const long long nc = (long long)grid_c[0] * grid_c[1] * grid_c[2];
     void* backup;
     float* fields[4];
-    if ((rc = jump_workspace(c, f, &backup, fields))) return rc;
+    double* measures;
+    if ((rc = jump_workspace(c, f, &backup, fields, &measures))) return rc;
     float *in = fields[0], *xin = fields[1], *yout = fields[2], *pred = fields[3];
     auto cu = [&](cudaError_t e) { return e == cudaSuccess ? LBM_OK : lbm::ctx_error(c, LBM_ECUDA, cudaGetErrorString(e)); };
     const int saved_cur = c->cur;
@@ -437,18 +442,27 @@ int lbm_surrogate_jump(lbm_ctx* c, lbm_net* n, int f, const float mean_std[10], 
     if ((rc = cu(lbm::launch_normalize(yout, pred, nc, mean_std, -1, n->stream)))) return rc;
     if ((rc = cu(cudaStreamSynchronize(n->stream)))) return rc;
     if ((rc = check_tc(n))) return lbm::ctx_error(c, rc, lbm_net_last_error(n));
-    std::vector<float> h_in((size_t)nc), h_pred((size_t)nc);
-    if ((rc = cu(cudaMemcpy(h_in.data(), in, (size_t)nc * sizeof(float), cudaMemcpyDeviceToHost)))) return rc;
-    if ((rc = cu(cudaMemcpy(h_pred.data(), pred, (size_t)nc * sizeof(float), cudaMemcpyDeviceToHost)))) return rc;
-    // 2. mass of the prediction
+    // 2. mass and interface position of the prediction, measured on the coarse grid
+    if ((rc = cu(cudaMemsetAsync(measures, 0, 4 * sizeof(double), c->stream)))) return rc;
+    if ((rc = cu(lbm::launch_jump_measures(in, pred, grid_c[0], grid_c[1], grid_c[2], c->P.walls, measures, c->stream))))
+        return rc;
+    double m[4];
+    if ((rc = cu(cudaMemcpyAsync(m, measures, sizeof m, cudaMemcpyDeviceToHost, c->stream)))) return rc;
+    if ((rc = cu(cudaStreamSynchronize(c->stream)))) return rc;
+    c->launches += 1;
     const double mass_before = (double)m_before / 1073741824.0;
-    double mass_pred = 0.0, jump = 0.0;
-    for (long long i = 0; i < nc; ++i) {
-        mass_pred += (double)h_pred[i] * f * f * f;
-        jump += std::fabs((double)h_pred[i] - (double)h_in[i]);
-    }
+    const double mass_pred = m[0] * f * f * f, jump = m[1];
     rep->mass_error = std::fabs(mass_pred - mass_before) / std::fabs(mass_before);
-    bool accept = rep->mass_error <= mass_tol;
+    // Mean displacement of the interface, in fine cells: a profile moved by d along its normal
+    // changes phi by |grad phi| d, so int |phi_pred - phi_start| dV = d int |grad phi| dV. On the
+    // coarse grid both integrals are sums over coarse cells (f^3 fine cells each; the coarse
+    // gradient is f times the fine one), so d = f sum |dphi| / sum |grad_c phi|.
+    rep->interface_shift = m[2] > 0 ? f * jump / m[2] : (jump > 0 ? INFINITY : 0.0);
+    // Kinematic bound: the phi = 1/2 surface is carried by the flow (the sharpening flux of the
+    // conservative phase-field equation vanishes on the equilibrium profile), so in k steps no
+    // part of it moves farther than the largest speed times k.
+    rep->interface_limit = interface_tol * std::sqrt(m[3]) * k;
+    bool accept = rep->mass_error <= mass_tol && rep->interface_shift <= rep->interface_limit;
     // 3-4. restart and judge
     if (accept) {
         if ((rc = lbm_restart_from_coarse(c, f, pred, saved_P.w0d / 3.0))) return rc;

@@ -65,6 +65,15 @@ cudaError_t launch_restart(const Params& P, const float* coarse, int factor, dou
                            cudaStream_t s);
 // Adds delta units (2^-30) of phi to the state, spread over the cells so that it sums exactly.
 cudaError_t launch_adjust_phi(const Params& P, void* fg, long long delta, cudaStream_t s);
+// What the judge of a jump measures on the coarse grid [5][ncz][ncy][ncx] of the starting fields
+// `start` and of the prediction `pred`, accumulated into out[4] (zeroed by the caller):
+//   out[0] += sum of the predicted phi;
+//   out[1] += sum |phi_pred - phi_start|;
+//   out[2] += sum |grad phi_start|, central differences in coarse cells (periodic, or the cell
+//             itself beyond a wall, bit 0 x, bit 1 y, bit 2 z of walls);
+//   out[3]  = max(out[3], largest |u|^2 of start and prediction) (as non-negative double bits).
+cudaError_t launch_jump_measures(const float* start, const float* pred, int ncx, int ncy, int ncz, int walls, double* out,
+                                 cudaStream_t s);
 // (x - mean[c]) / std[c] per channel of [5][n] (dir = +1) or x std[c] + mean[c] (dir = -1).
 cudaError_t launch_normalize(const float* x, float* y, long long n, const float* mean_std, int dir, cudaStream_t s);
 

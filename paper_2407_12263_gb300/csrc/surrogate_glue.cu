@@ -308,6 +308,82 @@ cudaError_t launch_adjust_phi(const Params& P, void* fg, long long delta, cudaSt
     return cudaGetLastError();
 }
 
+__device__ __forceinline__ double warp_sum_jm(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max_jm(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+constexpr int kJumpThreads = 256;
+
+__global__ void __launch_bounds__(kJumpThreads)
+jump_measures_kernel(const float* __restrict__ start, const float* __restrict__ pred, int ncx, int ncy, int ncz,
+                     int walls, double* __restrict__ out) {
+    const long long nc = (long long)ncx * ncy * ncz;
+    double acc[3] = {0.0, 0.0, 0.0}, umax = 0.0;
+    for (long long l = (long long)blockIdx.x * kJumpThreads + threadIdx.x; l < nc; l += (long long)gridDim.x * kJumpThreads) {
+        const int x = (int)(l % ncx), y = (int)((l / ncx) % ncy), z = (int)(l / ((long long)ncx * ncy));
+        auto idx = [&](int xx, int yy, int zz) { return ((long long)zz * ncy + yy) * ncx + xx; };
+        auto nb = [](int i, int d, int n, bool wall) { return wall ? min(max(i + d, 0), n - 1) : (i + d + n) % n; };
+        const float ps = __ldg(start + l), pp = __ldg(pred + l);
+        acc[0] += (double)pp;
+        acc[1] += fabs((double)pp - (double)ps);
+        const double gx = 0.5 * ((double)__ldg(start + idx(nb(x, 1, ncx, walls & 1), y, z)) -
+                                 (double)__ldg(start + idx(nb(x, -1, ncx, walls & 1), y, z)));
+        const double gy = 0.5 * ((double)__ldg(start + idx(x, nb(y, 1, ncy, walls & 2), z)) -
+                                 (double)__ldg(start + idx(x, nb(y, -1, ncy, walls & 2), z)));
+        const double gz = 0.5 * ((double)__ldg(start + idx(x, y, nb(z, 1, ncz, walls & 4))) -
+                                 (double)__ldg(start + idx(x, y, nb(z, -1, ncz, walls & 4))));
+        acc[2] += sqrt(gx * gx + gy * gy + gz * gz);
+        double u2s = 0.0, u2p = 0.0;
+#pragma unroll
+        for (int a = 1; a <= 3; ++a) {
+            const double us = __ldg(start + a * nc + l), up = __ldg(pred + a * nc + l);
+            u2s += us * us;
+            u2p += up * up;
+        }
+        umax = fmax(umax, fmax(u2s, u2p));
+    }
+    __shared__ double red[4][kJumpThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc[k] = warp_sum_jm(acc[k]);
+    umax = warp_max_jm(umax);
+    if (lane == 0) {
+        for (int k = 0; k < 3; ++k) red[k][warp] = acc[k];
+        red[3][warp] = umax;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        double v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = (lane < kJumpThreads / 32) ? red[k][lane] : 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) v[k] = warp_sum_jm(v[k]);
+        v[3] = warp_max_jm(v[3]);
+        if (lane == 0) {
+            for (int k = 0; k < 3; ++k) atomicAdd(out + k, v[k]);
+            // non-negative doubles order like their bit patterns
+            atomicMax(reinterpret_cast<unsigned long long*>(out + 3), (unsigned long long)__double_as_longlong(v[3]));
+        }
+    }
+}
+
+cudaError_t launch_jump_measures(const float* start, const float* pred, int ncx, int ncy, int ncz, int walls, double* out,
+                                 cudaStream_t s) {
+    const long long nc = (long long)ncx * ncy * ncz;
+    const long long blocks = (nc + kJumpThreads - 1) / kJumpThreads;
+    jump_measures_kernel<<<(unsigned)(blocks < 1216 ? blocks : 1216), kJumpThreads, 0, s>>>(start, pred, ncx, ncy, ncz,
+                                                                                           walls, out);
+    return cudaGetLastError();
+}
+
 __global__ void normalize_kernel(const float* __restrict__ x, float* __restrict__ y, long long n, float m0, float m1,
                                  float m2, float m3, float m4, float s0, float s1, float s2, float s3, float s4, int dir) {
     const float mean[5] = {m0, m1, m2, m3, m4}, sd[5] = {s0, s1, s2, s3, s4};

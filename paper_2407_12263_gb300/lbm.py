@@ -44,6 +44,7 @@ class lbm_batch_opts(ctypes.Structure):
 
 class lbm_jump_report(ctypes.Structure):
     _fields_ = [("accepted", ctypes.c_int), ("mass_error", ctypes.c_double), ("relax_ratio", ctypes.c_double),
+                ("interface_shift", ctypes.c_double), ("interface_limit", ctypes.c_double),
                 ("seconds_surrogate", ctypes.c_double)]
 
 
@@ -101,7 +102,7 @@ SIGNATURES = [
     ("lbm_restart_from_coarse", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_double]),
     ("lbm_surrogate_jump", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
                                           ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
-                                          ctypes.POINTER(lbm_jump_report)]),
+                                          ctypes.c_double, ctypes.POINTER(lbm_jump_report)]),
     ("lbm_surrogate_reserve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
 ]
 
@@ -515,10 +516,11 @@ def lbm_surrogate_reserve(h, factor):
     _check(h, load().lbm_surrogate_reserve(h, int(factor)))
 
 
-def lbm_surrogate_jump(h, net, factor, mean_std, k, judge_steps, mass_tol, relax_tol):
+def lbm_surrogate_jump(h, net, factor, mean_std, k, judge_steps, mass_tol, relax_tol, interface_tol=1.0):
     ms = (ctypes.c_float * 10)(*[float(v) for v in mean_std])
     rep = lbm_jump_report()
     _check(h, load().lbm_surrogate_jump(h, net.n, int(factor), ms, int(k), int(judge_steps), float(mass_tol),
-                                        float(relax_tol), ctypes.byref(rep)))
+                                        float(relax_tol), float(interface_tol), ctypes.byref(rep)))
     return {"accepted": bool(rep.accepted), "mass_error": rep.mass_error, "relax_ratio": rep.relax_ratio,
+            "interface_shift": rep.interface_shift, "interface_limit": rep.interface_limit,
             "seconds": rep.seconds_surrogate}

@@ -3,9 +3,10 @@
 * forward pass and gradients against the FP64 restatement in oracle/cnn.py (FP32 activations:
   relative 1e-5 of each array's scale; FP16 activations: 1e-2);
 * one Adam step against its formula;
-* coarse fields against block means of lbm_moments; a restart holds sum phi exactly;
-* the judge: a wild prediction is rejected and the state is then the LBM's own k steps, bit for
-  bit;
+* coarse fields against block means of lbm_moments; a restart holds sum phi exactly, and its
+  populations match the oracle's restart (oracle/restart.py) element by element;
+* the judge: a wild prediction, and a prediction whose interface moved farther than the flow can
+  carry it (mass exact), are rejected and the state is then the LBM's own k steps, bit for bit;
 * what the network gains: trained on seeded Taylor-Green trajectories of this solver, it
   predicts a held-out trajectory k steps ahead far better than persistence (the state itself),
   and the judged jump is accepted with sum phi unchanged.
@@ -13,7 +14,8 @@
 import numpy as np
 import pytest
 
-from oracle import cnn
+import oracle as O
+from oracle import cnn, restart
 from paper_2407_12263_gb300 import build as cuda_build
 from paper_2407_12263_gb300 import inputs as I
 from paper_2407_12263_gb300 import lbm
@@ -167,6 +169,59 @@ def test_restart_holds_sum_phi_exactly():
     assert g.mass()[0] == s0
 
 
+# FP32: each stored value within a few FP32 roundings of the FP64 value (populations of order
+# t_i, the upsampling, gradient and equilibria evaluated in FP32); the rest populations are
+# rebuilt from the zeroth moments minus 18 stored values. FP16: half a unit in the last place of
+# the scaled deviations (f: |dev| < 2^-6, scaled by 2^12; g: |dev| < 2^-4, scaled by 2^10),
+# 18 of them in the rest populations.
+RESTART_TOL = {lbm.LBM_STORAGE_FP32: dict(f=2e-7, g=2e-7, f0=5e-7, g0=5e-7),
+               lbm.LBM_STORAGE_FP16: dict(f=4e-6, g=1.6e-5, f0=8e-5, g0=3e-4)}
+
+
+@pytest.mark.parametrize("Q,grid,factor,walls,storage", [
+    (19, (24, 16, 20), 4, 0, lbm.LBM_STORAGE_FP32),
+    (19, (18, 14, 12), 2, 7, lbm.LBM_STORAGE_FP32),
+    (19, (16, 16, 16), 2, 0, lbm.LBM_STORAGE_FP16),
+    (9, (20, 14, 1), 1, 3, lbm.LBM_STORAGE_FP32),
+])
+def test_restart_populations_match_oracle(Q, grid, factor, walls, storage):
+    """lbm_restart_from_coarse against the oracle's restart on the same coarse fields: block
+    means of seeded droplets, velocity and pressure, with one coarse phi far above the range the
+    lattice accepts (the upsampled values are clamped to 1.5). Density ratio 3."""
+    params = dict(tau_f=0.7, tau_g=0.8, M=0.02, xi=4.0, sigma=2e-3, rho_ratio=3.0, mu_ratio=2.0)
+    phi0 = I.multi_droplet_phi(grid, seed=101, count=2, r_range=(3.0, 5.0), xi=4.0)
+    u0 = I.smooth_velocity(grid, seed=102, amplitude=0.02)
+    if Q == 9:
+        u0[2] = 0
+    nx, ny, nz = grid
+    zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    p = 1.0 / 3.0 + 1e-3 * np.cos(2 * np.pi * (xx + 0.5) / nx) * np.sin(2 * np.pi * (yy + 0.5) / ny)
+    f = factor
+    bm = lambda a: a.reshape(nz // f, f, ny // f, f, nx // f, f).mean(axis=(1, 3, 5))  # noqa: E731
+    coarse = np.stack([bm(phi0), bm(u0[0]), bm(u0[1]), bm(u0[2]), bm(p)]).astype(np.float32)
+    k = np.unravel_index(np.argmax(coarse[0]), coarse[0].shape)
+    coarse[0][k] = 3.0
+    gpu = lbm.Lattice(grid, Q, walls=walls, storage=storage, **params)
+    gpu.init_phi(phi0, u0)
+    ref = O.Oracle(Q, grid, walls=walls, **params)
+    ref.init_phi(phi0, u0)
+    s0 = gpu.mass()[0]
+    c_dev = _dev(coarse)
+    torch.cuda.synchronize()
+    lbm.lbm_restart_from_coarse(gpu.h, f, c_dev.data_ptr(), 1.0 / 3.0)
+    ref.restart_from_coarse(coarse.astype(np.float64), f, 1.0 / 3.0)
+    assert gpu.mass()[0] == s0
+    fg, gg = gpu.get_pops()
+    fo, go = ref.get_pops()
+    tol = RESTART_TOL[storage]
+    np.testing.assert_allclose(fg[1:], fo[1:], rtol=0, atol=tol["f"])
+    np.testing.assert_allclose(gg[1:], go[1:], rtol=0, atol=tol["g"])
+    np.testing.assert_allclose(fg[0], fo[0], rtol=0, atol=tol["f0"])
+    np.testing.assert_allclose(gg[0], go[0], rtol=0, atol=tol["g0"])
+    # the clamp was exercised
+    assert restart.upsample_fields(coarse.astype(np.float64), f, walls)[0].max() == 1.5
+
+
 def test_wild_prediction_is_rejected_and_the_lbm_takes_over():
     c = _tgv_case(16, 0.04, 4.0, 20.0)
     g, twin = _tgv_lattice(c), _tgv_lattice(c)
@@ -184,6 +239,65 @@ def test_wild_prediction_is_rejected_and_the_lbm_takes_over():
         fb, gb = twin.get_pops()
         np.testing.assert_array_equal(fa, fb)
         np.testing.assert_array_equal(ga, gb)
+
+
+def _shift_net():
+    """A network (FP32 activations) whose prediction is the input with phi moved one coarse cell
+    along +x and u, v, w, p unchanged: layer 1 splits phi into relu(phi) and relu(-phi), layers 2
+    and 3 pass both on, layer 4 returns shift(phi) - phi (tap 9 dz + 3 dy + dx reads the input at
+    offset (dz - 1, dy - 1, dx - 1); tap 12 is offset -1 in x, tap 13 the centre)."""
+    net = _net(False, 0)
+    p = np.zeros(net.param_count, dtype=np.float32)
+    off = 0
+    layers = []
+    for cin, cout in zip(CHANS[:-1], CHANS[1:]):
+        W = p[off:off + cout * cin * 27].reshape(cout, cin, 27)
+        layers.append(W)
+        off += cout * cin * 27 + cout
+    layers[0][0, 0, 13], layers[0][1, 0, 13] = 1.0, -1.0
+    for W in layers[1:3]:
+        W[0, 0, 13] = W[1, 1, 13] = 1.0
+    layers[3][0, 0, 12], layers[3][0, 1, 12] = 1.0, -1.0
+    layers[3][0, 0, 13], layers[3][0, 1, 13] = -1.0, 1.0
+    net.set_params(p)
+    return net
+
+
+def test_shifted_interface_is_rejected_and_the_lbm_takes_over():
+    """A prediction whose droplet is moved two cells (one coarse cell) with its mass exact: the
+    mean interface displacement exceeds the kinematic bound max|u| k, so the jump is rejected
+    before any restart, and the state is then the LBM's own k steps, bit for bit. The unshifted
+    prediction (persistence) passes that test (shift 0) and is judged by the LBM."""
+    c = _tgv_case(16, 0.04, 4.0, 20.0)
+    g, twin = _tgv_lattice(c), _tgv_lattice(c)
+    g.step(8)
+    twin.step(8)
+    ms = [0.5, 0, 0, 0, 1 / 3, 0.5, 0.04, 0.04, 0.04, 1e-4]
+    k = 16
+    net = _shift_net()
+    x0 = _coarse(g, 2)
+    xin = ((x0 - torch.tensor(ms[:5], device="cuda")[:, None, None, None])
+           / torch.tensor(ms[5:], device="cuda")[:, None, None, None]).contiguous()
+    y = torch.empty_like(xin)
+    net.forward(xin.data_ptr(), y.data_ptr(), 1, (8, 8, 8))
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(y[0].cpu().numpy(), np.roll(xin[0].cpu().numpy(), 1, axis=2), rtol=0, atol=1e-5)
+    np.testing.assert_allclose(y[1:].cpu().numpy(), xin[1:].cpu().numpy(), rtol=0, atol=1e-6)
+    rep = lbm.lbm_surrogate_jump(g.h, net, 2, ms, k, 4, 1e-3, 1e9, 1.0)
+    assert rep["mass_error"] < 1e-5
+    # a sphere moved 2 cells along x moves its surface by 2 |n_x| along the normal: 1 cell on average
+    assert 0.85 < rep["interface_shift"] < 1.15, rep
+    assert rep["interface_limit"] == pytest.approx(float(x0[1:4].pow(2).sum(0).sqrt().max()) * k, rel=1e-2)
+    assert rep["interface_shift"] > rep["interface_limit"]
+    assert not rep["accepted"] and rep["relax_ratio"] == 0.0
+    twin.step(k)
+    fa, ga = g.get_pops()
+    fb, gb = twin.get_pops()
+    np.testing.assert_array_equal(fa, fb)
+    np.testing.assert_array_equal(ga, gb)
+    net.set_params(np.zeros(net.param_count, dtype=np.float32))  # persistence
+    rep = lbm.lbm_surrogate_jump(g.h, net, 2, ms, k, 4, 1e-3, 1e9, 1.0)
+    assert rep["interface_shift"] == 0.0 and rep["relax_ratio"] > 0.0
 
 
 def test_trained_surrogate_beats_persistence_and_is_accepted():
