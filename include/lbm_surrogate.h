@@ -61,6 +61,14 @@ int lbm_net_gradients(lbm_net *net, const float *x, const float *target, int bat
 /* One Adam step with learning rate lr from the gradients of the last lbm_net_gradients. */
 int lbm_net_adam(lbm_net *net, float lr);
 
+/* Every wait of the tensor-core kernels polls its mbarrier a bounded number of times (2^26)
+ * and gives up after that. on = 1 makes every wait for a step's MMAs give up at once instead:
+ * the kernel then stops issuing, waits (with the full bound) for the MMAs it issued, frees its
+ * tensor memory and returns, and the next synchronising call on the network returns
+ * LBM_ETIMEOUT once; the network stays usable. on = 0 restores the normal waits. This exists to
+ * test the timeout path without a hung GPU; the paper has no counterpart. */
+int lbm_net_fail_waits(lbm_net *net, int on);
+
 const char *lbm_net_last_error(const lbm_net *net);
 void lbm_net_destroy(lbm_net *net);
 

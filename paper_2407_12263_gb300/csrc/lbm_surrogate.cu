@@ -30,6 +30,7 @@ struct lbm_net {
     float* wt;                        // adjoint weights of one layer
     __half* wimg;                     // FP16 tensor-core weight image of one 32 -> 32 layer
     int* tc_err;                      // set by the tensor-core kernel if a wait timed out
+    long long tc_spin;                // polls of an mbarrier before a tensor-core wait for a step gives up
     int adam_step;
     float loss_w[kFieldChannels];     // per-channel weights of the loss
     // workspace for (batch, voxels)
@@ -140,10 +141,15 @@ int check_grid(lbm_net* n, int batch, const int grid[3]) {
 bool on_tensor_cores(const lbm_net* n) { return n->fp16 != 0; }
 
 // A timeout of the tensor-core kernel, read at a point where the stream has been synchronised.
+// The flag is cleared once reported, so the network stays usable: the kernel that timed out has
+// waited for its MMAs in flight and freed its tensor memory before it returned.
 int check_tc(lbm_net* n) {
     int flag = 0;
     LBM_NCUDA(n, cudaMemcpy(&flag, n->tc_err, sizeof flag, cudaMemcpyDeviceToHost));
-    if (flag) return nerr(n, LBM_ETIMEOUT, "a tensor-core convolution timed out waiting for its MMAs");
+    if (flag) {
+        LBM_NCUDA(n, cudaMemset(n->tc_err, 0, sizeof(int)));
+        return nerr(n, LBM_ETIMEOUT, "a tensor-core convolution timed out waiting for its MMAs");
+    }
     return LBM_OK;
 }
 
@@ -161,7 +167,8 @@ int forward_keep(lbm_net* n, const float* x, int batch, const int grid[3]) {
         if (on_tensor_cores(n)) {
             LBM_NCUDA(n, lbm::net::weight_image(n->params + n->w_off[l], n->cout[l], n->cin[l], n->wimg, n->stream));
             LBM_NCUDA(n, lbm::net::conv32_tc(in, 1, n->cin[l], 1.0f, n->wimg, n->params + n->b_off[l], out, last ? 0 : 1,
-                                             n->cout[l], last ? 0 : 1, batch, D, H, W, n->tc_err, n->stream));
+                                             n->cout[l], last ? 0 : 1, batch, D, H, W, n->tc_spin, n->tc_err,
+                                             n->stream));
         } else {
             LBM_NCUDA(n, lbm::net::conv_forward(in, n->fp16, n->cin[l], n->params + n->w_off[l], n->params + n->b_off[l],
                                                 out, last ? 0 : n->fp16, n->cout[l], last ? 0 : 1, batch, D, H, W, n->stream));
@@ -182,6 +189,7 @@ int lbm_net_create(lbm_net** out, int activations_fp16, unsigned long long seed,
     if (!n) return nerr(nullptr, LBM_ENOMEM, "host allocation failed");
     std::snprintf(n->err, sizeof n->err, "no error");
     n->fp16 = activations_fp16 ? 1 : 0;
+    n->tc_spin = lbm::net::kTcWaitPolls;
     for (int c = 0; c < kFieldChannels; ++c) n->loss_w[c] = 1.f;
     auto fail = [&](int code) {
         std::snprintf(g_net_error, sizeof g_net_error, "%s", n->err);
@@ -281,7 +289,8 @@ int lbm_net_gradients(lbm_net* n, const float* x, const float* target, int batch
         const void* h_in = (l == 0) ? n->x_t : n->h[l - 1];
         if (on_tensor_cores(n))
             LBM_NCUDA(n, lbm::net::wgrad32_tc(g, n->cout[l], grad_scale, h_in, n->fp16, n->cin[l], n->grads + n->w_off[l],
-                                              n->grads + n->b_off[l], batch, D, H, W, n->tc_err, n->stream));
+                                              n->grads + n->b_off[l], batch, D, H, W, n->tc_spin, n->tc_err,
+                                              n->stream));
         else
             LBM_NCUDA(n, lbm::net::conv_wgrad(g, n->cout[l], h_in, n->fp16, n->cin[l], n->grads + n->w_off[l],
                                               n->grads + n->b_off[l], batch, D, H, W, n->stream));
@@ -291,7 +300,7 @@ int lbm_net_gradients(lbm_net* n, const float* x, const float* target, int batch
             LBM_NCUDA(n, lbm::net::weight_image(n->wt, n->cin[l], n->cout[l], n->wimg, n->stream));
             // the loss gradient is 2 diff / (elements): scale it back to order one before FP16
             LBM_NCUDA(n, lbm::net::conv32_tc(g, 0, n->cout[l], grad_scale, n->wimg, nullptr, other, 0, n->cin[l], 0, batch,
-                                             D, H, W, n->tc_err, n->stream));
+                                             D, H, W, n->tc_spin, n->tc_err, n->stream));
         } else {
             LBM_NCUDA(n, lbm::net::conv_forward(g, 0, n->cout[l], n->wt, nullptr, other, 0, n->cin[l], 0, batch, D, H, W,
                                                 n->stream));
@@ -328,6 +337,12 @@ int lbm_net_adam(lbm_net* n, float lr) {
     if (!(lr > 0.f)) return nerr(n, LBM_EINVAL, "lr must be > 0");
     n->adam_step += 1;
     LBM_NCUDA(n, lbm::net::adam(n->params, n->grads, n->m, n->v, n->n_params, lr, n->adam_step, n->stream));
+    return LBM_OK;
+}
+
+int lbm_net_fail_waits(lbm_net* n, int on) {
+    if (!n) return nerr(nullptr, LBM_EINVAL, "null network");
+    n->tc_spin = on ? 0 : lbm::net::kTcWaitPolls;
     return LBM_OK;
 }
 

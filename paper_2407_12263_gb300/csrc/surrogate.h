@@ -38,16 +38,21 @@ cudaError_t adam(float* p, const float* g, float* m, float* v, long long n, floa
 // wimg is the layer's weight image (weight_image, weight_image_bytes() bytes); inputs FP16 or
 // FP32, multiplied by in_scale (a power of two) before they are rounded to FP16 and the sums
 // divided by it again (so small gradients keep their bits); outputs FP16 with relu or FP32
-// without. *err is set to 1 if a wait for the tensor cores timed out.
+// without. *err is set to 1 if a wait for the tensor cores timed out: each wait for a step's
+// MMAs polls its mbarrier at most `spin` times, kTcWaitPolls normally or 0 (give up at once,
+// the same in every thread: a test of the timeout path); the last wait for MMAs still in
+// flight, before the tensor memory is freed, always allows kTcWaitPolls.
 // Layers with cin, cout <= 32 (the unused channels are zero-padded).
+constexpr long long kTcWaitPolls = 1ll << 26;
 size_t weight_image_bytes();
 cudaError_t weight_image(const float* W, int cout, int cin, __half* img, cudaStream_t s);
 cudaError_t conv32_tc(const void* in, int in_fp16, int cin, float in_scale, const __half* wimg, const float* bias, void* out,
-                      int out_fp16, int cout, int relu, int batch, int D, int H, int Wd, int* err, cudaStream_t s);
+                      int out_fp16, int cout, int relu, int batch, int D, int H, int Wd, long long spin, int* err,
+                      cudaStream_t s);
 // gW [cout][cin][27] += correlation of g [B][cout] with h [B][cin] on the tensor cores (g scaled by
 // g_scale, a power of two, before FP16 rounding and unscaled after); gb [cout] += sum of g.
 cudaError_t wgrad32_tc(const float* g, int cout, float g_scale, const void* h, int h_fp16, int cin, float* gW, float* gb,
-                       int batch, int D, int H, int Wd, int* err, cudaStream_t s);
+                       int batch, int D, int H, int Wd, long long spin, int* err, cudaStream_t s);
 
 }  // namespace net
 

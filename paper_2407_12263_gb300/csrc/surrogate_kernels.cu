@@ -341,7 +341,7 @@ constexpr int kIssuer = CONV_THREADS - 32;
 constexpr uint32_t W_TAP = 2048;             // bytes of one tap's 32 x 32 FP16 weights
 constexpr uint32_t W_BYTES = 27 * W_TAP;
 constexpr uint32_t SMEM = 4 * SLOT_BYTES + W_BYTES;  // 101,376: two CTAs per SM
-constexpr long long kSpin = 1ll << 26;        // polls of an mbarrier before giving up
+constexpr long long kSpin = kTcWaitPolls;     // polls of an mbarrier before giving up, at most
 
 // offset of weight (out n, in k) of a tap inside its 2 KB block: core matrix (k/8, n/8)
 __host__ __device__ inline uint32_t w_off(int n, int k) { return (k / 8) * 512 + (n / 8) * 128 + (n % 8) * 16 + (k % 8) * 2; }
@@ -377,8 +377,10 @@ __global__ void weight_image_kernel(const float* __restrict__ W, int cout, int c
     *reinterpret_cast<__half*>(reinterpret_cast<unsigned char*>(img) + tap * W_TAP + w_off(n, k)) = __float2half_rn(w);
 }
 
-__device__ inline bool wait_parity(uint32_t mbar, uint32_t parity) {
-    for (long long it = 0; it < kSpin; ++it) {
+// Polls mbarrier `mbar` until phase `parity` completes, at most `limit` times (limit 0 gives up
+// at once without polling).
+__device__ inline bool wait_parity(uint32_t mbar, uint32_t parity, long long limit) {
+    for (long long it = 0; it < limit; ++it) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred P1;\n\tmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\tselp.b32 %0, 1, 0, P1;\n\t}\n"
@@ -501,7 +503,7 @@ template <typename TIN, int MODE, typename TOUT>
 __global__ void __launch_bounds__(CONV_THREADS, 2)
 conv32_tc_kernel(const TIN* __restrict__ in, int cin, float in_scale, const __half* __restrict__ wimg,
                  const float* __restrict__ bias, TOUT* __restrict__ out, int cout, int D, int H, int Wd, int tiles_x,
-                 int tiles_y, int zchunk, int n_chunks, int n_columns, int vec_in, int* __restrict__ err) {
+                 int tiles_y, int zchunk, int n_chunks, int n_columns, int vec_in, long long spin, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem;                   // ring of four haloed planes
     unsigned char* sW = smem + 4 * SLOT_BYTES;  // weights of the 27 taps
@@ -537,9 +539,11 @@ conv32_tc_kernel(const TIN* __restrict__ in, int cin, float in_scale, const __ha
     const float out_scale = 1.0f / in_scale;  // in_scale is a power of two: exact
     const bool vin = vec_in != 0;
     uint32_t phase = 0u, pending = 0u;        // per barrier k (bit k): the parity it waits for; a commit not waited for
-    auto drain = [&](int k) {
+    // waits for the MMAs committed on barrier k, if any, polling at most `limit` times; false on a
+    // timeout (they stay pending)
+    auto drain = [&](int k, long long limit) {
         if (!((pending >> k) & 1u)) return true;
-        if (!wait_parity(mbar0 + 8u * (uint32_t)k, (phase >> k) & 1u)) return false;
+        if (!wait_parity(mbar0 + 8u * (uint32_t)k, (phase >> k) & 1u, limit)) return false;
         phase ^= 1u << k;
         pending &= ~(1u << k);
         return true;
@@ -625,7 +629,7 @@ conv32_tc_kernel(const TIN* __restrict__ in, int cin, float in_scale, const __ha
             pending |= 1u << k;
             if (zi > 0) {
                 // step z - 1 is done: its output, then its ring slot takes plane z + 2
-                if (!drain(k ^ 1)) {
+                if (!drain(k ^ 1, spin)) {
                     s_fail = 1;
                     atomicExch(err, 1);
                 } else {
@@ -643,7 +647,7 @@ conv32_tc_kernel(const TIN* __restrict__ in, int cin, float in_scale, const __ha
         // the column's last step
         const int kl = (z_end - 1 - z_begin) & 1;
         if (!s_fail) {
-            if (!drain(kl)) {
+            if (!drain(kl, spin)) {
                 s_fail = 1;
                 atomicExch(err, 1);
             } else {
@@ -655,8 +659,9 @@ conv32_tc_kernel(const TIN* __restrict__ in, int cin, float in_scale, const __ha
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
     }
-    // on a timeout, one more bounded wait for MMAs still in flight before the memory is freed
-    for (int kb = 0; kb < 2; ++kb) drain(kb);
+    // on a timeout, one more wait, bounded by the full limit whatever `spin` was, for MMAs still
+    // in flight before the memory is freed
+    for (int kb = 0; kb < 2; ++kb) drain(kb, kSpin);
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (t < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
@@ -785,7 +790,7 @@ template <typename TH>
 __global__ void __launch_bounds__(WG_THREADS, 1)
 wgrad32_tc_kernel(const float* __restrict__ g, int cout, float g_scale, const TH* __restrict__ h, int cin,
                   float* __restrict__ gW, int D, int H, int Wd, int tiles_x, int tiles_y, int n_chunks, int n_columns,
-                  int vec_h, int vec_g, int* __restrict__ err) {
+                  int vec_h, int vec_g, long long spin, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sH = smem;                       // ring of four haloed planes
     unsigned char* sG = smem + 4 * WG_PLANE_BYTES;  // two g buffers
@@ -817,10 +822,11 @@ wgrad32_tc_kernel(const float* __restrict__ g, int cout, float g_scale, const TH
     const long long vox = (long long)D * H * Wd;
     uint32_t phase = 0u, pending = 0u;  // bit k: the parity barrier k waits for; a commit on it not yet waited for
     bool first = true;
-    // waits for the MMAs committed on barrier k, if any; false on a timeout (they stay pending)
-    auto drain = [&](int k) {
+    // waits for the MMAs committed on barrier k, if any, polling at most `limit` times; false on a
+    // timeout (they stay pending)
+    auto drain = [&](int k, long long limit) {
         if (!((pending >> k) & 1u)) return true;
-        if (!wait_parity(mbar0 + 8u * (uint32_t)k, (phase >> k) & 1u)) return false;
+        if (!wait_parity(mbar0 + 8u * (uint32_t)k, (phase >> k) & 1u, limit)) return false;
         phase ^= 1u << k;
         pending &= ~(1u << k);
         return true;
@@ -878,7 +884,7 @@ wgrad32_tc_kernel(const float* __restrict__ g, int cout, float g_scale, const TH
             first = false;
             if (z + 1 < z_end) {
                 // the buffers of step z - 1 are free once its MMAs are done; stage into them
-                if (!drain(k ^ 1)) {
+                if (!drain(k ^ 1, spin)) {
                     s_fail = 1;
                     atomicExch(err, 1);
                 }
@@ -893,14 +899,15 @@ wgrad32_tc_kernel(const float* __restrict__ g, int cout, float g_scale, const TH
         }
         // the column's last MMAs read the ring: wait for them before the next prologue
         for (int kb = 0; kb < 2; ++kb)
-            if (!drain(kb)) {
+            if (!drain(kb, spin)) {
                 s_fail = 1;
                 atomicExch(err, 1);
             }
         __syncthreads();
     }
-    // on a timeout, one more bounded wait for MMAs still in flight before the memory is freed
-    for (int kb = 0; kb < 2; ++kb) drain(kb);
+    // on a timeout, one more wait, bounded by the full limit whatever `spin` was, for MMAs still
+    // in flight before the memory is freed
+    for (int kb = 0; kb < 2; ++kb) drain(kb, kSpin);
     asm volatile("tcgen05.fence::after_thread_sync;");
     __syncthreads();
     // read the nine accumulators out: warp w < 4 holds rows 32 w .. 32 w + 31, i.e. dx = w, c = lane
@@ -970,7 +977,7 @@ static int tc_blocks() {
 }
 
 cudaError_t wgrad32_tc(const float* g, int cout, float g_scale, const void* h, int h_fp16, int cin, float* gW, float* gb,
-                       int batch, int D, int H, int Wd, int* err, cudaStream_t s) {
+                       int batch, int D, int H, int Wd, long long spin, int* err, cudaStream_t s) {
     if (cin > 32 || cout > 32) return cudaErrorInvalidValue;
     const int tx = (Wd + tc::WG_TX - 1) / tc::WG_TX, ty = (H + tc::WG_TY - 1) / tc::WG_TY;
     const int n_chunks = (D + tc::WG_ZCHUNK - 1) / tc::WG_ZCHUNK;
@@ -987,12 +994,12 @@ cudaError_t wgrad32_tc(const float* g, int cout, float g_scale, const void* h, i
         e = cudaFuncSetAttribute(tc::wgrad32_tc_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::WG_SMEM);
         if (e != cudaSuccess) return e;
         tc::wgrad32_tc_kernel<__half><<<blocks, tc::WG_THREADS, tc::WG_SMEM, s>>>(
-            g, cout, g_scale, (const __half*)h, cin, gW, D, H, Wd, tx, ty, n_chunks, n_columns, vec_h, vec_g, err);
+            g, cout, g_scale, (const __half*)h, cin, gW, D, H, Wd, tx, ty, n_chunks, n_columns, vec_h, vec_g, spin, err);
     } else {
         e = cudaFuncSetAttribute(tc::wgrad32_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::WG_SMEM);
         if (e != cudaSuccess) return e;
         tc::wgrad32_tc_kernel<float><<<blocks, tc::WG_THREADS, tc::WG_SMEM, s>>>(
-            g, cout, g_scale, (const float*)h, cin, gW, D, H, Wd, tx, ty, n_chunks, n_columns, vec_h, vec_g, err);
+            g, cout, g_scale, (const float*)h, cin, gW, D, H, Wd, tx, ty, n_chunks, n_columns, vec_h, vec_g, spin, err);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1003,7 +1010,8 @@ cudaError_t wgrad32_tc(const float* g, int cout, float g_scale, const void* h, i
 }
 
 cudaError_t conv32_tc(const void* in, int in_fp16, int cin, float in_scale, const __half* wimg, const float* bias, void* out,
-                      int out_fp16, int cout, int relu, int batch, int D, int H, int Wd, int* err, cudaStream_t s) {
+                      int out_fp16, int cout, int relu, int batch, int D, int H, int Wd, long long spin, int* err,
+                      cudaStream_t s) {
     if (cin > 32 || cout > 32) return cudaErrorInvalidValue;
     const int tx = (Wd + tc::TX - 1) / tc::TX, ty = (H + tc::TY - 1) / tc::TY;
     // z chunks of 8 planes: 10 staged planes per 8 steps, and enough columns to fill the GPU
@@ -1020,7 +1028,7 @@ cudaError_t conv32_tc(const void* in, int in_fp16, int cin, float in_scale, cons
         if (e_ != cudaSuccess) return e_;                                                                          \
         tc::conv32_tc_kernel<TIN, MODE, TOUT><<<blocks, tc::CONV_THREADS, tc::SMEM, s>>>(                          \
             (const TIN*)in, cin, in_scale, wimg, bias, (TOUT*)out, cout, D, H, Wd, tx, ty, zchunk, n_chunks,       \
-            n_columns, vec_in, err);                                                                               \
+            n_columns, vec_in, spin, err);                                                                         \
     } while (0)
     if (in_fp16 && out_fp16 && relu) LBM_TC(__half, 1, __half);
     else if (!in_fp16 && !out_fp16 && !relu) LBM_TC(float, 0, float);

@@ -96,6 +96,7 @@ SIGNATURES = [
     ("lbm_net_gradients", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, _ip, _dp]),
     ("lbm_net_set_loss_weights", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
     ("lbm_net_adam", ctypes.c_int, [ctypes.c_void_p, ctypes.c_float]),
+    ("lbm_net_fail_waits", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("lbm_net_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("lbm_net_destroy", None, [ctypes.c_void_p]),
     ("lbm_coarse_fields", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
@@ -502,6 +503,9 @@ class Net:
 
     def adam(self, lr):
         _ncheck(self.n, load().lbm_net_adam(self.n, float(lr)))
+
+    def fail_waits(self, on):
+        _ncheck(self.n, load().lbm_net_fail_waits(self.n, int(bool(on))))
 
 
 def lbm_coarse_fields(h, factor, out_ptr):

@@ -106,6 +106,37 @@ def test_gradients_match_oracle(fp16, tol, cw, grid):
             assert np.abs(g[l][j] - want).max() <= tol * np.abs(want).max()
 
 
+def test_tensor_core_wait_timeout_is_reported_and_the_network_recovers():
+    """The bounded waits of the tensor-core kernels, made to run out: with lbm_net_fail_waits on,
+    every wait for a step's MMAs gives up at once, the kernels stop, wait (with the full bound)
+    for the MMAs they issued and free their tensor memory, and the call returns LBM_ETIMEOUT. With
+    the normal waits restored, the same network's forward pass and gradients match the oracle."""
+    net, weights = _random_net(True)
+    rng = np.random.default_rng(14)
+    grid = (16, 16, 16)
+    x = rng.normal(0, 1, (1, 5, 16, 16, 16)).astype(np.float32)
+    t = (x + rng.normal(0, 0.3, x.shape)).astype(np.float32)
+    xd, td, yd = _dev(x), _dev(t), torch.empty(x.shape, device="cuda")
+    net.fail_waits(True)
+    with pytest.raises(lbm.LBMError) as e:
+        net.forward(xd.data_ptr(), yd.data_ptr(), 1, grid)
+        torch.cuda.synchronize()
+        net.get_params()  # a synchronising call reads the flag
+    assert e.value.status == lbm.LBM_ETIMEOUT
+    with pytest.raises(lbm.LBMError) as e:
+        net.gradients(xd.data_ptr(), td.data_ptr(), 1, grid)
+    assert e.value.status == lbm.LBM_ETIMEOUT
+    net.fail_waits(False)
+    net.forward(xd.data_ptr(), yd.data_ptr(), 1, grid)
+    torch.cuda.synchronize()
+    net.get_params()
+    want, _ = cnn.forward(x[0].astype(np.float64), weights)
+    assert np.abs(yd.cpu().numpy()[0] - want).max() <= 1e-2 * np.abs(want - x[0]).max()
+    loss = net.gradients(xd.data_ptr(), td.data_ptr(), 1, grid)
+    want_loss, _ = cnn.loss_and_gradients(x[0].astype(np.float64), t[0].astype(np.float64), weights, None)
+    assert loss == pytest.approx(want_loss, rel=2e-2)
+
+
 def test_adam_step_matches_its_formula():
     net, _ = _random_net(False, seed=9)
     rng = np.random.default_rng(13)
