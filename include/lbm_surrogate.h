@@ -77,6 +77,11 @@ void lbm_net_destroy(lbm_net *net);
  * v, w and p as lbm_moments computes them. */
 int lbm_coarse_fields(lbm_ctx *ctx, int factor, float *out);
 
+/* Block means over f^3 cells of the state's own phi (the fixed-point zeroth moment of g, before
+ * propagation), device out [nz/f][ny/f][nx/f]: what the judge of lbm_surrogate_jump measures
+ * right after a restart and judge_steps later. f must divide 32 as well as nx, ny and nz. */
+int lbm_coarse_phi(lbm_ctx *ctx, int factor, float *out);
+
 /* Replace the state by the one lbm_init_fields builds from coarse fields (device [5][...] as
  * above) upsampled trilinearly between coarse cell centres (periodic; clamped across walls),
  * with p0 the reference pressure of the storage; the construction runs in FP32 in one pass, and

@@ -76,6 +76,8 @@ def _load():
     lib.oracle_mass.argtypes = [ctypes.c_void_p, _dp, _dp]
     lib.oracle_get_pops.argtypes = [ctypes.c_void_p, _dp, _dp]
     lib.oracle_set_pops.argtypes = [ctypes.c_void_p, _dp, _dp]
+    lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
+    lib.oracle_set_num_threads.restype = None
     _lib = lib
     return lib
 
@@ -93,6 +95,11 @@ def _vec(v, n=3):
 
 def num_threads() -> int:
     return int(_load().oracle_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the following oracle calls (results do not depend on it)."""
+    _load().oracle_set_num_threads(int(n))
 
 
 # --------------------------------------------------------------------------

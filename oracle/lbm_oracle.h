@@ -91,6 +91,9 @@ int oracle_mass(oracle *o, double *sum_phi, double *sum_rho_phi);
 int oracle_get_pops(const oracle *o, double *f, double *g);
 int oracle_set_pops(oracle *o, const double *f, const double *g);
 int oracle_num_threads(void);
+/* Threads the following oracle calls use (n >= 1; a no-op without OpenMP). Results do not depend
+ * on it: every cell writes only its own outputs. */
+void oracle_set_num_threads(int n);
 
 #ifdef __cplusplus
 }

@@ -363,6 +363,18 @@ int lbm_coarse_fields(lbm_ctx* c, int f, float* out) {
     return LBM_OK;
 }
 
+int lbm_coarse_phi(lbm_ctx* c, int f, float* out) {
+    int rc = lbm::ctx_check(c);
+    if (rc) return rc;
+    if (!out || f < 1 || f > 32 || 32 % f || c->P.nx % f || c->P.ny % f || c->P.nz % f)
+        return lbm::ctx_error(c, LBM_EINVAL, "factor must divide 32, nx, ny and nz, and out may not be NULL");
+    if (!c->initialised) return lbm::ctx_error(c, LBM_ESTATE, "no state: call lbm_init_phi first");
+    cudaError_t e = lbm::launch_coarse_phi(c->P, c->fg[c->cur], f, out, c->stream);
+    if (e != cudaSuccess) return lbm::ctx_error(c, LBM_ECUDA, cudaGetErrorString(e));
+    c->launches += 1;
+    return LBM_OK;
+}
+
 int lbm_restart_from_coarse(lbm_ctx* c, int f, const float* coarse, double p0) {
     int rc = lbm::ctx_check(c);
     if (rc) return rc;

@@ -100,6 +100,7 @@ SIGNATURES = [
     ("lbm_net_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("lbm_net_destroy", None, [ctypes.c_void_p]),
     ("lbm_coarse_fields", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    ("lbm_coarse_phi", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     ("lbm_restart_from_coarse", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_double]),
     ("lbm_surrogate_jump", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
                                           ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -510,6 +511,10 @@ class Net:
 
 def lbm_coarse_fields(h, factor, out_ptr):
     _check(h, load().lbm_coarse_fields(h, int(factor), ctypes.c_void_p(out_ptr)))
+
+
+def lbm_coarse_phi(h, factor, out_ptr):
+    _check(h, load().lbm_coarse_phi(h, int(factor), ctypes.c_void_p(out_ptr)))
 
 
 def lbm_restart_from_coarse(h, factor, coarse_ptr, p0=1.0 / 3.0):

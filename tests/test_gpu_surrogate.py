@@ -328,7 +328,8 @@ def test_shifted_interface_is_rejected_and_the_lbm_takes_over():
     np.testing.assert_array_equal(ga, gb)
     net.set_params(np.zeros(net.param_count, dtype=np.float32))  # persistence
     rep = lbm.lbm_surrogate_jump(g.h, net, 2, ms, k, 4, 1e-3, 1e9, 1.0)
-    assert rep["interface_shift"] == 0.0 and rep["relax_ratio"] > 0.0
+    # shift 0 up to the FP32 rounding of normalising and denormalising phi; judged by the LBM
+    assert rep["interface_shift"] < 1e-6 and rep["relax_ratio"] > 0.0
 
 
 def test_trained_surrogate_beats_persistence_and_is_accepted():
