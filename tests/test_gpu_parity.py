@@ -334,12 +334,14 @@ def test_launch_count_is_one_kernel_per_step():
 
 
 # ---------------------------------------------------------------- physics on the GPU
-def test_laplace_law_3d_full_size():
-    """3D static droplet, 128^3, R = 24, 5000 steps: p_in - p_out = 2 sigma / R_eff within 5%,
-    sum phi unchanged, spurious currents small."""
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_laplace_law_3d_full_size(scheme):
+    """3D static droplet, 128^3, R = 24, 5000 steps, in the difference-free scheme and the
+    finite-difference variant: p_in - p_out = 2 sigma / R_eff within 5%, sum phi unchanged,
+    spurious currents small."""
     w = I.WORKLOADS["droplet3d_128"]
     grid, R, xi = w["grid"], w["R"], w["xi"]
-    g = lbm.Lattice(grid, 19, w["tau_f"], w["tau_g"], w["M"], xi, w["sigma"])
+    g = lbm.Lattice(grid, 19, w["tau_f"], w["tau_g"], w["M"], xi, w["sigma"], scheme=scheme)
     g.init_phi(I.droplet_phi(grid, R, xi))
     s0 = g.mass()[0]
     g.step(w["steps"])
