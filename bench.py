@@ -167,12 +167,21 @@ def sig(x, n=4):
     return round(x, n - 1 - int(math.floor(math.log10(abs(x)))))
 
 
+def hold_stream(torch, stream):
+    """Keep `stream` busy for about half a millisecond (a bounded spin of torch's), so that the
+    host has queued the timed launches before the start event is reached: the timed region then
+    holds the steps, not the host's latency in issuing the first of them."""
+    with torch.cuda.stream(stream):
+        torch.cuda._sleep(1_000_000)
+
+
 def time_region(torch, stream, step_fn, world):
     """Device seconds of step_fn on `stream` (CUDA events), barrier and synchronize on both
     sides, max over ranks."""
     torch.cuda.synchronize()
     barrier(world)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    hold_stream(torch, stream)
     ev0.record(stream)
     step_fn()
     ev1.record(stream)
@@ -248,6 +257,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     n0 = g.launch_count
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    hold_stream(torch, stream)
     ev0.record(stream)
     g.step(args.steps)
     ev1.record(stream)
