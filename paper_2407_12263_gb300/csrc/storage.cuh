@@ -100,9 +100,13 @@ struct Store<STORE_F16> {
     __device__ __forceinline__ static void store(T* p, float f, float g, const Params&) {
         store_raw(p, f * kScaleF, g * kScaleG);
     }
-    __device__ __forceinline__ static void store_raw(T* p, float f, float g) {
+    // the pair (f, g), already in storage units, rounded to its stored bits
+    __device__ __forceinline__ static unsigned int pack_raw(float f, float g) {
         const __half2 h = __floats2half2_rn(f, g);
-        __stcs(reinterpret_cast<unsigned int*>(p), *reinterpret_cast<const unsigned int*>(&h));
+        return *reinterpret_cast<const unsigned int*>(&h);
+    }
+    __device__ __forceinline__ static void store_raw(T* p, float f, float g) {
+        __stcs(reinterpret_cast<unsigned int*>(p), pack_raw(f, g));
     }
 };
 
@@ -133,9 +137,12 @@ struct Store<STORE_BF16> {
     static constexpr float kScaleF = 1.0f, kScaleG = 1.0f, kInvF = 1.0f, kInvG = 1.0f;
     __device__ __forceinline__ static float2 load(const T* p, const Params&) { return __bfloat1622float2(__ldg(p)); }
     __device__ __forceinline__ static void store(T* p, float f, float g, const Params&) { store_raw(p, f, g); }
-    __device__ __forceinline__ static void store_raw(T* p, float f, float g) {
+    __device__ __forceinline__ static unsigned int pack_raw(float f, float g) {
         const __nv_bfloat162 h = __floats2bfloat162_rn(f, g);
-        __stcs(reinterpret_cast<unsigned int*>(p), *reinterpret_cast<const unsigned int*>(&h));
+        return *reinterpret_cast<const unsigned int*>(&h);
+    }
+    __device__ __forceinline__ static void store_raw(T* p, float f, float g) {
+        __stcs(reinterpret_cast<unsigned int*>(p), pack_raw(f, g));
     }
 };
 
