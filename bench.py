@@ -335,6 +335,8 @@ def summary(value, df_long, fd, sixteen, bubbles, laplace, acc, rt_acc, tgv, rt,
     s["rt512_fp16_vs_fp32"] = rt["fp16"]["speedup_vs_fp32"]
     b = bubbles
     s["batch"] = {"one_per_launch": sig(b["one_case_per_launch_fp32"]),
+                  "group_only": sig(b["batched_fp32_group_launches_only"]["value"]),
+                  "group_only_hbm_frac": b["batched_fp32_group_launches_only"]["hbm_frac"],
                   "fp32": sig(b["batched_fp32_default_tiles"]["value"]),
                   "fp32_tuned": sig(b["batched_fp32_tuned"]["value"]),
                   "auto_tuned": sig(b["batched_auto_tuned"]["value"]),
@@ -676,11 +678,14 @@ def run_batched_bubbles(lbm, torch, stream, args, world):
         h.close()
     del singles
 
-    def batched(storage, tune):
+    def batched(storage, tune, group_only=False):
         structs = [lbm.make_case(**{k: c[k] for k in CASE_KEYS}, storage=storage) for c in cases]
         b = lbm.Batch(structs, stream=stream.cuda_stream)
         if tune:
             b.tune(trial_steps=5)
+        if group_only:  # every case in group launches of its default tile
+            for k in range(len(cases)):
+                b.set_config(k, b.config(k)[0], dedicated=False)
         for k, c in enumerate(cases):
             b.case(k).init_phi(I.bubble_phi(c))
         m0 = [b.case(k).mass()[0] for k in range(len(cases))]
@@ -704,12 +709,18 @@ def run_batched_bubbles(lbm, torch, stream, args, world):
         return {"value": round(aggregate_mlups(cells, steps, secs, world), 1), "launches_per_step": launches / steps,
                 "cases_by_form": forms, "nonfinite_cases": nonfinite, "sum_phi_changed_cases": changed}
 
+    out["batched_fp32_group_launches_only"] = batched(lbm.LBM_STORAGE_FP32, False, group_only=True)
     out["batched_fp32_default_tiles"] = batched(lbm.LBM_STORAGE_FP32, False)
     out["batched_fp32_tuned"] = batched(lbm.LBM_STORAGE_FP32, True)
     out["batched_auto_tuned"] = batched(lbm.LBM_STORAGE_AUTO, True)
     base = out["one_case_per_launch_fp32"]
-    for key in ("batched_fp32_default_tiles", "batched_fp32_tuned", "batched_auto_tuned"):
+    peak = measured_peak_hbm()[0]
+    out["one_case_per_launch_hbm_frac"] = round(base * 1e6 * BYTES_PER_CELL["df"] / 1e9 / peak, 4)
+    for key in ("batched_fp32_group_launches_only", "batched_fp32_default_tiles", "batched_fp32_tuned",
+                "batched_auto_tuned"):
         out[key]["speedup_vs_one_case_per_launch"] = round(out[key]["value"] / base, 4)
+    for key in ("batched_fp32_group_launches_only", "batched_fp32_default_tiles", "batched_fp32_tuned"):
+        out[key]["hbm_frac"] = round(out[key]["value"] * 1e6 * BYTES_PER_CELL["df"] / 1e9 / peak, 4)
     return out
 
 

@@ -1,10 +1,10 @@
 // batch_kernels.cu -- many independent cases of the difference-free conservative phase-field
 // LBM (arXiv:2407.12263) of one grid size advanced by ONE launch ("group launch").
 //
-// The group's cases (up to 128, each with its own parameters, walls and buffers) travel in the
+// The group's cases (up to 128, each with its own fluid properties and buffers) travel in the
 // kernel's parameter block. Block (t, k, tz) runs one tile of 128 cells, a 2^a x 2^b x 2^c box
-// chosen by the tuner, of case k = blockIdx.y: the case index is uniform over the block, so
-// every parameter read is a uniform load from the constant bank. Each thread runs step_cell,
+// chosen by the tuner, of case k = blockIdx.y: the case index is uniform over the block, so its
+// parameter reads are uniform loads from the constant bank. Each thread runs step_cell,
 // the same per-cell code as the single-case kernel, so a case gives the same bits either way.
 // A group of 35 cases of 32^3 cells is 8960 blocks, where each case alone is 256: the group
 // fills the 152 SMs that a single small case cannot.
@@ -16,7 +16,19 @@ template <int Q, bool GEN, int S>
 __global__ void __launch_bounds__(kBatchThreads, 4)
 batch_step_kernel(const __grid_constant__ BatchLaunch L) {
     const LaunchCase& C = L.cases[blockIdx.y];
-    const Params& P = C.P;
+    // The host groups cases that share every parameter except their fluid properties (see
+    // group_key in lbm_batch.cu), so those shared fields are read from case 0, at fixed offsets
+    // of the parameter block: operands of the instructions that use them, not loads. Only the
+    // fluid properties of case blockIdx.y are loads through a run-time index.
+    Params P = L.cases[0].P;
+    P.tau_f = C.P.tau_f;
+    P.omega_f = C.P.omega_f;
+    P.drho = C.P.drho;
+    P.mu_m1 = C.P.mu_m1;
+    P.sigma = C.P.sigma;
+    P.G[0] = C.P.G[0];
+    P.G[1] = C.P.G[1];
+    P.G[2] = C.P.G[2];
     const int txs = L.tx_shift, tys = L.ty_shift, tzs = 7 - txs - tys;
     const int ty_i = blockIdx.x / L.ntx;
     const int tx_i = blockIdx.x - ty_i * L.ntx;

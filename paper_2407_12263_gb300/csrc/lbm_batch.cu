@@ -18,6 +18,7 @@
 #include <cstring>
 #include <map>
 #include <new>
+#include <string>
 #include <tuple>
 #include <vector>
 
@@ -123,17 +124,31 @@ int next_pow2_shift(int n) {
 
 long long case_cells(const lbm_ctx* c) { return c->P.N; }
 
-// Group launches for the cases in `which` (dedicated cases excluded by the caller): cases of one
-// grid size, tile shape, kernel variant and storage, up to kMaxLaunchCases per launch.
+// The bytes of every parameter a group launch takes from its first case for all of its cases
+// (batch_step_kernel): the grid, walls, kernel variant and storage, the propagation and flux
+// weights, the phase-field relaxation and interface constants and the storage shifts. Cases with
+// equal keys differ only in their fluid properties (tau_f, density and viscosity ratio, surface
+// tension, body force), which the kernel reads per case.
+std::string group_key(const lbm::Params& P, int tx_shift, int ty_shift) {
+    std::string k;
+    auto put = [&](const void* v, size_t n) { k.append(static_cast<const char*>(v), n); };
+    const int ints[] = {P.Q, P.nx, P.ny, P.nz, P.general, P.storage, P.walls, P.phi_ref_fx, tx_shift, ty_shift};
+    const float floats[] = {P.lw_m, P.lw_p, P.flux_as, P.flux_bs, P.tau_phi, P.omega_g, P.grad_s, P.grad_k,
+                            P.rho2, P.four_over_delta, P.w0, P.phi_ref};
+    put(ints, sizeof ints);
+    put(floats, sizeof floats);
+    return k;
+}
+
+// Group launches for the cases in `which` (dedicated cases excluded by the caller): cases with
+// equal group keys (one grid size, tile shape, kernel variant, storage and shared parameters),
+// up to kMaxLaunchCases per launch.
 void build_groups(const lbm_batch* b, const std::vector<int>& which, std::vector<lbm::BatchLaunch>& groups,
                   std::vector<long long>* group_cells) {
     groups.clear();
     if (group_cells) group_cells->clear();
-    std::map<std::tuple<int, int, int, int, int, int, int>, std::vector<int>> by_class;
-    for (int k : which) {
-        const lbm::Params& P = b->cases[k]->P;
-        by_class[std::make_tuple(P.nx, P.ny, P.nz, b->tx_shift[k], b->ty_shift[k], P.general, P.storage)].push_back(k);
-    }
+    std::map<std::string, std::vector<int>> by_class;
+    for (int k : which) by_class[group_key(b->cases[k]->P, b->tx_shift[k], b->ty_shift[k])].push_back(k);
     for (auto& kv : by_class) {
         const std::vector<int>& ks = kv.second;
         for (size_t i = 0; i < ks.size(); i += lbm::kMaxLaunchCases) {
