@@ -35,6 +35,8 @@
 #ifndef LBM_GB300_H
 #define LBM_GB300_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -103,6 +105,28 @@ void lbm_default_opts(lbm_opts *opts);
 int lbm_create(lbm_ctx **out, const int grid[3], int lattice, double tau_f, double tau_g,
                double M, double xi, double sigma, double rho_ratio, double mu_ratio,
                const double body_force[3], const lbm_opts *opts);
+
+/* Bytes of one state buffer (a handle holds two) for this lattice, grid and storage: 8 B per
+ * cell for the zeroth moments plus Q - 1 moving (f, g) pairs of 8 B (FP32) or 4 B (FP16, BF16).
+ * Host-only; 0 for invalid arguments. */
+long long lbm_state_bytes(int lattice, const int grid[3], int storage);
+
+/*
+ * lbm_create with the two state buffers owned by the caller (a framework's tensors, a pool or
+ * an arena the caller manages). fg0 and fg1: device memory of the current device, starting on
+ * 16-byte boundaries, not overlapping, bytes_each >= lbm_state_bytes(lattice, grid,
+ * opts->storage) each. The handle keeps its state in them for its lifetime, in the layout of
+ * lbm.h's storage description, and never frees them: lbm_destroy leaves them to the caller,
+ * who must not free or reuse them before it. The library still allocates its small buffers
+ * (reduction scratch, the finite-difference phi plane, host staging on first use, the surrogate
+ * workspace). LBM_EINVAL for NULL, misaligned, overlapping, too small or non-device buffers;
+ * otherwise as lbm_create. (The paper does not discuss memory ownership; Sec. 3.4 runs
+ * IMEXLBM, which owns its arrays.)
+ */
+int lbm_create_ext(lbm_ctx **out, const int grid[3], int lattice, double tau_f, double tau_g,
+                   double M, double xi, double sigma, double rho_ratio, double mu_ratio,
+                   const double body_force[3], const lbm_opts *opts, void *fg0, void *fg1,
+                   size_t bytes_each);
 
 /*
  * Initial state from the order parameter (host FP64, nx*ny*nz), an optional velocity

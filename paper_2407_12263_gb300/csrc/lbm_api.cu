@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <climits>
+#include <cstdint>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -55,7 +56,8 @@ void free_ctx(lbm_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    for (int k = 0; k < 2; ++k) cudaFree(c->fg[k]);
+    if (c->own_fg)
+        for (int k = 0; k < 2; ++k) cudaFree(c->fg[k]);
     cudaFree(c->phi_fd);
     cudaFree(c->partials);
     cudaFree(c->result);
@@ -153,11 +155,48 @@ int lbm_create(lbm_ctx** out, const int grid[3], int lattice, double tau_f, doub
                            o.storage);
 }
 
+long long lbm_state_bytes(int lattice, const int grid[3], int storage) {
+    if (!grid || (lattice != LBM_D2Q9 && lattice != LBM_D3Q19) || storage < 0 || storage > 2) return 0;
+    if (grid[0] < 1 || grid[1] < 1 || grid[2] < 1) return 0;
+    const long long N = (long long)grid[0] * grid[1] * grid[2];
+    if (N >= (long long)INT_MAX) return 0;
+    return (long long)lbm::state_bytes(lattice, N, storage);
+}
+
+int lbm_create_ext(lbm_ctx** out, const int grid[3], int lattice, double tau_f, double tau_g, double M, double xi,
+                   double sigma, double rho_ratio, double mu_ratio, const double body_force[3], const lbm_opts* opts,
+                   void* fg0, void* fg1, size_t bytes_each) {
+    lbm_opts o;
+    lbm_default_opts(&o);
+    if (opts) o = *opts;
+    if (out) *out = nullptr;
+    if (!fg0 || !fg1) return set_error(nullptr, LBM_EINVAL, "the two state buffers may not be NULL");
+    if ((reinterpret_cast<uintptr_t>(fg0) | reinterpret_cast<uintptr_t>(fg1)) % 16)
+        return set_error(nullptr, LBM_EINVAL, "the state buffers must start on 16-byte boundaries");
+    const uintptr_t a = reinterpret_cast<uintptr_t>(fg0), b = reinterpret_cast<uintptr_t>(fg1);
+    if ((a < b ? b - a : a - b) < bytes_each)
+        return set_error(nullptr, LBM_EINVAL, "the state buffers overlap");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return set_error(nullptr, LBM_ECUDA, "no CUDA device available");
+    for (void* ptr : {fg0, fg1}) {
+        cudaPointerAttributes attr;
+        if (cudaPointerGetAttributes(&attr, ptr) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return set_error(nullptr, LBM_EINVAL, "a state buffer is not memory the CUDA runtime knows");
+        }
+        if (attr.type != cudaMemoryTypeDevice || attr.device != dev)
+            return set_error(nullptr, LBM_EINVAL, "the state buffers must be device memory of the current device");
+    }
+    void* fg[2] = {fg0, fg1};
+    return lbm::create_ctx(out, grid, lattice, tau_f, tau_g, M, xi, sigma, rho_ratio, mu_ratio, body_force, &o,
+                           o.storage, fg, bytes_each);
+}
+
 }  // extern "C"
 
 int lbm::create_ctx(lbm_ctx** out, const int grid[3], int lattice, double tau_f, double tau_g, double M, double xi,
                     double sigma, double rho_ratio, double mu_ratio, const double body_force[3], const lbm_opts* opts,
-                    int alloc_storage) {
+                    int alloc_storage, void* const* ext_fg, size_t ext_bytes) {
     if (!out) return set_error(nullptr, LBM_EINVAL, "out is NULL");
     *out = nullptr;
     if (!grid) return set_error(nullptr, LBM_EINVAL, "grid is NULL");
@@ -271,12 +310,26 @@ int lbm::create_ctx(lbm_ctx** out, const int grid[3], int lattice, double tau_f,
         lbm::state_bytes(lattice, N, alloc_storage) < lbm::state_bytes(lattice, N, o.storage))
         alloc_storage = o.storage;
     const size_t pop_bytes = lbm::state_bytes(lattice, N, alloc_storage);
-    c->fg_bytes = pop_bytes;
-    for (int k = 0; k < 2 && rc == LBM_OK; ++k) {
-        cudaError_t e = cudaMalloc(&c->fg[k], pop_bytes);
-        if (e != cudaSuccess)
-            rc = set_error(c, e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA,
-                           "allocating %zu bytes of populations failed: %s", 2 * pop_bytes, cudaGetErrorString(e));
+    if (ext_fg) {
+        // the caller's buffers: used for the handle's lifetime, never freed here
+        if (ext_bytes < pop_bytes) {
+            set_error(c, LBM_EINVAL, "the state buffers hold %zu bytes each; this grid and storage need %zu", ext_bytes,
+                      pop_bytes);
+            return fail(LBM_EINVAL);
+        }
+        c->fg[0] = ext_fg[0];
+        c->fg[1] = ext_fg[1];
+        c->fg_bytes = ext_bytes;
+        c->own_fg = false;
+    } else {
+        c->fg_bytes = pop_bytes;
+        c->own_fg = true;
+        for (int k = 0; k < 2 && rc == LBM_OK; ++k) {
+            cudaError_t e = cudaMalloc(&c->fg[k], pop_bytes);
+            if (e != cudaSuccess)
+                rc = set_error(c, e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA,
+                               "allocating %zu bytes of populations failed: %s", 2 * pop_bytes, cudaGetErrorString(e));
+        }
     }
     if (rc == LBM_OK && c->scheme == LBM_SCHEME_FINITE_DIFFERENCE) {
         cudaError_t e = cudaMalloc(&c->phi_fd, (size_t)N * sizeof(float));

@@ -15,6 +15,7 @@ struct lbm_ctx {
     cudaStream_t stream;
     bool own_stream;
     void* fg[2];           // ping-pong state: Q planes of N (f, g) pairs each (storage.cuh)
+    bool own_fg;           // false: the caller's buffers (lbm_create_ext), never freed here
     size_t fg_bytes;       // bytes allocated per state buffer (the largest storage the case may take)
     int cur;               // index of the buffer holding the current state
     float* phi_fd;         // propagated phi plane of the finite-difference variant
@@ -39,9 +40,11 @@ namespace lbm {
 // lbm_create with the state buffers sized for alloc_storage (>= the bytes of opts->storage), so
 // that set_ctx_storage may later switch to any storage that fits. Messages of a failed create
 // are in lbm_last_error(NULL).
+// ext_fg, ext_bytes: two caller-owned state buffers of ext_bytes each (lbm_create_ext), or
+// nullptr to allocate them.
 int create_ctx(lbm_ctx** out, const int grid[3], int lattice, double tau_f, double tau_g, double M, double xi,
                double sigma, double rho_ratio, double mu_ratio, const double body_force[3], const lbm_opts* opts,
-               int alloc_storage);
+               int alloc_storage, void* const* ext_fg = nullptr, size_t ext_bytes = 0);
 
 // Switches the storage of a handle that holds no state yet (LBM_ESTATE after lbm_init_phi or
 // lbm_set_pops, LBM_EINVAL if the buffers are too small for it).

@@ -59,6 +59,9 @@ SIGNATURES = [
     ("lbm_default_opts", None, [ctypes.POINTER(lbm_opts)]),
     ("lbm_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), _ip, ctypes.c_int] + [ctypes.c_double] * 7
      + [_dp, ctypes.POINTER(lbm_opts)]),
+    ("lbm_state_bytes", ctypes.c_longlong, [ctypes.c_int, _ip, ctypes.c_int]),
+    ("lbm_create_ext", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), _ip, ctypes.c_int] + [ctypes.c_double] * 7
+     + [_dp, ctypes.POINTER(lbm_opts), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     ("lbm_init_phi", ctypes.c_int, [ctypes.c_void_p, _dp, _dp, ctypes.c_double]),
     ("lbm_init_fields", ctypes.c_int, [ctypes.c_void_p, _dp, _dp, _dp, ctypes.c_double]),
     ("lbm_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
@@ -160,6 +163,24 @@ def lbm_create(grid, lattice, tau_f, tau_g, M, xi, sigma, rho_ratio=1.0, mu_rati
     bf = None if body_force is None else np.ascontiguousarray(body_force, dtype=np.float64)
     st = load().lbm_create(ctypes.byref(h), g, int(lattice), tau_f, tau_g, M, xi, sigma, rho_ratio, mu_ratio,
                            _ptr(bf), ctypes.byref(opts) if opts is not None else None)
+    _check(None, st)
+    return h
+
+
+def lbm_state_bytes(lattice, grid, storage=LBM_STORAGE_FP32) -> int:
+    g = (ctypes.c_int * 3)(*[int(v) for v in grid])
+    return int(load().lbm_state_bytes(int(lattice), g, int(storage)))
+
+
+def lbm_create_ext(grid, lattice, tau_f, tau_g, M, xi, sigma, rho_ratio=1.0, mu_ratio=1.0,
+                   body_force=(0.0, 0.0, 0.0), opts: lbm_opts | None = None, fg0=0, fg1=0, bytes_each=0):
+    """lbm_create on two caller-owned device buffers (raw device pointers)."""
+    h = ctypes.c_void_p()
+    g = (ctypes.c_int * 3)(*[int(v) for v in grid])
+    bf = None if body_force is None else np.ascontiguousarray(body_force, dtype=np.float64)
+    st = load().lbm_create_ext(ctypes.byref(h), g, int(lattice), tau_f, tau_g, M, xi, sigma, rho_ratio, mu_ratio,
+                               _ptr(bf), ctypes.byref(opts) if opts is not None else None, ctypes.c_void_p(fg0),
+                               ctypes.c_void_p(fg1), ctypes.c_size_t(int(bytes_each)))
     _check(None, st)
     return h
 
@@ -316,7 +337,9 @@ class Lattice:
 
     def __init__(self, grid, lattice, tau_f=0.8, tau_g=0.8, M=0.02, xi=4.0, sigma=1e-3, rho_ratio=1.0, mu_ratio=1.0,
                  body_force=(0.0, 0.0, 0.0), scheme=LBM_SCHEME_DIFFERENCE_FREE, courant=0.997, stream=None,
-                 storage=LBM_STORAGE_FP32, graph_steps=None, walls=0, handle=None):
+                 storage=LBM_STORAGE_FP32, graph_steps=None, walls=0, handle=None, buffers=None):
+        """buffers: None (the library allocates the state), or (fg0, fg1, bytes_each), two
+        caller-owned device buffers (lbm_create_ext) that must outlive the handle."""
         if handle is not None:  # a handle owned elsewhere (a case of a Batch)
             self.h, self._owned = handle, False
             nx, ny, nz = grid
@@ -328,7 +351,12 @@ class Lattice:
         if graph_steps is not None:
             o.graph_steps = graph_steps
         o.stream = stream
-        self.h = lbm_create(grid, lattice, tau_f, tau_g, M, xi, sigma, rho_ratio, mu_ratio, body_force, o)
+        if buffers is None:
+            self.h = lbm_create(grid, lattice, tau_f, tau_g, M, xi, sigma, rho_ratio, mu_ratio, body_force, o)
+        else:
+            fg0, fg1, nbytes = buffers
+            self.h = lbm_create_ext(grid, lattice, tau_f, tau_g, M, xi, sigma, rho_ratio, mu_ratio, body_force, o,
+                                    fg0, fg1, nbytes)
         nx, ny, nz = grid
         self.Q, self.grid, self.shape, self.N = lattice, tuple(grid), (nz, ny, nx), nx * ny * nz
 

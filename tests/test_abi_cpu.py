@@ -205,3 +205,19 @@ def test_rising_bubble_recipe_matches_its_groups():
         assert g * eta1 ** 4 * drho / (c["rho_ratio"] ** 2 * c["sigma"] ** 3) == pytest.approx(c["Mo"], rel=1e-12)
         assert 1 <= c["Eo"] <= 50 and 1e-5 <= c["Mo"] <= 1e-1
         assert np.sqrt(g * D) == pytest.approx(c["U"], rel=1e-12) and 0.04 <= c["U"] <= 0.1
+
+
+@pytest.mark.parametrize("Q,grid,storage,per_cell", [
+    (19, (128, 128, 128), 0, 8 + 18 * 8), (19, (37, 21, 19), 1, 8 + 18 * 4), (19, (8, 8, 8), 2, 8 + 18 * 4),
+    (9, (64, 64, 1), 0, 8 + 8 * 8), (9, (45, 39, 1), 1, 8 + 8 * 4),
+])
+def test_state_bytes_is_the_documented_layout(lib, Q, grid, storage, per_cell):
+    """8 B of zeroth moments plus Q - 1 moving pairs of 8 B (FP32) or 4 B (16-bit) per cell."""
+    assert lbm.lbm_state_bytes(Q, grid, storage) == per_cell * grid[0] * grid[1] * grid[2]
+
+
+def test_state_bytes_rejects_invalid_arguments(lib):
+    assert lbm.lbm_state_bytes(7, (8, 8, 8), 0) == 0
+    assert lbm.lbm_state_bytes(19, (8, 8, 8), 3) == 0
+    assert lbm.lbm_state_bytes(19, (0, 8, 8), 0) == 0
+    assert lbm.lbm_state_bytes(19, (2048, 2048, 1024), 0) == 0
