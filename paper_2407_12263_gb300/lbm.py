@@ -482,7 +482,10 @@ def _ncheck(n, status):
 
 class Net:
     """The convolutional surrogate. Field batches are device FP32 arrays [B][5][D][H][W] passed
-    by pointer (e.g. torch tensors' data_ptr()); grids are (nx, ny, nz)."""
+    by pointer (e.g. torch tensors' data_ptr()); grids are (nx, ny, nz). stream: the cudaStream_t
+    handle the network runs on; None or 0 makes the library create a stream of its own, which is
+    not ordered with torch's default stream (also handle 0), so pass a non-default stream that
+    also runs the torch work producing the inputs."""
 
     def __init__(self, fp16=True, seed=0, stream=None):
         h = ctypes.c_void_p()

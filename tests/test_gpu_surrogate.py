@@ -48,9 +48,22 @@ def _dev(a):
     return torch.tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
 
 
+@pytest.fixture(autouse=True)
+def _one_stream():
+    """Every test runs its torch work on one stream of its own, and its networks on the same
+    stream: torch's default stream has the handle 0, which a network would read as "make a
+    stream of your own", unordered with the torch kernels that write its inputs."""
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        yield
+    s.synchronize()
+
+
 def _net(fp16, seed):
     """A network on torch's current stream, the stream that writes its input tensors."""
-    return lbm.Net(fp16=fp16, seed=seed, stream=torch.cuda.current_stream().cuda_stream)
+    stream = torch.cuda.current_stream().cuda_stream
+    assert stream != 0
+    return lbm.Net(fp16=fp16, seed=seed, stream=stream)
 
 
 def _random_net(fp16, seed=3):
