@@ -31,6 +31,7 @@ struct lbm_net {
     __half* wimg;                     // FP16 tensor-core weight image of one 32 -> 32 layer
     int* tc_err;                      // set by the tensor-core kernel if a wait timed out
     long long tc_spin;                // polls of an mbarrier before a tensor-core wait for a step gives up
+    float* wscratch;                  // partial sums of the tensor-core weight gradients
     int adam_step;
     float loss_w[kFieldChannels];     // per-channel weights of the loss
     // workspace for (batch, voxels)
@@ -93,6 +94,7 @@ void free_net(lbm_net* n) {
     cudaFree(n->wt);
     cudaFree(n->wimg);
     cudaFree(n->tc_err);
+    cudaFree(n->wscratch);
     if (n->own_stream && n->stream) cudaStreamDestroy(n->stream);
     delete n;
 }
@@ -228,6 +230,7 @@ int lbm_net_create(lbm_net** out, int activations_fp16, unsigned long long seed,
     if (e == cudaSuccess) e = cudaMalloc(&n->wt, (size_t)kHidden * kHidden * 27 * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&n->wimg, lbm::net::weight_image_bytes());
     if (e == cudaSuccess) e = cudaMalloc(&n->tc_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&n->wscratch, lbm::net::wgrad_scratch_floats() * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(n->tc_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(n->params, h.data(), bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(n->grads, 0, bytes);
@@ -289,8 +292,8 @@ int lbm_net_gradients(lbm_net* n, const float* x, const float* target, int batch
         const void* h_in = (l == 0) ? n->x_t : n->h[l - 1];
         if (on_tensor_cores(n))
             LBM_NCUDA(n, lbm::net::wgrad32_tc(g, n->cout[l], grad_scale, h_in, n->fp16, n->cin[l], n->grads + n->w_off[l],
-                                              n->grads + n->b_off[l], batch, D, H, W, n->tc_spin, n->tc_err,
-                                              n->stream));
+                                              n->grads + n->b_off[l], batch, D, H, W, n->tc_spin, n->wscratch,
+                                              n->tc_err, n->stream));
         else
             LBM_NCUDA(n, lbm::net::conv_wgrad(g, n->cout[l], h_in, n->fp16, n->cin[l], n->grads + n->w_off[l],
                                               n->grads + n->b_off[l], batch, D, H, W, n->stream));

@@ -51,8 +51,12 @@ cudaError_t conv32_tc(const void* in, int in_fp16, int cin, float in_scale, cons
                       cudaStream_t s);
 // gW [cout][cin][27] += correlation of g [B][cout] with h [B][cin] on the tensor cores (g scaled by
 // g_scale, a power of two, before FP16 rounding and unscaled after); gb [cout] += sum of g.
+// scratch: wgrad_scratch_floats() floats of device memory for the per-CTA and per-block partial
+// sums, which are added in a fixed order: the gradients are the same bits on every run.
+constexpr int kBiasParts = 256;
+size_t wgrad_scratch_floats();
 cudaError_t wgrad32_tc(const float* g, int cout, float g_scale, const void* h, int h_fp16, int cin, float* gW, float* gb,
-                       int batch, int D, int H, int Wd, long long spin, int* err, cudaStream_t s);
+                       int batch, int D, int H, int Wd, long long spin, float* scratch, int* err, cudaStream_t s);
 
 }  // namespace net
 

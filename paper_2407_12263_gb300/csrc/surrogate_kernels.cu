@@ -789,7 +789,7 @@ __device__ __forceinline__ void wg_store_g(unsigned char* __restrict__ buf, cons
 template <typename TH>
 __global__ void __launch_bounds__(WG_THREADS, 1)
 wgrad32_tc_kernel(const float* __restrict__ g, int cout, float g_scale, const TH* __restrict__ h, int cin,
-                  float* __restrict__ gW, int D, int H, int Wd, int tiles_x, int tiles_y, int n_chunks, int n_columns,
+                  float* __restrict__ part, int D, int H, int Wd, int tiles_x, int tiles_y, int n_chunks, int n_columns,
                   int vec_h, int vec_g, long long spin, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sH = smem;                       // ring of four haloed planes
@@ -927,9 +927,10 @@ wgrad32_tc_kernel(const float* __restrict__ g, int cout, float g_scale, const TH
             asm volatile("tcgen05.wait::ld.sync.aligned;");
             if (warp < 3 && c < cin) {
                 const int tap = 9 * (pr / 3) + 3 * (pr % 3) + warp;
+                float* pb = part + (long long)blockIdx.x * cout * cin * 27;
 #pragma unroll
                 for (int o = 0; o < 32; ++o)
-                    if (o < cout) atomicAdd(&gW[((long long)o * cin + c) * 27 + tap], __uint_as_float(v[o]) * inv);
+                    if (o < cout) pb[((long long)o * cin + c) * 27 + tap] = __uint_as_float(v[o]) * inv;
             }
         }
     }
@@ -938,8 +939,17 @@ wgrad32_tc_kernel(const float* __restrict__ g, int cout, float g_scale, const TH
     if (t < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
 }
 
-// gb[o] += sum over the batch and the voxels of g[b][o][v]
-__global__ void bias_grad_kernel(const float* __restrict__ g, int cout, long long vox, int batch, float* __restrict__ gb) {
+// y[i] += sum over k < parts of x[k n + i], k in increasing order (the same bits on every run)
+__global__ void sum_parts_kernel(const float* __restrict__ x, int parts, long long n, float* __restrict__ y) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float acc = 0.f;
+        for (int k = 0; k < parts; ++k) acc += x[(long long)k * n + i];
+        y[i] += acc;
+    }
+}
+
+// partial[blockIdx.x][o] = this block's sum over the batch and the voxels of g[b][o][v]
+__global__ void bias_grad_kernel(const float* __restrict__ g, int cout, long long vox, int batch, float* __restrict__ part) {
     __shared__ float red[256 / 32];
     const int o = blockIdx.y;
     float acc = 0.f;
@@ -953,7 +963,7 @@ __global__ void bias_grad_kernel(const float* __restrict__ g, int cout, long lon
     if (threadIdx.x == 0) {
         float s = 0.f;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-        atomicAdd(&gb[o], s);
+        part[(long long)blockIdx.x * cout + o] = s;
     }
 }
 
@@ -976,16 +986,27 @@ static int tc_blocks() {
     return 2 * (sms > 0 ? sms : 1);
 }
 
+int wgrad_parts() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+size_t wgrad_scratch_floats() { return (size_t)wgrad_parts() * 32 * 32 * 27 + (size_t)kBiasParts * 32; }
+
 cudaError_t wgrad32_tc(const float* g, int cout, float g_scale, const void* h, int h_fp16, int cin, float* gW, float* gb,
-                       int batch, int D, int H, int Wd, long long spin, int* err, cudaStream_t s) {
+                       int batch, int D, int H, int Wd, long long spin, float* scratch, int* err, cudaStream_t s) {
     if (cin > 32 || cout > 32) return cudaErrorInvalidValue;
     const int tx = (Wd + tc::WG_TX - 1) / tc::WG_TX, ty = (H + tc::WG_TY - 1) / tc::WG_TY;
     const int n_chunks = (D + tc::WG_ZCHUNK - 1) / tc::WG_ZCHUNK;
     const int n_columns = tx * ty * n_chunks * batch;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = wgrad_parts();
     const int blocks = n_columns < sms ? n_columns : sms;  // 512 tensor-memory columns each: one per SM
+    // each CTA writes its sums over its columns to its own slice of the scratch; the slices are
+    // then added in CTA order, so the gradients are the same bits on every run
+    float* wpart = scratch;
+    float* bpart = scratch + (size_t)sms * 32 * 32 * 27;
     // 16-byte row loads where every 8-voxel run is aligned and inside its row
     const int vec_h = (Wd % 8 == 0) && ((uintptr_t)h % 16 == 0);
     const int vec_g = (Wd % 8 == 0) && ((uintptr_t)g % 16 == 0);
@@ -994,18 +1015,22 @@ cudaError_t wgrad32_tc(const float* g, int cout, float g_scale, const void* h, i
         e = cudaFuncSetAttribute(tc::wgrad32_tc_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::WG_SMEM);
         if (e != cudaSuccess) return e;
         tc::wgrad32_tc_kernel<__half><<<blocks, tc::WG_THREADS, tc::WG_SMEM, s>>>(
-            g, cout, g_scale, (const __half*)h, cin, gW, D, H, Wd, tx, ty, n_chunks, n_columns, vec_h, vec_g, spin, err);
+            g, cout, g_scale, (const __half*)h, cin, wpart, D, H, Wd, tx, ty, n_chunks, n_columns, vec_h, vec_g, spin, err);
     } else {
         e = cudaFuncSetAttribute(tc::wgrad32_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::WG_SMEM);
         if (e != cudaSuccess) return e;
         tc::wgrad32_tc_kernel<float><<<blocks, tc::WG_THREADS, tc::WG_SMEM, s>>>(
-            g, cout, g_scale, (const float*)h, cin, gW, D, H, Wd, tx, ty, n_chunks, n_columns, vec_h, vec_g, spin, err);
+            g, cout, g_scale, (const float*)h, cin, wpart, D, H, Wd, tx, ty, n_chunks, n_columns, vec_h, vec_g, spin, err);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    const long long nw = (long long)cout * cin * 27;
+    tc::sum_parts_kernel<<<(unsigned)((nw + 255) / 256), 256, 0, s>>>(wpart, blocks, nw, gW);
     const long long vox = (long long)D * H * Wd;
     const long long blk = (vox * batch + 255) / 256;
-    tc::bias_grad_kernel<<<dim3((unsigned)(blk < 256 ? blk : 256), (unsigned)cout), 256, 0, s>>>(g, cout, vox, batch, gb);
+    const int bblocks = (int)(blk < kBiasParts ? blk : kBiasParts);
+    tc::bias_grad_kernel<<<dim3((unsigned)bblocks, (unsigned)cout), 256, 0, s>>>(g, cout, vox, batch, bpart);
+    tc::sum_parts_kernel<<<1, 256, 0, s>>>(bpart, bblocks, cout, gb);
     return cudaGetLastError();
 }
 

@@ -150,6 +150,27 @@ def test_tensor_core_wait_timeout_is_reported_and_the_network_recovers():
     assert loss == pytest.approx(want_loss, rel=2e-2)
 
 
+def test_training_on_the_tensor_cores_is_deterministic():
+    """The weight and bias gradients sum per-CTA partials in a fixed order (no float atomics), so
+    two networks trained alike hold the same bits."""
+    rng = np.random.default_rng(15)
+    grid = (16, 16, 34)
+    x = rng.normal(0, 1, (2, 5) + grid[::-1]).astype(np.float32)
+    t = (x + rng.normal(0, 0.3, x.shape)).astype(np.float32)
+    xd, td = _dev(x), _dev(t)
+    params, losses = [], []
+    for _ in range(2):
+        net = _net(True, 21)
+        ls = [net.gradients(xd.data_ptr(), td.data_ptr(), 2, grid) for _ in range(1)]
+        for _ in range(12):
+            net.adam(1e-3)
+            ls.append(net.gradients(xd.data_ptr(), td.data_ptr(), 2, grid))
+        params.append(net.get_params())
+        losses.append(ls)
+    assert losses[0] == losses[1]
+    np.testing.assert_array_equal(params[0], params[1])
+
+
 def test_adam_step_matches_its_formula():
     net, _ = _random_net(False, seed=9)
     rng = np.random.default_rng(13)
