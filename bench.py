@@ -583,33 +583,14 @@ def run_surrogate_on_stream(lbm, torch, stream, args, world):
     torch.cuda.synchronize()
     t_lbm = ev0.elapsed_time(ev1) / 1e3
     xt = coarse(truth, f)
-    # The judge's relaxation tolerance from the solver itself: restart from the LBM's own coarse
-    # state k steps on (the best prediction the coarse grid can hold) and measure, as the judge
-    # does, how fast phi moves in the next judge_steps steps relative to the rate that state
-    # implies. That is the relaxation the restart alone causes; a prediction may relax at most
-    # twice as fast.
-    phi_c = torch.empty_like(xt[0])
-
-    def coarse_phi(h):
-        torch.cuda.synchronize()
-        lbm.lbm_coarse_phi(h.h, f, phi_c.data_ptr())
-        torch.cuda.synchronize()
-        return phi_c.clone()
-
-    # p0: the handles' reference pressure (init_phi's default 1/3), as the jump's own restart uses
-    lbm.lbm_restart_from_coarse(truth.h, f, xt.contiguous().data_ptr(), 1.0 / 3.0)
-    r_phi = coarse_phi(truth)
-    truth.step(judge_steps)
-    relax_exact = float((coarse_phi(truth) - r_phi).abs().sum()) / judge_steps
-    rate_exact = float((xt[0] - x0[0]).abs().sum()) / k
-    r0 = relax_exact / rate_exact
-    relax_tol = 2.0 * r0
     # the LBM's own interface displacement over the k steps, measured as the judge measures it
     gphi = torch.stack([0.5 * (torch.roll(x0[0], -1, a) - torch.roll(x0[0], 1, a)) for a in range(3)])
     shift_true = f * float((xt[0] - x0[0]).abs().sum()) / float(gphi.pow(2).sum(0).sqrt().sum())
     ms = torch.cat([mean, std]).cpu().numpy().tolist()
-    # judge: mass within 1%, the kinematic interface bound (interface_tol = 1), relaxation within
-    # relax_tol
+    # judge: mass within 1%; the kinematic interface bound (interface_tol = 1); and phi may move
+    # at most twice as fast after the restart from the prediction as after the same restart from
+    # the starting state (relax_tol = 2)
+    relax_tol = 2.0
     rep = lbm.lbm_surrogate_jump(jumper.h, net, f, ms, k, judge_steps, 1e-2, relax_tol, 1.0)
     t_jump = rep["seconds"]
     # the prediction itself, for its error (the jumper now holds it advanced by the judge's steps)
@@ -627,8 +608,7 @@ def run_surrogate_on_stream(lbm, torch, stream, args, world):
                      "mass_error_of_prediction": sig(rep["mass_error"], 3),
                      "interface_shift": rep["interface_shift"], "interface_limit": rep["interface_limit"],
                      "interface_shift_of_the_lbm": sig(shift_true, 3),
-                     "relax_ratio": rep["relax_ratio"], "relax_ratio_of_the_lbm_state": sig(r0, 3),
-                     "relax_tol": relax_tol, "seconds_jump": round(t_jump, 5),
+                     "relax_ratio": rep["relax_ratio"], "relax_tol": relax_tol, "seconds_jump": round(t_jump, 5),
                      "seconds_workspace_reserve": round(t_reserve, 5),
                      "seconds_lbm_k_steps": round(t_lbm, 5), "speedup": round(t_lbm / t_jump, 3),
                      "phi_l1_error": {"surrogate": sig(err(pred, [0]), 3), "persistence": sig(err(x0, [0]), 3)},

@@ -93,8 +93,10 @@ typedef struct {
     int accepted;       /* 1: the state holds the prediction advanced by judge_steps steps;
                            0: it holds the LBM's own k steps from the starting state */
     double mass_error;  /* |sum phi of the prediction - sum phi before| / sum phi before */
-    double relax_ratio; /* how fast the LBM moves phi right after the restart, relative to the
-                           rate the prediction implies (1 = consistent); 0 if not judged */
+    double relax_ratio; /* how fast the LBM moves phi after the restart from the prediction,
+                           relative to after the same restart from the starting state's own
+                           coarse fields (1 = as consistent as the starting state); 0 if the
+                           prediction was rejected before any restart */
     double interface_shift; /* mean displacement of the interface from the starting state to the
                                prediction, in cells: f sum |phi_pred - phi_start| / sum |grad phi_start|
                                over the coarse cells (central differences in coarse cells) */
@@ -112,13 +114,13 @@ typedef struct {
  *      (see lbm_jump_report). The phi = 1/2 surface of the conservative phase field moves with
  *      the fluid, because the sharpening flux vanishes on the equilibrium profile (Sec. 2.3), so
  *      in k steps no part of it moves farther than max |u| k; interface_tol = 1 is that bound;
- *   3. restart the lattice from the prediction with sum phi held exactly;
- *   4. run judge_steps LBM steps and compare how far phi moves per step with the rate the
- *      prediction implies (|phi_after - phi_restart| / judge_steps against
- *      |phi_pred - phi_before| / k, coarse, L1, phi_restart the coarse phi right after the
- *      restart; phi_restart and phi_after are block means of the state's own phi when factor
- *      divides 32); reject if the ratio exceeds relax_tol: a prediction whose phi, u and p do
- *      not fit together relaxes fast;
+ *   3. restart the lattice from the starting state's own coarse fields, run judge_steps LBM
+ *      steps and measure how fast phi moves (|phi_after - phi_restart| / judge_steps, coarse,
+ *      L1; phi_restart the coarse phi right after the restart, both block means of the state's
+ *      own phi when factor divides 32): the relaxation a restart alone causes;
+ *   4. restart from the prediction (sum phi held exactly), measure the same, and reject if it
+ *      exceeds relax_tol times the rate of step 3: a prediction whose phi, u and p do not fit
+ *      together relaxes faster than the starting state does after the same restart;
  *   5. on rejection restore the starting state and advance it k steps with the LBM.
  * Synchronous. Needs a workspace of one more state buffer plus four coarse field arrays: the
  * first jump on a handle allocates it (or lbm_surrogate_reserve, beforehand) and the handle keeps

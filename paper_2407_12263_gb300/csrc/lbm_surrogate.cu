@@ -493,29 +493,35 @@ int lbm_surrogate_jump(lbm_ctx* c, lbm_net* n, int f, const float mean_std[10], 
     // part of it moves farther than the largest speed times k.
     rep->interface_limit = interface_tol * std::sqrt(m[3]) * k;
     bool accept = rep->mass_error <= mass_tol && rep->interface_shift <= rep->interface_limit;
-    // 3-4. restart and judge
+    // 3-4. restart and judge. How fast phi moves in the LBM's first judge_steps steps after a
+    // restart, as the L1 rate of its coarse block means: after the restart from the prediction,
+    // against the same after the restart from the starting state's own coarse fields. Both carry
+    // the relaxation a restart causes (upsampled fields are smoother than the lattice's); a
+    // prediction whose phi, u and p do not fit together relaxes faster than that.
     if (accept) {
-        if ((rc = lbm_restart_from_coarse(c, f, pred, saved_P.w0d / 3.0))) return rc;
-        // phi right after the restart (it differs from the prediction by the smoothing of
-        // upsampling and block means, which is not motion) and judge_steps steps later: block
-        // means of the state's own phi (plane 0), where the factor allows, else of the
-        // propagated state's moments
-        auto coarse_phi = [&]() {
-            if (f <= 32 && 32 % f == 0) return cu(lbm::launch_coarse_phi(c->P, c->fg[c->cur], f, in, c->stream));
-            return lbm_coarse_fields(c, f, in);
+        auto coarse_phi_into = [&](float* dst) -> int {
+            if (f <= 32 && 32 % f == 0) return cu(lbm::launch_coarse_phi(c->P, c->fg[c->cur], f, dst, c->stream));
+            return lbm_coarse_fields(c, f, dst);  // phi is channel 0 of the five it writes
         };
         std::vector<float> h_r((size_t)nc), h_after((size_t)nc);
-        if ((rc = coarse_phi())) return rc;
-        if ((rc = cu(cudaStreamSynchronize(c->stream)))) return rc;
-        if ((rc = cu(cudaMemcpy(h_r.data(), in, (size_t)nc * sizeof(float), cudaMemcpyDeviceToHost)))) return rc;
-        if ((rc = lbm_step(c, judge_steps))) return rc;
-        if ((rc = coarse_phi())) return rc;
-        if ((rc = cu(cudaStreamSynchronize(c->stream)))) return rc;
-        if ((rc = cu(cudaMemcpy(h_after.data(), in, (size_t)nc * sizeof(float), cudaMemcpyDeviceToHost)))) return rc;
-        double relax = 0.0;
-        for (long long i = 0; i < nc; ++i) relax += std::fabs((double)h_after[i] - (double)h_r[i]);
-        const double rate_pred = jump / k, rate_after = relax / judge_steps;
-        rep->relax_ratio = rate_pred > 0 ? rate_after / rate_pred : (rate_after > 0 ? INFINITY : 0.0);
+        auto restart_and_relax = [&](const float* src, double* rate) -> int {
+            int r = lbm_restart_from_coarse(c, f, src, saved_P.w0d / 3.0);
+            if (r) return r;
+            if ((r = coarse_phi_into(xin))) return r;
+            if ((r = lbm_step(c, judge_steps))) return r;
+            if ((r = coarse_phi_into(yout))) return r;
+            if ((r = cu(cudaStreamSynchronize(c->stream)))) return r;
+            if ((r = cu(cudaMemcpy(h_r.data(), xin, (size_t)nc * sizeof(float), cudaMemcpyDeviceToHost)))) return r;
+            if ((r = cu(cudaMemcpy(h_after.data(), yout, (size_t)nc * sizeof(float), cudaMemcpyDeviceToHost)))) return r;
+            double sum = 0.0;
+            for (long long i = 0; i < nc; ++i) sum += std::fabs((double)h_after[i] - (double)h_r[i]);
+            *rate = sum / judge_steps;
+            return LBM_OK;
+        };
+        double rate_ref = 0.0, rate_pred = 0.0;
+        if ((rc = restart_and_relax(in, &rate_ref))) return rc;
+        if ((rc = restart_and_relax(pred, &rate_pred))) return rc;
+        rep->relax_ratio = rate_ref > 0 ? rate_pred / rate_ref : (rate_pred > 0 ? INFINITY : 0.0);
         accept = rep->relax_ratio <= relax_tol;
     }
     // 5. fallback

@@ -417,6 +417,6 @@ def test_trained_surrogate_beats_persistence_and_is_accepted():
     assert sum(err(pred, a) for a in (1, 2, 3)) < 0.6 * sum(err(x0, a) for a in (1, 2, 3))
     s0 = g.mass()[0]
     ms = torch.cat([mean, std]).cpu().numpy().tolist()
-    rep = lbm.lbm_surrogate_jump(g.h, net, f, ms, k, 8, 1e-2, 4.0)
+    rep = lbm.lbm_surrogate_jump(g.h, net, f, ms, k, 8, 1e-2, 2.0)
     assert rep["accepted"], rep
     assert g.mass()[0] == s0
