@@ -8,13 +8,18 @@ namespace lbm {
 constexpr int kAuxBX = 32, kAuxBY = 4;
 
 // ---------------------------------------------------------------------------------------
-// Initial post-collision populations (FP64 arithmetic, stored FP32):
+// Initial post-collision populations:
 //   grad phi0 = 3 sum_{i != 0} t_i e_i phi0(x + e_i)   (isotropic central difference)
 //   n0 = grad phi0 / |grad phi0|, S0 = 4 phi0 (1 - phi0) / delta n0, rho0 = rho2 + drho phi0
 //   f*_i = f^eq_i(p0, u0, rho0, Pi_s0)                                   (Eq. geq_s)
 //   g*_i = g^eq_i(phi0, u0, S0) - t_i (tau_phi - 1/2) e_i . grad phi0     (Eq. geq)
 // The g term is the first-order non-equilibrium part a relaxed state carries after collision,
 // so the first K1 already points along -grad phi for any tau_phi.
+// The moving populations are computed in FP32, directly as deviations from the storage's
+// reference levels (the values are stored in FP32 or 16 bits anyway; GB300's FP64 rate made the
+// FP64 version of this kernel a millisecond at 128^3). Plane 0 takes the zeroth moments from
+// their closed forms in FP64: sum_i f*_i = p / cs^2 (sum_i t_i gam_i = 0 and the Pi_s term has no
+// trace over the velocity set) and sum_i g*_i = phi0 (the first moments of t_i e_i vanish).
 // ---------------------------------------------------------------------------------------
 template <int Q, int S>
 __global__ void init_kernel(const Params P, int z0, const double* __restrict__ phi0s,
@@ -26,9 +31,10 @@ __global__ void init_kernel(const Params P, int z0, const double* __restrict__ p
     if (x >= P.nx || y >= P.ny) return;
     const int nzs = gridDim.z;
     const int ls = (zl + 1) * P.nxy + y * P.nx + x;  // this cell in the staged phi0 slab
-    const double phi = phi0s[ls];
+    const double phid = phi0s[ls];
+    const float phi = (float)phid;
 
-    double gx = 0.0, gy = 0.0, gz = 0.0;
+    float gx = 0.f, gy = 0.f, gz = 0.f;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         int xx = x + Lat<Q>::cx(i), yy = y + Lat<Q>::cy(i);
@@ -36,49 +42,48 @@ __global__ void init_kernel(const Params P, int z0, const double* __restrict__ p
         xx = (P.walls & 1) ? min(max(xx, 0), P.nx - 1) : (xx + P.nx) % P.nx;
         yy = (P.walls & 2) ? min(max(yy, 0), P.ny - 1) : (yy + P.ny) % P.ny;
         const int ll = (zl + 1 + Lat<Q>::cz(i)) * P.nxy + yy * P.nx + xx;
-        const double v = Lat<Q>::wd(i) * phi0s[ll];
+        const float v = Lat<Q>::w(i) * (float)phi0s[ll];
         gx += Lat<Q>::cx(i) * v;
         gy += Lat<Q>::cy(i) * v;
         gz += Lat<Q>::cz(i) * v;
     }
-    gx *= 3.0;
-    gy *= 3.0;
-    gz *= 3.0;
-    const double g2 = gx * gx + gy * gy + gz * gz;
-    const double gn = sqrt(g2);
-    const double inv = (g2 > 1e-24) ? 1.0 / gn : 0.0;
-    const double n[3] = {gx * inv, gy * inv, gz * inv};
-    const double smag = P.four_over_delta_d * phi * (1.0 - phi);
-    const double Sv[3] = {smag * n[0], smag * n[1], smag * n[2]};
-    const double rho = P.rho2_d + P.drho_d * phi;
+    gx *= 3.f;
+    gy *= 3.f;
+    gz *= 3.f;
+    const float g2 = gx * gx + gy * gy + gz * gz;
+    const float gn = sqrtf(g2);
+    const float inv = (g2 > kNormalGuard) ? 1.0f / gn : 0.f;
+    const float n[3] = {gx * inv, gy * inv, gz * inv};
+    const float smag = P.four_over_delta * phi * (1.f - phi);
+    const float Sv[3] = {smag * n[0], smag * n[1], smag * n[2]};
+    const float rho = P.rho2 + P.drho * phi;
     const size_t slab = (size_t)nzs * P.nxy;
     const int lu = zl * P.nxy + y * P.nx + x;
-    const double u[3] = {u0s ? u0s[lu] : 0.0, u0s ? u0s[slab + lu] : 0.0, u0s ? u0s[2 * slab + lu] : 0.0};
+    const float u[3] = {u0s ? (float)u0s[lu] : 0.f, u0s ? (float)u0s[slab + lu] : 0.f, u0s ? (float)u0s[2 * slab + lu] : 0.f};
     const double pc = ps ? ps[lu] : p0;
-    const double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    const double sg = P.sigma_d * gn;
-    const double trc = (double)Lat<Q>::D - (n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    const float u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const float sg = P.sigma * gn;
+    const float trc3 = ((float)Lat<Q>::D - (n[0] * n[0] + n[1] * n[1] + n[2] * n[2])) * (1.0f / 3.0f);
+    const float dP = (float)(3.0 * pc - P.w0d);     // p / cs^2 - w0
+    const float Phi = (float)(phid - P.phi_ref_d);  // phi - phi_ref
+    const float tnq = P.tau_phi - 0.5f;
 
     const size_t c = (size_t)(z0 + zl) * P.nxy + (size_t)y * P.nx + x;
-    double fsum = 0.0, gsum = 0.0;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const double t = Lat<Q>::wd(i);
-        const double eu = Lat<Q>::cx(i) * u[0] + Lat<Q>::cy(i) * u[1] + Lat<Q>::cz(i) * u[2];
-        const double en = Lat<Q>::cx(i) * n[0] + Lat<Q>::cy(i) * n[1] + Lat<Q>::cz(i) * n[2];
-        const double es = Lat<Q>::cx(i) * Sv[0] + Lat<Q>::cy(i) * Sv[1] + Lat<Q>::cz(i) * Sv[2];
-        const double eg = Lat<Q>::cx(i) * gx + Lat<Q>::cy(i) * gy + Lat<Q>::cz(i) * gz;
-        const double gam = 3.0 * eu + 4.5 * eu * eu - 1.5 * u2;
-        const double pis = sg * ((double)Lat<Q>::e2(i) - en * en - trc / 3.0);
-        const double fstar = t * (3.0 * pc + rho * gam - 4.5 * pis);
-        const double gstar = t * (phi * (1.0 + gam) + P.tau_phi_d * es) - t * (P.tau_phi_d - 0.5) * eg;
-        fsum += fstar;
-        gsum += gstar;
-        if (i > 0)
-            Store<S>::store(moving_plane<S>(fg, P.N, i) + c, (float)(fstar - t * P.w0d), (float)(gstar - t * P.phi_ref_d), P);
+    for (int i = 1; i < Q; ++i) {
+        const float t = Lat<Q>::w(i);
+        const float eu = Lat<Q>::cx(i) * u[0] + Lat<Q>::cy(i) * u[1] + Lat<Q>::cz(i) * u[2];
+        const float en = Lat<Q>::cx(i) * n[0] + Lat<Q>::cy(i) * n[1] + Lat<Q>::cz(i) * n[2];
+        const float es = Lat<Q>::cx(i) * Sv[0] + Lat<Q>::cy(i) * Sv[1] + Lat<Q>::cz(i) * Sv[2];
+        const float eg = Lat<Q>::cx(i) * gx + Lat<Q>::cy(i) * gy + Lat<Q>::cz(i) * gz;
+        const float gam = 3.f * eu + 4.5f * eu * eu - 1.5f * u2;
+        const float pis = sg * ((float)Lat<Q>::e2(i) - en * en - trc3);
+        const float fdev = t * (dP + rho * gam - 4.5f * pis);                       // f*_i - t_i w0
+        const float gdev = t * (Phi + phi * gam + P.tau_phi * es) - t * tnq * eg;  // g*_i - t_i phi_ref
+        Store<S>::store(moving_plane<S>(fg, P.N, i) + c, fdev, gdev, P);
     }
-    // plane 0: the zeroth moments, sum f - w0 (FP32) and phi as the integer phi * 2^30
-    moment_plane(fg)[c] = make_float2((float)(fsum - P.w0d), __int_as_float((int)llrint(gsum * kPhiFx)));
+    // plane 0: the zeroth moments sum f - w0 = p / cs^2 - w0 (FP32) and phi as the integer phi * 2^30
+    moment_plane(fg)[c] = make_float2((float)(3.0 * pc - P.w0d), __int_as_float((int)llrint(phid * kPhiFx)));
 }
 
 cudaError_t launch_init(const Params& P, int z0, int nzs, const double* phi0s, const double* u0s,

@@ -69,6 +69,33 @@ void free_ctx(lbm_ctx* c) {
     delete c;
 }
 
+// Whether every value lies in [lo, hi] ((lo, hi] with open_low), NaN failing; eight independent
+// lanes so that the scan is not one long dependency chain.
+bool all_in_range(const double* v, long long n, double lo, double hi, bool open_low) {
+    bool ok[8] = {true, true, true, true, true, true, true, true};
+    long long k = 0;
+    for (; k + 8 <= n; k += 8)
+        for (int j = 0; j < 8; ++j) {
+            const double x = v[k + j];
+            ok[j] = ok[j] & (open_low ? (x > lo) : (x >= lo)) & (x <= hi) & (x - x == 0.0);
+        }
+    bool all = true;
+    for (int j = 0; j < 8; ++j) all = all && ok[j];
+    for (; k < n; ++k) all = all && (open_low ? (v[k] > lo) : (v[k] >= lo)) && v[k] <= hi && (v[k] - v[k] == 0.0);
+    return all;
+}
+
+// Sum of n values in eight interleaved partial sums added in a fixed order.
+double sum_of(const double* v, long long n) {
+    double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long k = 0;
+    for (; k + 8 <= n; k += 8)
+        for (int j = 0; j < 8; ++j) s[j] += v[k + j];
+    double t = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+    for (; k < n; ++k) t += v[k];
+    return t;
+}
+
 int ensure_staging(lbm_ctx* c, size_t elems) {
     if (c->staging_elems >= elems) return LBM_OK;
     cudaFree(c->staging);
@@ -408,20 +435,21 @@ int lbm_init_fields(lbm_ctx* c, const double* phi0, const double* u0, const doub
     if (rc) return rc;
     if (!phi0) return set_error(c, LBM_EINVAL, "phi0 is NULL");
     if (!(p0 > 0) || !is_fin(p0)) return set_error(c, LBM_EINVAL, "p0 must be > 0 and finite");
-    if (p)
-        for (long long k = 0; k < c->P.N; ++k)
+    const long long Ncells = c->P.N;
+    if (p && !all_in_range(p, Ncells, 0.0, INFINITY, /*open_low=*/true)) {
+        for (long long k = 0; k < Ncells; ++k)
             if (!(p[k] > 0) || !is_fin(p[k])) return set_error(c, LBM_EINVAL, "p[%lld] = %g must be > 0 and finite", k, p[k]);
+    }
+    if (!all_in_range(phi0, Ncells, kPhiMin, kPhiMax, false)) {
+        for (long long k = 0; k < Ncells; ++k)
+            if (!(phi0[k] >= kPhiMin && phi0[k] <= kPhiMax))
+                return set_error(c, LBM_EINVAL, "phi0[%lld] = %g outside [%g, %g]", k, phi0[k], kPhiMin, kPhiMax);
+    }
     Params& P = c->P;
     P.w0d = p0 * 3.0;  // w0 = p0 / cs^2: the level the f storage is shifted by
     P.w0 = (float)P.w0d;
     // g is stored as the deviation from the bulk phase (phi = 0 or 1) that covers most cells
-    double mean = 0.0;
-    for (long long k = 0; k < P.N; ++k) {
-        if (!(phi0[k] >= kPhiMin && phi0[k] <= kPhiMax))
-            return set_error(c, LBM_EINVAL, "phi0[%lld] = %g outside [%g, %g]", k, phi0[k], kPhiMin, kPhiMax);
-        mean += phi0[k];
-    }
-    mean /= (double)P.N;
+    const double mean = sum_of(phi0, Ncells) / (double)Ncells;
     P.phi_ref_d = (mean >= 0.5) ? 1.0 : 0.0;
     P.phi_ref = (float)P.phi_ref_d;
     P.phi_ref_fx = (mean >= 0.5) ? (1 << 30) : 0;
@@ -436,14 +464,17 @@ int lbm_init_fields(lbm_ctx* c, const double* phi0, const double* u0, const doub
     double* ps = us + (u0 ? (size_t)3 * nzs * nxy : 0);
     for (int z0 = 0; z0 < P.nz; z0 += nzs) {
         const int n = (z0 + nzs <= P.nz) ? nzs : P.nz - z0;
-        // phi0 planes z0-1 .. z0+n (periodic images at the ends); D2Q9 has only its one plane
-        const int lo = (P.Q == 9) ? 0 : -1, hi = (P.Q == 9) ? n - 1 : n;
-        for (int l = lo; l <= hi; ++l) {
-            // periodic image, or across a z wall the mirror image (zero normal gradient)
-            const int z = (P.walls & 4) ? std::min(std::max(z0 + l, 0), P.nz - 1) : ((z0 + l) % P.nz + P.nz) % P.nz;
-            LBM_CUDA(c, cudaMemcpyAsync(phis + (size_t)(l + 1) * nxy, phi0 + (size_t)z * nxy, nxy * sizeof(double),
-                                        cudaMemcpyHostToDevice, c->stream));
-        }
+        // phi0 planes z0-1 .. z0+n: the slab's own planes in one copy, and the two halo planes,
+        // periodic images or across a z wall the mirror image (zero normal gradient); D2Q9 has
+        // only its one plane
+        LBM_CUDA(c, cudaMemcpyAsync(phis + nxy, phi0 + (size_t)z0 * nxy, (size_t)n * nxy * sizeof(double),
+                                    cudaMemcpyHostToDevice, c->stream));
+        if (P.Q != 9)
+            for (int l : {-1, n}) {
+                const int z = (P.walls & 4) ? std::min(std::max(z0 + l, 0), P.nz - 1) : ((z0 + l) % P.nz + P.nz) % P.nz;
+                LBM_CUDA(c, cudaMemcpyAsync(phis + (size_t)(l + 1) * nxy, phi0 + (size_t)z * nxy, nxy * sizeof(double),
+                                            cudaMemcpyHostToDevice, c->stream));
+            }
         if (u0)
             for (int a = 0; a < 3; ++a)
                 LBM_CUDA(c, cudaMemcpyAsync(us + (size_t)a * n * nxy, u0 + (size_t)a * P.N + (size_t)z0 * nxy,
