@@ -290,6 +290,34 @@ cudaError_t launch_phi_fixed_sum(const Params& P, const void* fg, double* partia
     return cudaGetLastError();
 }
 
+// Validation of host input staged on the device: per block, the number of values outside
+// [lo, hi] ((lo, hi] with open_low; NaN and infinities count as outside) and the sum of the
+// values, in partials[2 b], partials[2 b + 1]. Each block sums its grid-stride elements in a
+// fixed order and the tree of block_sum is fixed, so the partials are the same bits on every run.
+__global__ void __launch_bounds__(kRedThreads)
+check_values_kernel(const double* __restrict__ v, long long n, double lo, double hi, int open_low,
+                    double* __restrict__ partials) {
+    long long unused = 0;
+    double acc[2] = {0.0, 0.0};
+    for (long long i = (long long)blockIdx.x * kRedThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kRedThreads) {
+        const double x = v[i];
+        const bool ok = (open_low ? (x > lo) : (x >= lo)) && x <= hi && isfinite(x);
+        acc[0] += ok ? 0.0 : 1.0;
+        acc[1] += x;
+    }
+    block_sum(unused, acc);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = acc[0];
+        partials[2 * blockIdx.x + 1] = acc[1];
+    }
+}
+
+cudaError_t launch_check_values(const double* v, long long n, double lo, double hi, int open_low, double* partials,
+                                int n_blocks, cudaStream_t s) {
+    check_values_kernel<<<n_blocks, kRedThreads, 0, s>>>(v, n, lo, hi, open_low, partials);
+    return cudaGetLastError();
+}
+
 int mass_partials_needed(const Params& P) {
     const long long blocks = (P.N + kRedThreads - 1) / kRedThreads;
     return (int)(blocks < 1024 ? blocks : 1024);

@@ -11,6 +11,7 @@
 #include <cstring>
 #include <algorithm>
 #include <new>
+#include <vector>
 
 #include "../../include/lbm.h"
 #include "lattice.cuh"
@@ -67,33 +68,6 @@ void free_ctx(lbm_ctx* c) {
         if (c->graph_exec[k]) cudaGraphExecDestroy(c->graph_exec[k]);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
-}
-
-// Whether every value lies in [lo, hi] ((lo, hi] with open_low), NaN failing; eight independent
-// lanes so that the scan is not one long dependency chain.
-bool all_in_range(const double* v, long long n, double lo, double hi, bool open_low) {
-    bool ok[8] = {true, true, true, true, true, true, true, true};
-    long long k = 0;
-    for (; k + 8 <= n; k += 8)
-        for (int j = 0; j < 8; ++j) {
-            const double x = v[k + j];
-            ok[j] = ok[j] & (open_low ? (x > lo) : (x >= lo)) & (x <= hi) & (x - x == 0.0);
-        }
-    bool all = true;
-    for (int j = 0; j < 8; ++j) all = all && ok[j];
-    for (; k < n; ++k) all = all && (open_low ? (v[k] > lo) : (v[k] >= lo)) && v[k] <= hi && (v[k] - v[k] == 0.0);
-    return all;
-}
-
-// Sum of n values in eight interleaved partial sums added in a fixed order.
-double sum_of(const double* v, long long n) {
-    double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    long long k = 0;
-    for (; k + 8 <= n; k += 8)
-        for (int j = 0; j < 8; ++j) s[j] += v[k + j];
-    double t = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
-    for (; k < n; ++k) t += v[k];
-    return t;
 }
 
 int ensure_staging(lbm_ctx* c, size_t elems) {
@@ -435,30 +409,62 @@ int lbm_init_fields(lbm_ctx* c, const double* phi0, const double* u0, const doub
     if (rc) return rc;
     if (!phi0) return set_error(c, LBM_EINVAL, "phi0 is NULL");
     if (!(p0 > 0) || !is_fin(p0)) return set_error(c, LBM_EINVAL, "p0 must be > 0 and finite");
-    const long long Ncells = c->P.N;
-    if (p && !all_in_range(p, Ncells, 0.0, INFINITY, /*open_low=*/true)) {
-        for (long long k = 0; k < Ncells; ++k)
-            if (!(p[k] > 0) || !is_fin(p[k])) return set_error(c, LBM_EINVAL, "p[%lld] = %g must be > 0 and finite", k, p[k]);
-    }
-    if (!all_in_range(phi0, Ncells, kPhiMin, kPhiMax, false)) {
-        for (long long k = 0; k < Ncells; ++k)
-            if (!(phi0[k] >= kPhiMin && phi0[k] <= kPhiMax))
-                return set_error(c, LBM_EINVAL, "phi0[%lld] = %g outside [%g, %g]", k, phi0[k], kPhiMin, kPhiMax);
-    }
     Params& P = c->P;
-    P.w0d = p0 * 3.0;  // w0 = p0 / cs^2: the level the f storage is shifted by
-    P.w0 = (float)P.w0d;
-    // g is stored as the deviation from the bulk phase (phi = 0 or 1) that covers most cells
-    const double mean = sum_of(phi0, Ncells) / (double)Ncells;
-    P.phi_ref_d = (mean >= 0.5) ? 1.0 : 0.0;
-    P.phi_ref = (float)P.phi_ref_d;
-    P.phi_ref_fx = (mean >= 0.5) ? (1 << 30) : 0;
-    drop_graphs(c);  // captured steps carry the old parameters
+    const long long Ncells = P.N;
     const size_t nxy = (size_t)P.nxy;
     const int per_z = 1 + (u0 ? 3 : 0) + (p ? 1 : 0);
     const int nzs = slab_depth(c, per_z, 2);
     rc = ensure_staging(c, (size_t)(nzs + 2 + (u0 ? 3 * nzs : 0) + (p ? nzs : 0)) * nxy);
     if (rc) return rc;
+    // Pass 1, before anything is written: every phi0 in [kPhiMin, kPhiMax] and every p > 0 and
+    // finite, and the sum of phi0, checked on the device slab by slab (block partials added on
+    // the host in a fixed order). Only when a value fails is the host array searched for it.
+    double mean = 0.0;
+    {
+        const int nb = std::max(1, std::min(3 * c->n_partials / 2, 1024));
+        std::vector<double> part(2 * (size_t)nb);
+        double sum = 0.0, bad_phi = 0.0, bad_p = 0.0;
+        auto check = [&](const double* dev, long long n, double lo, double hi, int open_low, double* bad,
+                         double* total) -> int {
+            LBM_CUDA(c, lbm::launch_check_values(dev, n, lo, hi, open_low, c->partials, nb, c->stream));
+            LBM_CUDA(c, cudaMemcpyAsync(part.data(), c->partials, part.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                        c->stream));
+            LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+            for (int b = 0; b < nb; ++b) {
+                *bad += part[2 * b];
+                if (total) *total += part[2 * b + 1];
+            }
+            return LBM_OK;
+        };
+        for (int z0 = 0; z0 < P.nz; z0 += nzs) {
+            const int n = (z0 + nzs <= P.nz) ? nzs : P.nz - z0;
+            const size_t cells = (size_t)n * nxy;
+            LBM_CUDA(c, cudaMemcpyAsync(c->staging, phi0 + (size_t)z0 * nxy, cells * sizeof(double), cudaMemcpyHostToDevice,
+                                        c->stream));
+            if ((rc = check(c->staging, (long long)cells, kPhiMin, kPhiMax, 0, &bad_phi, &sum))) return rc;
+            if (p) {
+                LBM_CUDA(c, cudaMemcpyAsync(c->staging, p + (size_t)z0 * nxy, cells * sizeof(double), cudaMemcpyHostToDevice,
+                                            c->stream));
+                if ((rc = check(c->staging, (long long)cells, 0.0, INFINITY, 1, &bad_p, nullptr))) return rc;
+            }
+        }
+        if (bad_p > 0)
+            for (long long k = 0; k < Ncells; ++k)
+                if (!(p[k] > 0) || !is_fin(p[k])) return set_error(c, LBM_EINVAL, "p[%lld] = %g must be > 0 and finite", k, p[k]);
+        if (bad_phi > 0)
+            for (long long k = 0; k < Ncells; ++k)
+                if (!(phi0[k] >= kPhiMin && phi0[k] <= kPhiMax))
+                    return set_error(c, LBM_EINVAL, "phi0[%lld] = %g outside [%g, %g]", k, phi0[k], kPhiMin, kPhiMax);
+        if (bad_p > 0 || bad_phi > 0) return set_error(c, LBM_EINVAL, "non-finite phi0 or p");
+        mean = sum / (double)Ncells;
+    }
+    P.w0d = p0 * 3.0;  // w0 = p0 / cs^2: the level the f storage is shifted by
+    P.w0 = (float)P.w0d;
+    // g is stored as the deviation from the bulk phase (phi = 0 or 1) that covers most cells
+    P.phi_ref_d = (mean >= 0.5) ? 1.0 : 0.0;
+    P.phi_ref = (float)P.phi_ref_d;
+    P.phi_ref_fx = (mean >= 0.5) ? (1 << 30) : 0;
+    drop_graphs(c);  // captured steps carry the old parameters
     double* phis = c->staging;
     double* us = c->staging + (size_t)(nzs + 2) * nxy;
     double* ps = us + (u0 ? (size_t)3 * nzs * nxy : 0);

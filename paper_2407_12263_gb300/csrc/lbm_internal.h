@@ -71,6 +71,11 @@ cudaError_t launch_moments(const Params& P, int scheme, int z0, int nzs, const v
 cudaError_t launch_mass(const Params& P, const void* fg, double* partials, int n_partials,
                         double* result /* 4 doubles */, cudaStream_t s);
 int mass_partials_needed(const Params& P);
+// Per block b < n_blocks: the count of
+// values of v[0, n) outside [lo, hi] ((lo, hi] with open_low; non-finite values count) and their
+// sum, in partials[2 b] and partials[2 b + 1]; fixed order, the same bits on every run.
+cudaError_t launch_check_values(const double* v, long long n, double lo, double hi, int open_low, double* partials,
+                                int n_blocks, cudaStream_t s);
 // Only result[3] of launch_mass (the exact fixed-point sum of phi), from plane 0 alone.
 cudaError_t launch_phi_fixed_sum(const Params& P, const void* fg, double* partials, int n_partials,
                                  double* result /* 4 doubles */, cudaStream_t s);

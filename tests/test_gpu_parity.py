@@ -203,8 +203,36 @@ def test_full_size_droplet_parity():
 
 
 # ---------------------------------------------------------------- edge cases
+def _noisy_twin_phi_divergence(Q, grid, phi0, u0, steps, seeds=2):
+    """How far an FP64 oracle run with FP32-sized noise (relative 6e-8, uniform) added to every
+    population after every step drifts from the noise-free run in phi: the trajectory's own
+    amplification of rounding, the most an FP32 run can be asked to stay within."""
+    base = dict(tau_f=0.8, tau_g=0.8, M=0.02, xi=4.0, sigma=1e-3)
+    ref = O.Oracle(Q, grid, **base)
+    ref.init_phi(phi0, u0)
+    ref.step(steps)
+    phi_o = ref.moments()[0]
+    worst = 0.0
+    for seed in range(seeds):
+        tw = O.Oracle(Q, grid, **base)
+        tw.init_phi(phi0, u0)
+        rng = np.random.default_rng(100 + seed)
+        for _ in range(steps):
+            f, g = tw.get_pops()
+            tw.set_pops(f * (1 + 6e-8 * rng.uniform(-1, 1, f.shape)), g * (1 + 6e-8 * rng.uniform(-1, 1, g.shape)))
+            tw.step(1)
+        worst = max(worst, float(np.abs(tw.moments()[0] - phi_o).max()))
+    return worst
+
+
 @pytest.mark.parametrize("Q,grid", [(9, (3, 3, 1)), (19, (3, 3, 3)), (19, (3, 5, 4)), (9, (3, 200, 1))])
 def test_minimum_grids(Q, grid):
+    """A sine phi field with no interface: phi (1 - phi) stays near 0.2, so the sharpening flux is
+    not small anywhere, while at the sine's extrema K1 nearly vanishes and n = -K1/|K1| is the
+    direction of a near-zero vector (reading R6). On the 3 x 200 grid that amplifies rounding:
+    an FP64 run with FP32-sized noise every step drifts by up to ~1.5e-4 in phi within 30 steps.
+    The phi bound is therefore the larger of the fixed one and three times that drift, measured
+    here; on the other grids the drift is ~1e-8 and the fixed bound applies."""
     phi0 = I.sine_phi(grid, 0.5, 0.3, axis=1)
     u0 = I.smooth_velocity(grid, seed=41, amplitude=0.02)
     if Q == 9:
@@ -212,9 +240,15 @@ def test_minimum_grids(Q, grid):
     gpu, ref = _pair(Q, grid, phi0, u0)
     gpu.step(30)
     ref.step(30)
+    phi_g, p_g, u_g = gpu.moments()
+    phi_o, p_o, u_o = ref.moments()
+    tol = max(PHI_TOL, 3 * _noisy_twin_phi_divergence(Q, grid, phi0, u0, 30))
+    assert np.abs(phi_g - phi_o).max() <= tol
     # on a 3-cell extent the short-wave flow decays to ~1e-7 within these steps: the velocity
     # bound is taken relative to the initial amplitude 0.02 there
-    _compare(gpu, ref, u_abs=1e-3 * 0.02 * 1e-3)
+    nu = np.linalg.norm(u_o)
+    assert np.linalg.norm(u_g - u_o) / nu <= U_REL_TOL or np.abs(u_g - u_o).max() <= 1e-3 * 0.02 * 1e-3
+    assert np.abs(p_g - p_o).max() <= 1e-6
 
 
 def test_zero_steps_and_state_errors():
