@@ -523,13 +523,16 @@ def run_surrogate_on_stream(lbm, torch, stream, args, world):
     (coarsened 4x to 64^3; k = 200 steps, the same jump in units of L0 / u0) with the LBM as judge.
     Reported beside 200 LBM steps: wall time, and the coarse phi and u errors against the LBM's
     own state, with persistence (the starting state) as the reference."""
-    f_train, k_train, n_train = 2, 100, 128
+    # training trajectories on the workload's own grid (f = 4, k = 200) or on a 128^3 copy (f = 2,
+    # k = 100, the same jump in units of L0 / u0 and the same coarse grid)
+    n_train = args.surrogate_train_grid
+    f_train, k_train = (4, 200) if n_train == 256 else (2, 100)
     rng = np.random.default_rng(12263)
     coarse = lambda g, f: _coarse_fields(lbm, torch, g, f)
     t0 = time.perf_counter()
     xs, ys = [], []
     for s in range(6):
-        c = tgv_case(n_train, rng.uniform(0.03, 0.05), rng.uniform(12.0, 20.0), rng.uniform(10.0, 30.0))
+        c = tgv_case(n_train, rng.uniform(0.03, 0.05), rng.uniform(12.0, 20.0) * n_train / 128, rng.uniform(10.0, 30.0))
         g = tgv_lattice(lbm, c, stream, lbm.LBM_STORAGE_FP16)
         prev = coarse(g, f_train)
         for _ in range(30):
@@ -600,7 +603,7 @@ def run_surrogate_on_stream(lbm, torch, stream, args, world):
     pred = y[0] * std[:, None, None, None] + mean[:, None, None, None]
     torch.cuda.synchronize()
     err = lambda a, chans: float(sum((a[ch] - xt[ch]).abs().mean() for ch in chans))
-    out = {"train": {"grid": [n_train] * 3, "trajectories": 6, "pairs": len(xs), "k": k_train, "coarse": 64,
+    out = {"train": {"grid": [n_train] * 3, "trajectories": 6, "pairs": len(xs), "k": k_train, "factor": f_train,
                      "iterations": iters, "batch": batch, "loss_first": sig(first), "loss_last": sig(last),
                      "seconds_data": round(t_data, 2), "seconds_train": round(t_train, 2)},
            "apply": {"grid": [256] * 3, "storage": "fp16", "start_step": 1600, "k": k, "factor": f,
@@ -913,6 +916,8 @@ def main(argv=None):
     ap.add_argument("--batch-cases", type=int, default=256,
                     help="rising-bubble cases of the batched leg (the first N of the seeded 256)")
     ap.add_argument("--surrogate-iters", type=int, default=1500, help="training iterations of the surrogate leg")
+    ap.add_argument("--surrogate-train-grid", type=int, default=128, choices=[128, 256],
+                    help="grid of the surrogate's training trajectories")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=90.0)
     args = ap.parse_args(argv)
