@@ -68,3 +68,25 @@ def test_bench_rejects_too_few_warmup_steps():
     r = subprocess.run([sys.executable, str(ROOT / "bench.py"), "--warmup", "2"], capture_output=True, text=True,
                        timeout=120, cwd=ROOT)
     assert r.returncode != 0 and "warmup" in r.stderr
+
+
+@pytest.mark.parametrize("warmup,steps,want", [(5, 20, 4), (3, 20, 2), (50, 10000, 20), (5, 7, 0), (4, 20, 4),
+                                               (3, 3, 0), (6, 30, 6), (64, 64, 32)])
+def test_headline_graph_steps(warmup, steps, want):
+    """The headline's graph length: even, at most 32, replayable once within the warm-up (so the
+    warm-up captures it) and a divisor of --steps; 0 (direct launches) when none exists."""
+    sys.path.insert(0, str(ROOT))
+    import bench
+    gs = bench.headline_graph_steps(warmup, steps)
+    assert gs == want
+    if gs:
+        assert gs % 2 == 0 and gs <= 32 and steps % gs == 0 and gs <= warmup - warmup % 2
+
+
+def test_summary_rounding_keeps_significant_digits():
+    sys.path.insert(0, str(ROOT))
+    import bench
+    assert bench.sig(21688.43) == 21690.0
+    assert bench.sig(0.000123456, 2) == 0.00012
+    assert bench.sig(0.0) == 0.0 and bench.sig(None) is None
+    assert bench.sig(float("inf")) == float("inf")

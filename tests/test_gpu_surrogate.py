@@ -218,6 +218,25 @@ def test_coarse_fields_are_block_means():
     np.testing.assert_allclose(got, want, rtol=0, atol=2e-7)
 
 
+@pytest.mark.parametrize("f", [2, 4])
+def test_coarse_phi_is_the_block_mean_of_the_state_phi(f):
+    """lbm_coarse_phi: block means of the state's own phi (sum_i g*_i, before propagation), the
+    quantity the judge measures; the factor must divide 32."""
+    c = _tgv_case(16, 0.04, 4.0, 20.0)
+    g = _tgv_lattice(c)
+    g.step(7)
+    out = torch.empty((16 // f,) * 3, device="cuda")
+    torch.cuda.synchronize()
+    lbm.lbm_coarse_phi(g.h, f, out.data_ptr())
+    torch.cuda.synchronize()
+    phis = g.get_pops()[1].sum(0)
+    n = 16 // f
+    want = phis.reshape(n, f, n, f, n, f).mean(axis=(1, 3, 5))
+    np.testing.assert_allclose(out.cpu().numpy(), want, rtol=0, atol=1e-7)
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_coarse_phi(g.h, 3, out.data_ptr())
+
+
 def test_restart_holds_sum_phi_exactly():
     c = _tgv_case(16, 0.04, 4.0, 20.0)
     g = _tgv_lattice(c)
