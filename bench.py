@@ -369,7 +369,8 @@ def summary(value, df_long, fd, sixteen, bubbles, laplace, acc, rt_acc, tgv, rt,
         a = sg["apply"]
         s["surrogate"] = {"accepted": a["accepted"], "x": a["speedup"], "shift": sig(a["interface_shift"], 3),
                           "limit": sig(a["interface_limit"], 3), "relax": sig(a["relax_ratio"], 3),
-                          "relax_tol": sig(a["relax_tol"], 3)}
+                          "relax_tol": sig(a["relax_tol"], 3), "projected": a["velocity_projected"],
+                          "phi_err": [a["phi_l1_error"]["surrogate"], a["phi_l1_error"]["persistence"]]}
     return s
 
 
@@ -521,6 +522,7 @@ def run_surrogate_on_stream(lbm, torch, stream, args, world):
     of this solver (FP16 storage, Re = 1000, seeded u0 in [0.03, 0.05], We in [10, 30], R in
     [12, 20]; pairs 100 steps apart coarsened 2x to 64^3), then applied to the 256^3 workload
     (coarsened 4x to 64^3; k = 200 steps, the same jump in units of L0 / u0) with the LBM as judge.
+    The jump replaces the predicted velocity by its divergence-free part before the restart.
     Reported beside 200 LBM steps: wall time, and the coarse phi and u errors against the LBM's
     own state, with persistence (the starting state) as the reference."""
     # training trajectories on the workload's own grid (f = 4, k = 200) or on a 128^3 copy (f = 2,
@@ -601,6 +603,15 @@ def run_surrogate_on_stream(lbm, torch, stream, args, world):
     y = torch.empty_like(xin)
     net.forward(xin.data_ptr(), y.data_ptr(), 1, tuple(int(v) for v in x0.shape[1:][::-1]))
     pred = y[0] * std[:, None, None, None] + mean[:, None, None, None]
+    # the velocity the lattice restarts from: the prediction's divergence-free part
+    pred_p = pred.clone().contiguous()
+    grid_c = tuple(int(v) for v in x0.shape[1:][::-1])
+    wb = lbm.lbm_project_workspace_bytes(grid_c)
+    work = torch.empty(wb, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    if lbm.lbm_project_solenoidal(pred_p.data_ptr() + pred_p[0].numel() * 4, grid_c, work.data_ptr(), wb,
+                                  torch.cuda.current_stream().cuda_stream) != lbm.LBM_OK:
+        raise RuntimeError("lbm_project_solenoidal failed")
     torch.cuda.synchronize()
     err = lambda a, chans: float(sum((a[ch] - xt[ch]).abs().mean() for ch in chans))
     out = {"train": {"grid": [n_train] * 3, "trajectories": 6, "pairs": len(xs), "k": k_train, "factor": f_train,
@@ -608,6 +619,7 @@ def run_surrogate_on_stream(lbm, torch, stream, args, world):
                      "seconds_data": round(t_data, 2), "seconds_train": round(t_train, 2)},
            "apply": {"grid": [256] * 3, "storage": "fp16", "start_step": 1600, "k": k, "factor": f,
                      "judge_steps": judge_steps, "accepted": rep["accepted"],
+                     "velocity_projected": rep["projected"],
                      "mass_error_of_prediction": sig(rep["mass_error"], 3),
                      "interface_shift": rep["interface_shift"], "interface_limit": rep["interface_limit"],
                      "interface_shift_of_the_lbm": sig(shift_true, 3),
@@ -615,7 +627,8 @@ def run_surrogate_on_stream(lbm, torch, stream, args, world):
                      "seconds_workspace_reserve": round(t_reserve, 5),
                      "seconds_lbm_k_steps": round(t_lbm, 5), "speedup": round(t_lbm / t_jump, 3),
                      "phi_l1_error": {"surrogate": sig(err(pred, [0]), 3), "persistence": sig(err(x0, [0]), 3)},
-                     "u_l1_error": {"surrogate": sig(err(pred, [1, 2, 3]), 3),
+                     "u_l1_error": {"surrogate": sig(err(pred_p, [1, 2, 3]), 3),
+                                    "surrogate_unprojected": sig(err(pred, [1, 2, 3]), 3),
                                     "persistence": sig(err(x0, [1, 2, 3]), 3)},
                      "sum_phi_change": jumper.mass()[0] - s0}}
     truth.close()

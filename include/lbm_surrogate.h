@@ -89,6 +89,26 @@ int lbm_coarse_phi(lbm_ctx *ctx, int factor, float *out);
  * before the call (the difference, in units of 2^-30, spread over the cells). */
 int lbm_restart_from_coarse(lbm_ctx *ctx, int factor, const float *coarse, double p0);
 
+/* The divergence-free part of a periodic velocity field: the field closest to u in the sum of
+ * squares over all cells and components whose central-difference divergence
+ *   div u = sum_a (u_a(x + e_a) - u_a(x - e_a)) / 2
+ * vanishes (the orthogonal projection onto the kernel of div; u minus it is a central-difference
+ * gradient). At low Mach number the flow is divergence-free (Sec. 2.1, with the pressure
+ * evolution equation), and a lattice restarted from a compressive velocity relaxes it away
+ * through pressure waves; lbm_surrogate_jump applies this to the predicted velocity.
+ * Evaluated per Fourier mode, U <- U - s (s . U) / |s|^2 with s_a = sin(2 pi k_a / n_a) (modes with
+ * s = 0 are kept), between a forward and an inverse discrete Fourier transform along each axis,
+ * as direct sums in FP32 in a fixed order: the same bits on every run.
+ * u: device FP32 [3][nz][ny][nx] (components x, y, z, x fastest), replaced in place; grid
+ * (nx, ny, nz), each extent 1 .. 512; work: device scratch of at least
+ * lbm_project_workspace_bytes(grid) bytes (caller-owned; nothing is allocated), 16-byte
+ * aligned; stream: cudaStream_t or NULL (the legacy default stream). Asynchronous: 9
+ * kernel launches on the stream. Returns LBM_EINVAL for a NULL pointer, an extent outside
+ * 1 .. 512, a misaligned pointer or too small a workspace (nothing is launched), LBM_ECUDA if a
+ * launch fails. */
+long long lbm_project_workspace_bytes(const int grid[3]); /* -1 for an invalid grid */
+int lbm_project_solenoidal(float *u, const int grid[3], void *work, long long work_bytes, void *stream);
+
 typedef struct {
     int accepted;       /* 1: the state holds the prediction advanced by judge_steps steps;
                            0: it holds the LBM's own k steps from the starting state */
@@ -103,12 +123,15 @@ typedef struct {
     double interface_limit; /* the largest shift accepted: interface_tol * k * the largest speed
                                |u| of the starting and the predicted coarse fields */
     double seconds_surrogate; /* host wall time of the jump, judge included */
+    int projected;      /* 1 if the predicted velocity was replaced by its divergence-free part
+                           (grids periodic in every axis), 0 if it was used as predicted */
 } lbm_jump_report;
 
 /*
  * Fast-forward k steps with the surrogate, judged by the LBM:
  *   1. coarsen the state by `factor`, normalise with mean_std (5 means, then 5 stds), predict,
- *      denormalise;
+ *      denormalise; on a grid without walls (coarse extents at most 512), replace the predicted
+ *      velocity by its divergence-free part (lbm_project_solenoidal);
  *   2. reject if the prediction's sum phi is off by more than mass_tol (relative), or if its
  *      interface moved farther than the flow can carry it: interface_shift > interface_limit
  *      (see lbm_jump_report). The phi = 1/2 surface of the conservative phase field moves with
@@ -122,7 +145,8 @@ typedef struct {
  *      exceeds relax_tol times the rate of step 3: a prediction whose phi, u and p do not fit
  *      together relaxes faster than the starting state does after the same restart;
  *   5. on rejection restore the starting state and advance it k steps with the LBM.
- * Synchronous. Needs a workspace of one more state buffer plus four coarse field arrays: the
+ * Synchronous. Needs a workspace of one more state buffer, four coarse field arrays and the
+ * projection's scratch (lbm_project_workspace_bytes of the coarse grid): the
  * first jump on a handle allocates it (or lbm_surrogate_reserve, beforehand) and the handle keeps
  * it until lbm_destroy, so later jumps allocate nothing.
  */

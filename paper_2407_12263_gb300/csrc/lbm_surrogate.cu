@@ -403,14 +403,23 @@ int lbm_restart_from_coarse(lbm_ctx* c, int f, const float* coarse, double p0) {
 
 namespace {
 
+// Whether the jump projects the predicted velocity: a grid without walls whose coarse extents
+// the projection takes.
+bool jump_projects(const lbm_ctx* c, int f) {
+    const int grid_c[3] = {c->P.nx / f, c->P.ny / f, c->P.nz / f};
+    return c->P.walls == 0 && lbm::project_extents_ok(grid_c);
+}
+
 // Carves the jump's buffers out of the handle's workspace, growing it if it is too small: a
-// backup state, four coarse field arrays and the judge's four FP64 measures.
-int jump_workspace(lbm_ctx* c, int f, void** backup, float* fields[4], double** measures) {
+// backup state, four coarse field arrays, the judge's four FP64 measures and the projection's
+// scratch (*proj, NULL when the jump does not project).
+int jump_workspace(lbm_ctx* c, int f, void** backup, float* fields[4], double** measures, void** proj) {
     const long long nc = (long long)(c->P.nx / f) * (c->P.ny / f) * (c->P.nz / f);
     const size_t align = 256;
     const size_t sb = (c->fg_bytes + align - 1) / align * align;
     const size_t fb = ((size_t)5 * nc * sizeof(float) + align - 1) / align * align;
-    const size_t need = sb + 4 * fb + align;
+    const size_t pb = jump_projects(c, f) ? lbm::project_workspace_bytes(c->P.nx / f, c->P.ny / f, c->P.nz / f) : 0;
+    const size_t need = sb + 4 * fb + align + pb;
     if (c->jump_ws_bytes < need) {
         cudaFree(c->jump_ws);
         c->jump_ws = nullptr;
@@ -423,6 +432,7 @@ int jump_workspace(lbm_ctx* c, int f, void** backup, float* fields[4], double** 
     *backup = base;
     for (int i = 0; i < 4; ++i) fields[i] = reinterpret_cast<float*>(base + sb + i * fb);
     *measures = reinterpret_cast<double*>(base + sb + 4 * fb);
+    *proj = pb ? base + sb + 4 * fb + align : nullptr;
     return LBM_OK;
 }
 
@@ -436,7 +446,8 @@ int lbm_surrogate_reserve(lbm_ctx* c, int f) {
     void* backup;
     float* fields[4];
     double* measures;
-    return jump_workspace(c, f, &backup, fields, &measures);
+    void* proj;
+    return jump_workspace(c, f, &backup, fields, &measures, &proj);
 }
 
 int lbm_surrogate_jump(lbm_ctx* c, lbm_net* n, int f, const float mean_std[10], int k, int judge_steps, double mass_tol,
@@ -456,7 +467,8 @@ int lbm_surrogate_jump(lbm_ctx* c, lbm_net* n, int f, const float mean_std[10], 
     void* backup;
     float* fields[4];
     double* measures;
-    if ((rc = jump_workspace(c, f, &backup, fields, &measures))) return rc;
+    void* proj;
+    if ((rc = jump_workspace(c, f, &backup, fields, &measures, &proj))) return rc;
     float *in = fields[0], *xin = fields[1], *yout = fields[2], *pred = fields[3];
     auto cu = [&](cudaError_t e) { return e == cudaSuccess ? LBM_OK : lbm::ctx_error(c, LBM_ECUDA, cudaGetErrorString(e)); };
     const int saved_cur = c->cur;
@@ -472,6 +484,13 @@ int lbm_surrogate_jump(lbm_ctx* c, lbm_net* n, int f, const float mean_std[10], 
     if ((rc = cu(lbm::launch_normalize(yout, pred, nc, mean_std, -1, n->stream)))) return rc;
     if ((rc = cu(cudaStreamSynchronize(n->stream)))) return rc;
     if ((rc = check_tc(n))) return lbm::ctx_error(c, rc, lbm_net_last_error(n));
+    // the predicted velocity (channels 1-3) replaced by its divergence-free part
+    if (proj) {
+        if ((rc = cu(lbm::launch_project_solenoidal(pred + nc, grid_c[0], grid_c[1], grid_c[2], proj, c->stream))))
+            return rc;
+        c->launches += 9;
+        rep->projected = 1;
+    }
     // 2. mass and interface position of the prediction, measured on the coarse grid
     if ((rc = cu(cudaMemsetAsync(measures, 0, 4 * sizeof(double), c->stream)))) return rc;
     if ((rc = cu(lbm::launch_jump_measures(in, pred, grid_c[0], grid_c[1], grid_c[2], c->P.walls, measures, c->stream))))

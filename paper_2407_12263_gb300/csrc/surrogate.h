@@ -83,6 +83,11 @@ cudaError_t launch_adjust_phi(const Params& P, void* fg, long long delta, cudaSt
 //   out[3]  = max(out[3], largest |u|^2 of start and prediction) (as non-negative double bits).
 cudaError_t launch_jump_measures(const float* start, const float* pred, int ncx, int ncy, int ncz, int walls, double* out,
                                  cudaStream_t s);
+// The divergence-free part of the periodic velocity u [3][nz][ny][nx] in place
+// (lbm_project_solenoidal); work holds project_workspace_bytes() bytes, 16-byte aligned.
+cudaError_t launch_project_solenoidal(float* u, int nx, int ny, int nz, void* work, cudaStream_t s);
+size_t project_workspace_bytes(int nx, int ny, int nz);
+bool project_extents_ok(const int grid[3]);  // every extent in 1 .. 512
 // (x - mean[c]) / std[c] per channel of [5][n] (dir = +1) or x std[c] + mean[c] (dir = -1).
 cudaError_t launch_normalize(const float* x, float* y, long long n, const float* mean_std, int dir, cudaStream_t s);
 

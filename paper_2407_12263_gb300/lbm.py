@@ -45,7 +45,7 @@ class lbm_batch_opts(ctypes.Structure):
 class lbm_jump_report(ctypes.Structure):
     _fields_ = [("accepted", ctypes.c_int), ("mass_error", ctypes.c_double), ("relax_ratio", ctypes.c_double),
                 ("interface_shift", ctypes.c_double), ("interface_limit", ctypes.c_double),
-                ("seconds_surrogate", ctypes.c_double)]
+                ("seconds_surrogate", ctypes.c_double), ("projected", ctypes.c_int)]
 
 
 class LBMError(RuntimeError):
@@ -109,6 +109,9 @@ SIGNATURES = [
                                           ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.POINTER(lbm_jump_report)]),
     ("lbm_surrogate_reserve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("lbm_project_workspace_bytes", ctypes.c_longlong, [_ip]),
+    ("lbm_project_solenoidal", ctypes.c_int, [ctypes.c_void_p, _ip, ctypes.c_void_p, ctypes.c_longlong,
+                                              ctypes.c_void_p]),
 ]
 
 _lib = None
@@ -563,4 +566,17 @@ def lbm_surrogate_jump(h, net, factor, mean_std, k, judge_steps, mass_tol, relax
                                         float(relax_tol), float(interface_tol), ctypes.byref(rep)))
     return {"accepted": bool(rep.accepted), "mass_error": rep.mass_error, "relax_ratio": rep.relax_ratio,
             "interface_shift": rep.interface_shift, "interface_limit": rep.interface_limit,
-            "seconds": rep.seconds_surrogate}
+            "seconds": rep.seconds_surrogate, "projected": bool(rep.projected)}
+
+
+def lbm_project_workspace_bytes(grid) -> int:
+    """Device scratch bytes of lbm_project_solenoidal on grid (nx, ny, nz); -1 if invalid."""
+    return int(load().lbm_project_workspace_bytes((ctypes.c_int * 3)(*[int(v) for v in grid])))
+
+
+def lbm_project_solenoidal(u_ptr, grid, work_ptr, work_bytes, stream=None) -> int:
+    """The divergence-free part of the periodic velocity at u_ptr (device FP32 [3][nz][ny][nx]),
+    in place, with caller-owned scratch (raw device pointers in; returns the lbm status)."""
+    gr = (ctypes.c_int * 3)(*[int(v) for v in grid])
+    return int(load().lbm_project_solenoidal(ctypes.c_void_p(u_ptr), gr, ctypes.c_void_p(work_ptr), int(work_bytes),
+                                             stream))

@@ -221,3 +221,16 @@ def test_state_bytes_rejects_invalid_arguments(lib):
     assert lbm.lbm_state_bytes(19, (8, 8, 8), 3) == 0
     assert lbm.lbm_state_bytes(19, (0, 8, 8), 0) == 0
     assert lbm.lbm_state_bytes(19, (2048, 2048, 1024), 0) == 0
+
+
+def test_projection_workspace_and_argument_checks(lib):
+    """Host-side checks of lbm_project_solenoidal: its workspace size is the twiddles (padded to
+    256 bytes) plus three complex FP32 planes, and invalid calls return LBM_EINVAL before any
+    launch (NULL pointers, extents outside 1 .. 512)."""
+    from paper_2407_12263_gb300 import lbm
+    assert lbm.lbm_project_workspace_bytes((64, 64, 64)) == 1536 + 3 * 64 ** 3 * 8
+    assert lbm.lbm_project_workspace_bytes((9, 7, 5)) == 256 + 3 * 9 * 7 * 5 * 8
+    for bad in ((0, 4, 4), (4, 4, 513), (-1, 2, 2)):
+        assert lbm.lbm_project_workspace_bytes(bad) == -1
+    assert lbm.lbm_project_solenoidal(0, (4, 4, 4), 0, 1 << 20, None) == lbm.LBM_EINVAL
+    assert lbm.lbm_project_solenoidal(16, (4, 4, 600), 16, 1 << 30, None) == lbm.LBM_EINVAL

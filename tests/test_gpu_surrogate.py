@@ -437,5 +437,5 @@ def test_trained_surrogate_beats_persistence_and_is_accepted():
     s0 = g.mass()[0]
     ms = torch.cat([mean, std]).cpu().numpy().tolist()
     rep = lbm.lbm_surrogate_jump(g.h, net, f, ms, k, 8, 1e-2, 2.0)
-    assert rep["accepted"], rep
+    assert rep["accepted"] and rep["projected"], rep
     assert g.mass()[0] == s0
