@@ -104,12 +104,12 @@ cudaError_t launch_init(const Params& P, int z0, int nzs, const double* phi0s, c
 }
 
 // ---------------------------------------------------------------------------------------
-// Fields of the propagated current state (the values the next step collides with).
-// Output slab layout: 11 FP64 planes of nzs * nxy values: phi, p, u(3), grad phi(3), n(3).
+// Fields of the propagated current state (the values the next step collides with), each as FP64
+// planes of the slab at its own destination (FieldOut): phi, p, u(3), grad phi(3), n(3).
 // ---------------------------------------------------------------------------------------
 template <int Q, int SCHEME, bool GEN, int S>
 __global__ void moments_kernel(const Params P, int z0, const void* __restrict__ fg,
-                               const float* __restrict__ phi_fd, int mask, double* __restrict__ out) {
+                               const float* __restrict__ phi_fd, int mask, const FieldOut out) {
     const int x = blockIdx.x * kAuxBX + threadIdx.x;
     const int y = blockIdx.y * kAuxBY + threadIdx.y;
     const int zl = blockIdx.z;
@@ -131,35 +131,34 @@ __global__ void moments_kernel(const Params P, int z0, const void* __restrict__ 
         macro_interface_fd(P, gx, gy, gz, m);
     }
     macro_pressure<GEN>(P, m);
-    const size_t slab = (size_t)gridDim.z * P.nxy;
     const size_t l = (size_t)zl * P.nxy + (size_t)y * P.nx + x;
-    if (mask & 1) out[l] = (double)phi_fx / kPhiFx;
-    if (mask & 2) out[slab + l] = (P.w0d + (double)m.P) / 3.0;  // p = cs^2 (w0 + P)
+    if (mask & 1) out.p[0][l] = (double)phi_fx / kPhiFx;
+    if (mask & 2) out.p[1][l] = (P.w0d + (double)m.P) / 3.0;  // p = cs^2 (w0 + P)
     for (int a = 0; a < 3; ++a) {
-        if (mask & 4) out[(2 + a) * slab + l] = (double)m.u[a];
-        if (mask & 8) out[(5 + a) * slab + l] = (double)m.gphi[a];
-        if (mask & 16) out[(8 + a) * slab + l] = (double)m.n[a];
+        if (mask & 4) out.p[2 + a][l] = (double)m.u[a];
+        if (mask & 8) out.p[5 + a][l] = (double)m.gphi[a];
+        if (mask & 16) out.p[8 + a][l] = (double)m.n[a];
     }
 }
 
 template <int Q, int SCHEME, int S>
-static void moments_qs(const Params& P, int z0, int nzs, const void* fg, const float* phi, int mask, double* out,
-                       cudaStream_t s) {
+static void moments_qs(const Params& P, int z0, int nzs, const void* fg, const float* phi, int mask,
+                       const FieldOut& out, cudaStream_t s) {
     const dim3 grid((P.nx + kAuxBX - 1) / kAuxBX, (P.ny + kAuxBY - 1) / kAuxBY, nzs), block(kAuxBX, kAuxBY);
     if (P.general) moments_kernel<Q, SCHEME, true, S><<<grid, block, 0, s>>>(P, z0, fg, phi, mask, out);
     else moments_kernel<Q, SCHEME, false, S><<<grid, block, 0, s>>>(P, z0, fg, phi, mask, out);
 }
 
 template <int Q, int SCHEME>
-static void moments_q(const Params& P, int z0, int nzs, const void* fg, const float* phi, int mask, double* out,
-                      cudaStream_t s) {
+static void moments_q(const Params& P, int z0, int nzs, const void* fg, const float* phi, int mask,
+                      const FieldOut& out, cudaStream_t s) {
     if (P.storage == STORE_F16) moments_qs<Q, SCHEME, STORE_F16>(P, z0, nzs, fg, phi, mask, out, s);
     else if (P.storage == STORE_BF16) moments_qs<Q, SCHEME, STORE_BF16>(P, z0, nzs, fg, phi, mask, out, s);
     else moments_qs<Q, SCHEME, STORE_F32>(P, z0, nzs, fg, phi, mask, out, s);
 }
 
 cudaError_t launch_moments(const Params& P, int scheme, int z0, int nzs, const void* fg, const float* phi_fd,
-                           int mask, double* out, cudaStream_t s) {
+                           int mask, const FieldOut& out, cudaStream_t s) {
     if (P.Q == 9) {
         if (scheme == SCHEME_DF) moments_q<9, SCHEME_DF>(P, z0, nzs, fg, phi_fd, mask, out, s);
         else moments_q<9, SCHEME_FD>(P, z0, nzs, fg, phi_fd, mask, out, s);

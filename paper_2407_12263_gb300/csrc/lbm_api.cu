@@ -416,6 +416,12 @@ int lbm_init_fields(lbm_ctx* c, const double* phi0, const double* u0, const doub
     const int nzs = slab_depth(c, per_z, 2);
     rc = ensure_staging(c, (size_t)(nzs + 2 + (u0 ? 3 * nzs : 0) + (p ? nzs : 0)) * nxy);
     if (rc) return rc;
+    double* phis = c->staging;
+    double* us = c->staging + (size_t)(nzs + 2) * nxy;
+    double* ps = us + (u0 ? (size_t)3 * nzs * nxy : 0);
+    // one slab holds the whole grid: pass 1 copies phi0 and p to where pass 2 reads them, and
+    // pass 2 copies them no more
+    const bool one_slab = nzs >= P.nz;
     // Pass 1, before anything is written: every phi0 in [kPhiMin, kPhiMax] and every p > 0 and
     // finite, and the sum of phi0, checked on the device slab by slab (block partials added on
     // the host in a fixed order). Only when a value fails is the host array searched for it.
@@ -439,13 +445,15 @@ int lbm_init_fields(lbm_ctx* c, const double* phi0, const double* u0, const doub
         for (int z0 = 0; z0 < P.nz; z0 += nzs) {
             const int n = (z0 + nzs <= P.nz) ? nzs : P.nz - z0;
             const size_t cells = (size_t)n * nxy;
-            LBM_CUDA(c, cudaMemcpyAsync(c->staging, phi0 + (size_t)z0 * nxy, cells * sizeof(double), cudaMemcpyHostToDevice,
+            double* dphi = one_slab ? phis + nxy : c->staging;
+            LBM_CUDA(c, cudaMemcpyAsync(dphi, phi0 + (size_t)z0 * nxy, cells * sizeof(double), cudaMemcpyHostToDevice,
                                         c->stream));
-            if ((rc = check(c->staging, (long long)cells, kPhiMin, kPhiMax, 0, &bad_phi, &sum))) return rc;
+            if ((rc = check(dphi, (long long)cells, kPhiMin, kPhiMax, 0, &bad_phi, &sum))) return rc;
             if (p) {
-                LBM_CUDA(c, cudaMemcpyAsync(c->staging, p + (size_t)z0 * nxy, cells * sizeof(double), cudaMemcpyHostToDevice,
+                double* dp = one_slab ? ps : c->staging;
+                LBM_CUDA(c, cudaMemcpyAsync(dp, p + (size_t)z0 * nxy, cells * sizeof(double), cudaMemcpyHostToDevice,
                                             c->stream));
-                if ((rc = check(c->staging, (long long)cells, 0.0, INFINITY, 1, &bad_p, nullptr))) return rc;
+                if ((rc = check(dp, (long long)cells, 0.0, INFINITY, 1, &bad_p, nullptr))) return rc;
             }
         }
         if (bad_p > 0)
@@ -465,27 +473,29 @@ int lbm_init_fields(lbm_ctx* c, const double* phi0, const double* u0, const doub
     P.phi_ref = (float)P.phi_ref_d;
     P.phi_ref_fx = (mean >= 0.5) ? (1 << 30) : 0;
     drop_graphs(c);  // captured steps carry the old parameters
-    double* phis = c->staging;
-    double* us = c->staging + (size_t)(nzs + 2) * nxy;
-    double* ps = us + (u0 ? (size_t)3 * nzs * nxy : 0);
     for (int z0 = 0; z0 < P.nz; z0 += nzs) {
         const int n = (z0 + nzs <= P.nz) ? nzs : P.nz - z0;
         // phi0 planes z0-1 .. z0+n: the slab's own planes in one copy, and the two halo planes,
         // periodic images or across a z wall the mirror image (zero normal gradient); D2Q9 has
-        // only its one plane
-        LBM_CUDA(c, cudaMemcpyAsync(phis + nxy, phi0 + (size_t)z0 * nxy, (size_t)n * nxy * sizeof(double),
-                                    cudaMemcpyHostToDevice, c->stream));
+        // only its one plane. With one slab the halos are copies of staged planes.
+        if (!one_slab)
+            LBM_CUDA(c, cudaMemcpyAsync(phis + nxy, phi0 + (size_t)z0 * nxy, (size_t)n * nxy * sizeof(double),
+                                        cudaMemcpyHostToDevice, c->stream));
         if (P.Q != 9)
             for (int l : {-1, n}) {
                 const int z = (P.walls & 4) ? std::min(std::max(z0 + l, 0), P.nz - 1) : ((z0 + l) % P.nz + P.nz) % P.nz;
-                LBM_CUDA(c, cudaMemcpyAsync(phis + (size_t)(l + 1) * nxy, phi0 + (size_t)z * nxy, nxy * sizeof(double),
-                                            cudaMemcpyHostToDevice, c->stream));
+                if (one_slab)
+                    LBM_CUDA(c, cudaMemcpyAsync(phis + (size_t)(l + 1) * nxy, phis + (size_t)(z + 1) * nxy,
+                                                nxy * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+                else
+                    LBM_CUDA(c, cudaMemcpyAsync(phis + (size_t)(l + 1) * nxy, phi0 + (size_t)z * nxy,
+                                                nxy * sizeof(double), cudaMemcpyHostToDevice, c->stream));
             }
         if (u0)
             for (int a = 0; a < 3; ++a)
                 LBM_CUDA(c, cudaMemcpyAsync(us + (size_t)a * n * nxy, u0 + (size_t)a * P.N + (size_t)z0 * nxy,
                                             (size_t)n * nxy * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-        if (p)
+        if (p && !one_slab)
             LBM_CUDA(c, cudaMemcpyAsync(ps, p + (size_t)z0 * nxy, (size_t)n * nxy * sizeof(double),
                                         cudaMemcpyHostToDevice, c->stream));
         LBM_CUDA(c, lbm::launch_init(P, z0, n, phis, u0 ? us : nullptr, p ? ps : nullptr, p0, c->fg[c->cur],
@@ -533,19 +543,44 @@ static int fields_out(lbm_ctx* c, int mask, double* const* dst /* 11 planes, NUL
     if (!c->initialised) return set_error(c, LBM_ESTATE, "no state: call lbm_init_phi first");
     Params& P = c->P;
     const size_t nxy = (size_t)P.nxy;
-    const int nzs = slab_depth(c, 11, 0);
-    rc = ensure_staging(c, (size_t)11 * nzs * nxy);
-    if (rc) return rc;
     const void* fg = c->fg[c->cur];
     if (c->scheme == LBM_SCHEME_FINITE_DIFFERENCE) {
         LBM_CUDA(c, lbm::launch_fd_phi(P, fg, c->phi_fd, c->stream));
         c->launches += 1;
     }
+    // Destinations in page-locked host memory are written by the kernel itself across the host
+    // link, in one launch over the grid, with no staging copy; any other host memory goes slab
+    // by slab through device staging and cudaMemcpyAsync.
+    lbm::FieldOut direct{};
+    bool all_direct = P.nz <= 65535;
+    for (int j = 0; j < 11 && all_direct; ++j) {
+        if (!dst[j]) continue;
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, dst[j]) != cudaSuccess) {
+            (void)cudaGetLastError();
+            all_direct = false;
+        } else if (a.type != cudaMemoryTypeHost || !a.devicePointer) {
+            all_direct = false;
+        } else {
+            direct.p[j] = static_cast<double*>(a.devicePointer);
+        }
+    }
+    if (all_direct) {
+        LBM_CUDA(c, lbm::launch_moments(P, c->scheme, 0, P.nz, fg, c->phi_fd, mask, direct, c->stream));
+        c->launches += 1;
+        LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+        return LBM_OK;
+    }
+    const int nzs = slab_depth(c, 11, 0);
+    rc = ensure_staging(c, (size_t)11 * nzs * nxy);
+    if (rc) return rc;
     for (int z0 = 0; z0 < P.nz; z0 += nzs) {
         const int n = (z0 + nzs <= P.nz) ? nzs : P.nz - z0;
-        LBM_CUDA(c, lbm::launch_moments(P, c->scheme, z0, n, fg, c->phi_fd, mask, c->staging, c->stream));
-        c->launches += 1;
         const size_t slab = (size_t)n * nxy;
+        lbm::FieldOut staged{};
+        for (int j = 0; j < 11; ++j) staged.p[j] = c->staging + (size_t)j * slab;
+        LBM_CUDA(c, lbm::launch_moments(P, c->scheme, z0, n, fg, c->phi_fd, mask, staged, c->stream));
+        c->launches += 1;
         for (int j = 0; j < 11; ++j) {
             if (!dst[j]) continue;
             LBM_CUDA(c, cudaMemcpyAsync(dst[j] + (size_t)z0 * nxy, c->staging + (size_t)j * slab, slab * sizeof(double),

@@ -60,11 +60,16 @@ cudaError_t launch_fd_phi(const Params& P, const void* fg_in, float* phi_fd, cud
 cudaError_t launch_init(const Params& P, int z0, int nzs, const double* phi0s, const double* u0s,
                         const double* ps, double p0, void* fg, cudaStream_t s);
 
-// Macroscopic fields for z in [z0, z0 + nzs) written as FP64 planes of the slab into out:
-// plane k of field j at out + (j * nzs) * nxy ... see the field order in the definition.
-// mask selects the fields: bit 0 phi, 1 p, 2 u (3 planes), 3 grad phi (3), 4 n (3).
+// Where the macroscopic fields go: field j (0 phi, 1 p, 2-4 u, 5-7 grad phi, 8-10 n) of cell
+// (x, y, z0 + zl) is written to p[j][zl * nxy + y * nx + x]; device memory or page-locked host
+// memory the device can address.
+struct FieldOut {
+    double* p[11];
+};
+// Macroscopic fields for z in [z0, z0 + nzs) as FP64. mask selects the fields: bit 0 phi, 1 p,
+// 2 u (3 planes), 3 grad phi (3), 4 n (3); the pointers of the selected fields must be set.
 cudaError_t launch_moments(const Params& P, int scheme, int z0, int nzs, const void* fg,
-                           const float* phi_fd, int mask, double* out, cudaStream_t s);
+                           const float* phi_fd, int mask, const FieldOut& out, cudaStream_t s);
 
 // sum phi, sum rho phi (FP64), the count of non-finite stored populations, and in result[3]
 // the bits of the exact 64-bit sum of the fixed-point phi values.
