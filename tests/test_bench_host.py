@@ -90,3 +90,12 @@ def test_summary_rounding_keeps_significant_digits():
     assert bench.sig(0.000123456, 2) == 0.00012
     assert bench.sig(0.0) == 0.0 and bench.sig(None) is None
     assert bench.sig(float("inf")) == float("inf")
+
+
+@pytest.mark.parametrize("warmup,want", [(3, 32), (5, 32), (50, 50), (51, 52), (64, 64)])
+def test_leg_warmup_covers_a_whole_graph_and_is_even(warmup, want):
+    """Legs other than the headline warm up for at least one whole 32-step graph and an even
+    count, so that their timed regions start from a buffer whose graph is already captured."""
+    sys.path.insert(0, str(ROOT))
+    import bench
+    assert bench.leg_warmup(warmup) == want
