@@ -7,8 +7,9 @@ CPU legs use it. The paper reports, for its static droplets, the spurious curren
 (Sec. 3.1); these are those quantities written out as plain reductions over the cells of
 fields given as arrays [nz][ny][nx] (u as [3][nz][ny][nx]):
 
-* speed = sqrt((u_x^2 + u_y^2) + u_z^2) per cell, each product and sum rounded once (FP64);
-  max_speed its largest value and argmax the cell index (x fastest) where it first occurs;
+* s2 = (u_x^2 + u_y^2) + u_z^2 per cell, each product and sum rounded once (FP64); argmax is
+  the cell index (x fastest) of the largest s2, the smallest index on ties, and max_speed the
+  square root of that s2;
 * kinetic = sum over cells of rho |u|^2 / 2 with rho = 1 + (rho_ratio - 1) phi (the density of
   the one-fluid model, fluid 2 of unit density);
 * the distance of a cell centre (integer coordinates) from `centre`: along an axis with walls
@@ -45,15 +46,14 @@ def diagnostics(phi, p, u, rho_ratio, centre, r_in, r_out, walls=0):
     p = np.asarray(p, dtype=np.float64)
     u = np.asarray(u, dtype=np.float64)
     nz, ny, nx = phi.shape
-    speed = np.sqrt((u[0] * u[0] + u[1] * u[1]) + u[2] * u[2])
-    flat = speed.reshape(-1)
-    k = int(np.argmax(flat))
+    s2 = ((u[0] * u[0] + u[1] * u[1]) + u[2] * u[2]).reshape(-1)
+    k = int(np.argmax(s2))  # the first occurrence of the largest value
     rho = 1.0 + (rho_ratio - 1.0) * phi
     kinetic = float(np.sum(0.5 * rho * ((u[0] * u[0] + u[1] * u[1]) + u[2] * u[2])))
     d = distance((nx, ny, nz), centre, walls)
     inside, outside = d < r_in, d > r_out
     n_in, n_out = int(inside.sum()), int(outside.sum())
-    return {"max_speed": float(flat[k]), "argmax": k, "kinetic": kinetic,
+    return {"max_speed": float(np.sqrt(s2[k])), "argmax": k, "kinetic": kinetic,
             "p_in": float(p[inside].mean()) if n_in else float("nan"),
             "p_out": float(p[outside].mean()) if n_out else float("nan"),
             "n_in": n_in, "n_out": n_out}

@@ -18,9 +18,9 @@ def _loop(phi, p, u, rho_ratio, centre, r_in, r_out, walls):
         for y in range(ny):
             for x in range(nx):
                 ux, uy, uz = float(u[0, z, y, x]), float(u[1, z, y, x]), float(u[2, z, y, x])
-                s = math.sqrt((ux * ux + uy * uy) + uz * uz)
-                if s > best:
-                    best, arg = s, (z * ny + y) * nx + x
+                s2 = (ux * ux + uy * uy) + uz * uz
+                if s2 > best:
+                    best, arg = s2, (z * ny + y) * nx + x
                 rho = 1.0 + (rho_ratio - 1.0) * float(phi[z, y, x])
                 kin += 0.5 * rho * ((ux * ux + uy * uy) + uz * uz)
                 d2 = 0.0
@@ -40,7 +40,7 @@ def _loop(phi, p, u, rho_ratio, centre, r_in, r_out, walls):
                 if d > r_out:
                     s_out += float(p[z, y, x])
                     n_out += 1
-    return {"max_speed": best, "argmax": arg, "kinetic": kin, "p_in": s_in / n_in if n_in else math.nan,
+    return {"max_speed": math.sqrt(best), "argmax": arg, "kinetic": kin, "p_in": s_in / n_in if n_in else math.nan,
             "p_out": s_out / n_out if n_out else math.nan, "n_in": n_in, "n_out": n_out}
 
 
