@@ -176,6 +176,33 @@ int lbm_gradients(lbm_ctx *ctx, double *grad_phi, double *normal);
  */
 int lbm_mass(lbm_ctx *ctx, double *sum_phi, double *sum_rho_phi);
 
+/*
+ * State diagnostics for the static-droplet checks of Sec. 3.1: the spurious currents (the
+ * largest |u|, Table 1) and the pressure inside and outside the droplet for Laplace's law,
+ * reduced on the device from the fields lbm_moments returns (u and p of the propagated current
+ * state), without moving the fields to the host. In FP64, every product and sum rounded once:
+ *   max_speed  sqrt of the largest (u_x^2 + u_y^2) + u_z^2 over the cells;
+ *   argmax     the cell index (x fastest) of that value, the smallest index on ties;
+ *   kinetic    sum over cells of rho |u|^2 / 2, rho = 1 + (rho_ratio - 1) phi;
+ *   p_in/n_in  mean p over, and count of, the cells whose centre (integer coordinates) lies
+ *              closer than r_in to centre; p_out/n_out the same farther than r_out. The
+ *              distance takes the minimum image along periodic axes, the plain difference
+ *              along walled axes, and leaves out an axis of extent 1. A mean over no cell is NaN.
+ * The reduction order is fixed (per thread, per block, then the blocks in order): the same bits
+ * on every run. The per-cell fields are computed by the code lbm_moments uses; compiled into
+ * another kernel, a fused multiply-add may round differently, so a field value can differ from
+ * lbm_moments' in its last FP32 bit. centre: 3 host doubles (x, y, z). Synchronous. LBM_EINVAL for NULL pointers or
+ * a non-finite centre or radius; LBM_ESTATE before lbm_init_phi.
+ */
+typedef struct {
+    double max_speed;
+    long long argmax;
+    double kinetic;
+    double p_in, p_out;
+    long long n_in, n_out;
+} lbm_diag;
+int lbm_diagnostics(lbm_ctx *ctx, const double centre[3], double r_in, double r_out, lbm_diag *out);
+
 /* Copy the post-collision populations f*, g* to / from host FP64 arrays (Q planes each;
  * either pointer of lbm_get_pops may be NULL). lbm_set_pops also marks the state
  * initialised; sum_i g_i must lie in [-1, 1.5] in every cell (LBM_EINVAL otherwise), and is

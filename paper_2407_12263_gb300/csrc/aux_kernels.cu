@@ -2,6 +2,7 @@
 // conversion for the difference-free conservative phase-field LBM (arXiv:2407.12263).
 // None of these runs inside the time-step loop.
 #include "cell.cuh"
+#include "diagnostics.h"
 
 namespace lbm {
 
@@ -107,21 +108,16 @@ cudaError_t launch_init(const Params& P, int z0, int nzs, const double* phi0s, c
 // Fields of the propagated current state (the values the next step collides with), each as FP64
 // planes of the slab at its own destination (FieldOut): phi, p, u(3), grad phi(3), n(3).
 // ---------------------------------------------------------------------------------------
+// The macroscopic fields of cell (x, y, z) of the propagated state, as the next step's
+// collision sees them; the fixed-point phi in phi_fx.
 template <int Q, int SCHEME, bool GEN, int S>
-__global__ void moments_kernel(const Params P, int z0, const void* __restrict__ fg,
-                               const float* __restrict__ phi_fd, int mask, const FieldOut out) {
-    const int x = blockIdx.x * kAuxBX + threadIdx.x;
-    const int y = blockIdx.y * kAuxBY + threadIdx.y;
-    const int zl = blockIdx.z;
-    if (x >= P.nx || y >= P.ny) return;
-    const int z = z0 + zl;
+__device__ __forceinline__ void cell_fields(const Params& P, const void* __restrict__ fg, const float* __restrict__ phi_fd,
+                                            int x, int y, int z, Macro& m, int& phi_fx) {
     const Nbr nb = make_nbr(P, x, y, z);
     const int c = (z * P.ny + y) * P.nx + x;
     const WallSide ws = GEN ? make_wall_side(P, x, y, z) : WallSide{};
     float fb[Q], gb[Q];
-    int phi_fx;
     pull<Q, true, S, GEN>(P, fg, c, nb, fb, gb, phi_fx, ws);
-    Macro m;
     macro_flow<Q, GEN>(P, fb, gb, m);
     if (SCHEME == SCHEME_DF) {
         macro_interface_df<Q>(P, m);
@@ -131,6 +127,19 @@ __global__ void moments_kernel(const Params P, int z0, const void* __restrict__ 
         macro_interface_fd(P, gx, gy, gz, m);
     }
     macro_pressure<GEN>(P, m);
+}
+
+template <int Q, int SCHEME, bool GEN, int S>
+__global__ void moments_kernel(const Params P, int z0, const void* __restrict__ fg,
+                               const float* __restrict__ phi_fd, int mask, const FieldOut out) {
+    const int x = blockIdx.x * kAuxBX + threadIdx.x;
+    const int y = blockIdx.y * kAuxBY + threadIdx.y;
+    const int zl = blockIdx.z;
+    if (x >= P.nx || y >= P.ny) return;
+    const int z = z0 + zl;
+    Macro m;
+    int phi_fx;
+    cell_fields<Q, SCHEME, GEN, S>(P, fg, phi_fd, x, y, z, m, phi_fx);
     const size_t l = (size_t)zl * P.nxy + (size_t)y * P.nx + x;
     if (mask & 1) out.p[0][l] = (double)phi_fx / kPhiFx;
     if (mask & 2) out.p[1][l] = (P.w0d + (double)m.P) / 3.0;  // p = cs^2 (w0 + P)
@@ -336,6 +345,170 @@ cudaError_t launch_mass(const Params& P, const void* fg, double* partials, int n
     }
 #undef LBM_MASS
     mass_finish<<<1, kRedThreads, 0, s>>>(partials, n_partials, result);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Diagnostics (lbm_diagnostics): the largest u^2 and its cell, the kinetic energy and the mean
+// pressure inside and outside a sphere, from the same per-cell fields lbm_moments returns, in
+// FP64 with every product and sum rounded once (no contraction), so that a host evaluation of
+// the same definitions on lbm_moments' output gives the same maximum and cell. Each thread takes
+// a grid-stride set of cells in a fixed order, a block combines its threads with warp shuffles
+// and shared memory in a fixed tree, and one block combines the per-block partials in order:
+// the same bits on every run.
+// ---------------------------------------------------------------------------------------
+struct DiagAcc {
+    double s2;      // the largest u^2 so far
+    long long arg;  // its cell (the smallest index among equal values)
+    double kin, pin, pout;
+    long long nin, nout;
+};
+
+__device__ __forceinline__ void diag_merge(DiagAcc& a, const DiagAcc& b) {
+    if (b.s2 > a.s2 || (b.s2 == a.s2 && b.arg < a.arg)) {
+        a.s2 = b.s2;
+        a.arg = b.arg;
+    }
+    a.kin += b.kin;
+    a.pin += b.pin;
+    a.pout += b.pout;
+    a.nin += b.nin;
+    a.nout += b.nout;
+}
+
+__device__ __forceinline__ DiagAcc diag_shfl_down(const DiagAcc& a, int o) {
+    DiagAcc b;
+    b.s2 = __shfl_down_sync(0xffffffffu, a.s2, o);
+    b.arg = __shfl_down_sync(0xffffffffu, a.arg, o);
+    b.kin = __shfl_down_sync(0xffffffffu, a.kin, o);
+    b.pin = __shfl_down_sync(0xffffffffu, a.pin, o);
+    b.pout = __shfl_down_sync(0xffffffffu, a.pout, o);
+    b.nin = __shfl_down_sync(0xffffffffu, a.nin, o);
+    b.nout = __shfl_down_sync(0xffffffffu, a.nout, o);
+    return b;
+}
+
+// Block total of a, valid in thread 0.
+__device__ __forceinline__ void diag_block(DiagAcc& a) {
+    __shared__ DiagAcc rs[kRedThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const DiagAcc b = diag_shfl_down(a, o);
+        diag_merge(a, b);
+    }
+    if (lane == 0) rs[warp] = a;
+    __syncthreads();
+    if (warp == 0) {
+        a = lane < kRedThreads / 32 ? rs[lane] : DiagAcc{-1.0, -1, 0.0, 0.0, 0.0, 0, 0};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const DiagAcc b = diag_shfl_down(a, o);
+            diag_merge(a, b);
+        }
+    }
+}
+
+// distance of the cell centre (x, y, z) from the centre along one axis, squared
+__device__ __forceinline__ double axis_d2(int i, double c, int n, bool wall) {
+    if (n == 1) return 0.0;
+    double d = fabs((double)i - c);
+    if (!wall) {
+        d = fmod(d, (double)n);
+        d = fmin(d, __dsub_rn((double)n, d));
+    }
+    return __dmul_rn(d, d);
+}
+
+struct DiagArgs {
+    double cx, cy, cz, r_in, r_out;
+};
+
+template <int Q, int SCHEME, bool GEN, int S>
+__global__ void __launch_bounds__(kRedThreads)
+diag_kernel(const Params P, const void* __restrict__ fg, const float* __restrict__ phi_fd, const DiagArgs A,
+            DiagAcc* __restrict__ partials) {
+    DiagAcc a{-1.0, -1, 0.0, 0.0, 0.0, 0, 0};
+    for (long long c = (long long)blockIdx.x * kRedThreads + threadIdx.x; c < P.N;
+         c += (long long)gridDim.x * kRedThreads) {
+        const int z = (int)(c / P.nxy);
+        const int r = (int)(c - (long long)z * P.nxy);
+        const int y = r / P.nx, x = r - y * P.nx;
+        Macro m;
+        int phi_fx;
+        cell_fields<Q, SCHEME, GEN, S>(P, fg, phi_fd, x, y, z, m, phi_fx);
+        const double ux = m.u[0], uy = m.u[1], uz = m.u[2];
+        const double s2 = __dadd_rn(__dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy)), __dmul_rn(uz, uz));
+        if (s2 > a.s2) {  // cells come in increasing order: the first of equal values stays
+            a.s2 = s2;
+            a.arg = c;
+        }
+        const double phi = (double)phi_fx / kPhiFx;
+        const double rho = __dadd_rn(P.rho2_d, __dmul_rn(P.drho_d, phi));
+        a.kin = __dadd_rn(a.kin, __dmul_rn(__dmul_rn(0.5, rho), s2));
+        const double p = (P.w0d + (double)m.P) / 3.0;  // as lbm_moments writes it
+        const double d = __dsqrt_rn(__dadd_rn(__dadd_rn(axis_d2(x, A.cx, P.nx, P.walls & 1), axis_d2(y, A.cy, P.ny, P.walls & 2)),
+                                              axis_d2(z, A.cz, P.nz, P.walls & 4)));
+        if (d < A.r_in) {
+            a.pin = __dadd_rn(a.pin, p);
+            a.nin += 1;
+        }
+        if (d > A.r_out) {
+            a.pout = __dadd_rn(a.pout, p);
+            a.nout += 1;
+        }
+    }
+    diag_block(a);
+    if (threadIdx.x == 0) partials[blockIdx.x] = a;
+}
+
+// result: max |u|, its cell (as double bits of the integer), kinetic, p_in, p_out, n_in, n_out
+// (doubles of the counts)
+__global__ void __launch_bounds__(kRedThreads)
+diag_finish(const DiagAcc* __restrict__ partials, int n, double* __restrict__ result) {
+    DiagAcc a{-1.0, -1, 0.0, 0.0, 0.0, 0, 0};
+    for (int b = threadIdx.x; b < n; b += kRedThreads) diag_merge(a, partials[b]);
+    diag_block(a);
+    if (threadIdx.x == 0) {
+        result[0] = __dsqrt_rn(a.s2);
+        result[1] = __longlong_as_double(a.arg);
+        result[2] = a.kin;
+        result[3] = a.nin ? a.pin / (double)a.nin : __longlong_as_double(0x7ff8000000000000ll);
+        result[4] = a.nout ? a.pout / (double)a.nout : __longlong_as_double(0x7ff8000000000000ll);
+        result[5] = (double)a.nin;
+        result[6] = (double)a.nout;
+    }
+}
+
+size_t diag_partial_bytes(int n_blocks) { return (size_t)n_blocks * sizeof(DiagAcc); }
+
+template <int Q, int SCHEME, int S>
+static void diag_qs(const Params& P, const void* fg, const float* phi_fd, const DiagArgs& A, DiagAcc* part, int nb,
+                    cudaStream_t s) {
+    if (P.general) diag_kernel<Q, SCHEME, true, S><<<nb, kRedThreads, 0, s>>>(P, fg, phi_fd, A, part);
+    else diag_kernel<Q, SCHEME, false, S><<<nb, kRedThreads, 0, s>>>(P, fg, phi_fd, A, part);
+}
+
+template <int Q, int SCHEME>
+static void diag_q(const Params& P, const void* fg, const float* phi_fd, const DiagArgs& A, DiagAcc* part, int nb,
+                   cudaStream_t s) {
+    if (P.storage == STORE_F16) diag_qs<Q, SCHEME, STORE_F16>(P, fg, phi_fd, A, part, nb, s);
+    else if (P.storage == STORE_BF16) diag_qs<Q, SCHEME, STORE_BF16>(P, fg, phi_fd, A, part, nb, s);
+    else diag_qs<Q, SCHEME, STORE_F32>(P, fg, phi_fd, A, part, nb, s);
+}
+
+cudaError_t launch_diagnostics(const Params& P, int scheme, const void* fg, const float* phi_fd, const double centre[3],
+                               double r_in, double r_out, void* partials, int n_blocks, double* result, cudaStream_t s) {
+    const DiagArgs A{centre[0], centre[1], centre[2], r_in, r_out};
+    DiagAcc* part = static_cast<DiagAcc*>(partials);
+    if (P.Q == 9) {
+        if (scheme == SCHEME_DF) diag_q<9, SCHEME_DF>(P, fg, phi_fd, A, part, n_blocks, s);
+        else diag_q<9, SCHEME_FD>(P, fg, phi_fd, A, part, n_blocks, s);
+    } else {
+        if (scheme == SCHEME_DF) diag_q<19, SCHEME_DF>(P, fg, phi_fd, A, part, n_blocks, s);
+        else diag_q<19, SCHEME_FD>(P, fg, phi_fd, A, part, n_blocks, s);
+    }
+    diag_finish<<<1, kRedThreads, 0, s>>>(part, n_blocks, result);
     return cudaGetLastError();
 }
 

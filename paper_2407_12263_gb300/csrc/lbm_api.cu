@@ -15,6 +15,7 @@
 
 #include "../../include/lbm.h"
 #include "lattice.cuh"
+#include "diagnostics.h"
 #include "lbm_ctx.h"
 #include "lbm_internal.h"
 #include "storage.cuh"
@@ -624,6 +625,43 @@ int lbm_mass(lbm_ctx* c, double* sum_phi, double* sum_rho_phi) {
     if (sum_phi) *sum_phi = r[0];
     if (sum_rho_phi) *sum_rho_phi = r[1];
     if (r[2] != 0.0) return set_error(c, LBM_ENONFINITE, "%.0f stored populations are not finite", r[2]);
+    return LBM_OK;
+}
+
+int lbm_diagnostics(lbm_ctx* c, const double centre[3], double r_in, double r_out, lbm_diag* out) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!centre || !out) return set_error(c, LBM_EINVAL, "centre and out may not be NULL");
+    if (!is_fin(centre[0]) || !is_fin(centre[1]) || !is_fin(centre[2]) || !is_fin(r_in) || !is_fin(r_out))
+        return set_error(c, LBM_EINVAL, "centre, r_in and r_out must be finite");
+    if (!c->initialised) return set_error(c, LBM_ESTATE, "no state: call lbm_init_phi first");
+    const Params& P = c->P;
+    const int nb = c->n_partials;
+    // scratch: the per-block partials, then the 7 result doubles
+    const size_t part_doubles = (lbm::diag_partial_bytes(nb) + sizeof(double) - 1) / sizeof(double);
+    rc = ensure_staging(c, part_doubles + 8);
+    if (rc) return rc;
+    const void* fg = c->fg[c->cur];
+    if (c->scheme == LBM_SCHEME_FINITE_DIFFERENCE) {
+        LBM_CUDA(c, lbm::launch_fd_phi(P, fg, c->phi_fd, c->stream));
+        c->launches += 1;
+    }
+    double* result = c->staging + part_doubles;
+    LBM_CUDA(c, lbm::launch_diagnostics(P, c->scheme, fg, c->phi_fd, centre, r_in, r_out, c->staging, nb, result,
+                                        c->stream));
+    c->launches += 2;
+    double r[7];
+    LBM_CUDA(c, cudaMemcpyAsync(r, result, sizeof r, cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    out->max_speed = r[0];
+    long long arg;
+    std::memcpy(&arg, &r[1], sizeof arg);
+    out->argmax = arg;
+    out->kinetic = r[2];
+    out->p_in = r[3];
+    out->p_out = r[4];
+    out->n_in = (long long)r[5];
+    out->n_out = (long long)r[6];
     return LBM_OK;
 }
 

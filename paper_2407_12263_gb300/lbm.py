@@ -42,6 +42,12 @@ class lbm_batch_opts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("graph_steps", ctypes.c_int)]
 
 
+class lbm_diag(ctypes.Structure):
+    _fields_ = [("max_speed", ctypes.c_double), ("argmax", ctypes.c_longlong), ("kinetic", ctypes.c_double),
+                ("p_in", ctypes.c_double), ("p_out", ctypes.c_double), ("n_in", ctypes.c_longlong),
+                ("n_out", ctypes.c_longlong)]
+
+
 class lbm_jump_report(ctypes.Structure):
     _fields_ = [("accepted", ctypes.c_int), ("mass_error", ctypes.c_double), ("relax_ratio", ctypes.c_double),
                 ("interface_shift", ctypes.c_double), ("interface_limit", ctypes.c_double),
@@ -68,6 +74,8 @@ SIGNATURES = [
     ("lbm_moments", ctypes.c_int, [ctypes.c_void_p, _dp, _dp, _dp]),
     ("lbm_gradients", ctypes.c_int, [ctypes.c_void_p, _dp, _dp]),
     ("lbm_mass", ctypes.c_int, [ctypes.c_void_p, _dp, _dp]),
+    ("lbm_diagnostics", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                                       ctypes.c_double, ctypes.POINTER(lbm_diag)]),
     ("lbm_get_pops", ctypes.c_int, [ctypes.c_void_p, _dp, _dp]),
     ("lbm_set_pops", ctypes.c_int, [ctypes.c_void_p, _dp, _dp]),
     ("lbm_launch_count", ctypes.c_longlong, [ctypes.c_void_p]),
@@ -206,6 +214,15 @@ def lbm_moments(h, phi=None, p=None, u=None):
 
 def lbm_gradients(h, grad_phi=None, normal=None):
     _check(h, load().lbm_gradients(h, _ptr(grad_phi), _ptr(normal)))
+
+
+def lbm_diagnostics(h, centre, r_in, r_out):
+    """Device-side diagnostics of the current state (see include/lbm.h): a dict with max_speed,
+    argmax, kinetic, p_in, p_out, n_in, n_out."""
+    c = (ctypes.c_double * 3)(*[float(v) for v in centre])
+    d = lbm_diag()
+    _check(h, load().lbm_diagnostics(h, c, float(r_in), float(r_out), ctypes.byref(d)))
+    return {k: getattr(d, k) for k, _ in lbm_diag._fields_}
 
 
 def lbm_mass(h):
@@ -409,6 +426,9 @@ class Lattice:
 
     def mass(self):
         return lbm_mass(self.h)
+
+    def diagnostics(self, centre, r_in, r_out):
+        return lbm_diagnostics(self.h, centre, r_in, r_out)
 
     def get_pops(self):
         f, g = np.empty((self.Q,) + self.shape), np.empty((self.Q,) + self.shape)
