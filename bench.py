@@ -877,7 +877,34 @@ def run_cpu_baseline(lbm, grid, w, params, phi0, cells, args):
                      "rel_l2_u": float(np.linalg.norm(u_g - u_o) / np.linalg.norm(u_o)),
                      "max_abs_u": float(np.abs(u_g - u_o).max()),
                      "max_abs_p": float(np.abs(p_g - p_o).max()), "bounds": bounds[name]}
+    cpu["droplet2d_64"] = run_cpu_droplet2d(oracle, cores)
     return cpu, acc
+
+
+def run_cpu_droplet2d(oracle, cores):
+    """The 2D static droplet (D2Q9, 64^2, R = 16, 5000 steps) on the FP64 oracle, all steps on
+    the host cores: its time, and Laplace's law (mean p over r < R - 2 xi minus mean p over
+    r > R + 2 xi against sigma / R_eff, R_eff from the area of the phi = 0 phase) and the drift
+    of sum phi at the end."""
+    w = I.WORKLOADS["droplet2d_64"]
+    grid = w["grid"]
+    ref = oracle.Oracle(9, grid, w["tau_f"], w["tau_g"], w["M"], w["xi"], w["sigma"])
+    phi0 = I.droplet_phi(grid, w["R"], w["xi"])
+    ref.init_phi(phi0)
+    s0 = math.fsum(ref.moments()[0].ravel())  # correctly rounded sums: the drift is the scheme's own
+    t0 = time.perf_counter()
+    ref.step(w["steps"])
+    secs = time.perf_counter() - t0
+    phi, p, u = ref.moments()
+    r = I.periodic_distance(grid, tuple((n - 1) / 2 for n in grid))
+    jump = float(p[r < w["R"] - 2 * w["xi"]].mean() - p[r > w["R"] + 2 * w["xi"]].mean())
+    r_eff = float(np.sqrt((1 - phi).sum() / np.pi))
+    want = w["sigma"] / r_eff
+    cells = grid[0] * grid[1] * grid[2]
+    return {"steps": w["steps"], "seconds": round(secs, 3), "mlups": round(cells * w["steps"] / secs / 1e6, 3),
+            "cores": cores, "laplace_jump": sig(jump), "sigma_over_R": sig(want), "rel": sig(jump / want - 1, 2),
+            "max_u": sig(float(np.sqrt((u ** 2).sum(0)).max()), 3),
+            "sum_phi_drift_rel": sig((math.fsum(phi.ravel()) - s0) / s0, 2)}
 
 
 # ---------------------------------------------------------------- reference arm: the oracle
