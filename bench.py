@@ -12,7 +12,9 @@ sigma = 1e-3, density and viscosity ratio 1, tau_f = 0.8, M = 0.02, FP32 populat
   roofline     algorithmic bytes per launch (2 x 2 x 19 x 4 B = 304 B per cell) / mean launch time,
                against the measured HBM copy bandwidth
   e2e          the same metric through the C ABI with host buffers: init from a pinned host phi0,
-               the steps, moments and mass back to pinned host arrays, all inside the timed region
+               the steps, and the result back to the host (the static-droplet diagnostics reduced
+               on the device, and the mass), all inside the timed region; `fields` beside it reads
+               the full FP64 fields back instead
   cpu_baseline the FP64 oracle on the host cores, all of them and one (bounded samples)
   detail       the other workloads (2D droplet, Rayleigh-Taylor, Taylor-Green, surrogate) and the
                GPU's errors against the oracle
@@ -798,31 +800,54 @@ def run_rt_accuracy(lbm):
 
 
 def run_e2e(lbm, torch, grid, w, params, phi0, cells, args, world):
-    """Through the C ABI with host buffers: pinned phi0 in, the steps, moments and mass out."""
+    """Through the C ABI with host buffers, each region: pinned phi0 in, the steps, the result out.
+    The result is the workload's metric, the static-droplet checks of Sec. 3.1 as lbm_diagnostics
+    reduces them on the device (largest |u|, the mean pressure inside r < R - 2 xi and outside
+    r > R + 2 xi, the kinetic energy) and sum phi and sum rho phi from lbm_mass: 80 bytes. The
+    same region reading the full fields back (phi, p, u as FP64 through lbm_moments, 84 MB at
+    128^3) is reported beside it as `fields`."""
     shape = phi0.shape
     pin = lambda n: torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
     phi_h = pin(phi0.size).reshape(shape)
     phi_h[...] = phi0
     phi_o, p_o, u_o = pin(phi0.size).reshape(shape), pin(phi0.size).reshape(shape), pin(3 * phi0.size).reshape((3,) + shape)
+    centre = tuple((n - 1) / 2 for n in grid)
+    r_in, r_out = w["R"] - 2 * w["xi"], w["R"] + 2 * w["xi"]
     g = lbm.Lattice(grid, w["Q"], **params)
     g.init_phi(phi_h)                 # warm the handle (staging allocation, module load)
     g.step(args.warmup)
     lbm.lbm_moments(g.h, phi_o, p_o, u_o)
-    barrier(world)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    g.init_phi(phi_h)
-    g.step(args.steps)
-    lbm.lbm_moments(g.h, phi_o, p_o, u_o)
-    s = g.mass()
-    t1 = time.perf_counter()
+    g.diagnostics(centre, r_in, r_out)
+
+    def region(read_fields):
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.init_phi(phi_h)
+        g.step(args.steps)
+        if read_fields:
+            lbm.lbm_moments(g.h, phi_o, p_o, u_o)
+            d = None
+        else:
+            d = g.diagnostics(centre, r_in, r_out)
+        s = g.mass()
+        t1 = time.perf_counter()
+        return max_over_ranks(t1 - t0, world), d, s
+
+    secs, d, s = region(False)
+    secs_f, _, _ = region(True)
     g.close()
-    secs = max_over_ranks(t1 - t0, world)
     h2d = phi0.size * 8
-    d2h = 5 * phi0.size * 8 + 16
+    d2h_metric = 7 * 8 + 3 * 8          # lbm_diag's seven 8-byte members, lbm_mass's three doubles
+    d2h_fields = 5 * phi0.size * 8 + 3 * 8
     return {"value": round(aggregate_mlups(cells, args.steps, secs, world), 1), "unit": "MLUPS",
-            "h2d_bytes_per_step": round(h2d / args.steps, 1), "d2h_bytes_per_step": round(d2h / args.steps, 1),
-            "seconds": round(secs, 4), "sum_phi": s[0]}
+            "h2d_bytes_per_step": round(h2d / args.steps, 1), "d2h_bytes_per_step": round(d2h_metric / args.steps, 1),
+            "seconds": round(secs, 4), "result": "lbm_diagnostics + lbm_mass",
+            "max_u": sig(d["max_speed"], 3), "laplace_jump": sig(d["p_in"] - d["p_out"]), "sum_phi": s[0],
+            "fields": {"value": round(aggregate_mlups(cells, args.steps, secs_f, world), 1), "unit": "MLUPS",
+                       "h2d_bytes_per_step": round(h2d / args.steps, 1),
+                       "d2h_bytes_per_step": round(d2h_fields / args.steps, 1), "seconds": round(secs_f, 4),
+                       "result": "lbm_moments (phi, p, u as FP64) + lbm_mass"}}
 
 
 def cpu_model() -> str:

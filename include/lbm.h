@@ -171,7 +171,8 @@ int lbm_gradients(lbm_ctx *ctx, double *grad_phi, double *normal);
  * Global sums over the propagated current state: sum phi and sum rho phi (the mass
  * m = sum rho phi dx^3 of Sec. 3.3). sum phi is the exact sum of the fixed-point phi values
  * (a 64-bit integer sum; the time step conserves it bit for bit, walls included); sum rho phi
- * accumulates in FP64. Also scans every stored population and returns LBM_ENONFINITE if one
+ * is rho2 sum phi + (rho1 - rho2) sum phi^2, the squares of the fixed-point values summed in
+ * FP64. Also scans every stored population and returns LBM_ENONFINITE if one
  * is not finite. Synchronous.
  */
 int lbm_mass(lbm_ctx *ctx, double *sum_phi, double *sum_rho_phi);
@@ -180,10 +181,14 @@ int lbm_mass(lbm_ctx *ctx, double *sum_phi, double *sum_rho_phi);
  * State diagnostics for the static-droplet checks of Sec. 3.1: the spurious currents (the
  * largest |u|, Table 1) and the pressure inside and outside the droplet for Laplace's law,
  * reduced on the device from the fields lbm_moments returns (u and p of the propagated current
- * state), without moving the fields to the host. In FP64, every product and sum rounded once:
+ * state), without moving the fields to the host. The largest speed, its cell and the masks are
+ * exact as defined here in FP64, every product and sum rounded once (the device decides in
+ * FP32 where that cannot change the outcome and takes FP64 where it can):
  *   max_speed  sqrt of the largest (u_x^2 + u_y^2) + u_z^2 over the cells;
  *   argmax     the cell index (x fastest) of that value, the smallest index on ties;
- *   kinetic    sum over cells of rho |u|^2 / 2, rho = 1 + (rho_ratio - 1) phi;
+ *   kinetic    sum over cells of rho |u|^2 / 2, rho = 1 + (rho_ratio - 1) phi, each cell's term
+ *              and a thread's few cells summed in FP32 (rho and u are FP32 fields), FP64 beyond:
+ *              within about 1e-6 relative of the same sum in FP64;
  *   p_in/n_in  mean p over, and count of, the cells whose centre (integer coordinates) lies
  *              closer than r_in to centre; p_out/n_out the same farther than r_out. The
  *              distance takes the minimum image along periodic axes, the plain difference

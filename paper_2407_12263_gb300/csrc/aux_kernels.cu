@@ -1,6 +1,8 @@
 // aux_kernels.cu -- initialisation, field output, FP64 mass reduction and population
 // conversion for the difference-free conservative phase-field LBM (arXiv:2407.12263).
 // None of these runs inside the time-step loop.
+#include <cmath>
+
 #include "cell.cuh"
 #include "diagnostics.h"
 
@@ -219,8 +221,11 @@ __device__ __forceinline__ void block_sum(long long& s, double (&v)[2]) {
 template <int Q, int S>
 __global__ void __launch_bounds__(kRedThreads)
 mass_kernel(const Params P, const void* __restrict__ fg, double* __restrict__ partials) {
-    long long phi_sum = 0;
+    long long phi_sum = 0, bad_sum = 0;
     double acc[2] = {0.0, 0.0};
+    // sum rho phi = rho2 sum phi + drho sum phi^2: sum phi is the exact integer sum, and only the
+    // squares of the fixed-point values are summed in FP64 (GB300 issues FP64 at a small fraction
+    // of its FP32 rate); mass_finish scales them by 2^-60
     for (long long c = (long long)blockIdx.x * kRedThreads + threadIdx.x; c < P.N;
          c += (long long)gridDim.x * kRedThreads) {
         const int z = (int)(c / P.nxy);
@@ -230,9 +235,9 @@ mass_kernel(const Params P, const void* __restrict__ fg, double* __restrict__ pa
         float fb[Q], gb[Q];
         int phi_fx;
         pull<Q, false, S, true>(P, fg, (int)c, nb, fb, gb, phi_fx, make_wall_side(P, x, y, z));
-        const double phi = (double)phi_fx / kPhiFx;
+        const double q = (double)phi_fx;
         phi_sum += phi_fx;
-        acc[0] += (P.rho2_d + P.drho_d * phi) * phi;
+        acc[0] += q * q;
         int bad = 0;
         const float2 m0 = __ldg(moment_plane(fg) + c);
         bad += !isfinite(m0.x);
@@ -241,8 +246,9 @@ mass_kernel(const Params P, const void* __restrict__ fg, double* __restrict__ pa
             const float2 v = Store<S>::load(moving_plane<S>(fg, P.N, i) + c, P);
             bad += !isfinite(v.x) + !isfinite(v.y);
         }
-        acc[1] += (double)bad;
+        bad_sum += bad;
     }
+    acc[1] = (double)bad_sum;
     block_sum(phi_sum, acc);
     if (threadIdx.x == 0) {
         partials[3 * blockIdx.x] = __longlong_as_double(phi_sum);
@@ -252,7 +258,7 @@ mass_kernel(const Params P, const void* __restrict__ fg, double* __restrict__ pa
 }
 
 __global__ void __launch_bounds__(kRedThreads)
-mass_finish(const double* __restrict__ partials, int n, double* __restrict__ result) {
+mass_finish(const double* __restrict__ partials, int n, double rho2, double drho, double* __restrict__ result) {
     long long phi_sum = 0;
     double acc[2] = {0.0, 0.0};
     for (int b = threadIdx.x; b < n; b += kRedThreads) {
@@ -263,7 +269,7 @@ mass_finish(const double* __restrict__ partials, int n, double* __restrict__ res
     block_sum(phi_sum, acc);
     if (threadIdx.x == 0) {
         result[0] = (double)phi_sum / kPhiFx;
-        result[1] = acc[0];
+        result[1] = rho2 * result[0] + drho * (acc[0] / (kPhiFx * kPhiFx));
         result[2] = acc[1];
         result[3] = __longlong_as_double(phi_sum);  // the exact integer sum, bit for bit
     }
@@ -344,7 +350,7 @@ cudaError_t launch_mass(const Params& P, const void* fg, double* partials, int n
         else LBM_MASS(19, STORE_F32);
     }
 #undef LBM_MASS
-    mass_finish<<<1, kRedThreads, 0, s>>>(partials, n_partials, result);
+    mass_finish<<<1, kRedThreads, 0, s>>>(partials, n_partials, P.rho2_d, P.drho_d, result);
     return cudaGetLastError();
 }
 
@@ -409,55 +415,87 @@ __device__ __forceinline__ void diag_block(DiagAcc& a) {
     }
 }
 
-// distance of the cell centre (x, y, z) from the centre along one axis, squared
-__device__ __forceinline__ double axis_d2(int i, double c, int n, bool wall) {
-    if (n == 1) return 0.0;
-    double d = fabs((double)i - c);
-    if (!wall) {
-        d = fmod(d, (double)n);
-        d = fmin(d, __dsub_rn((double)n, d));
-    }
-    return __dmul_rn(d, d);
-}
-
+// r_in, r_out, and the squared distance along each axis per coordinate (d2x, d2y, d2z; the
+// host evaluates them in FP64 with the operations of the definition), FP64 and FP32 copies.
 struct DiagArgs {
-    double cx, cy, cz, r_in, r_out;
+    double r_in, r_out;
+    float in2_lo, in2_hi, out2_lo, out2_hi;  // FP32 bands around r^2 outside which FP32 decides
+    const double* d2x;
+    const double* d2y;
+    const double* d2z;
+    const float* f2x;
+    const float* f2y;
+    const float* f2z;
 };
 
+// GB300 issues FP64 instructions at a small fraction of its FP32 rate, so the per-cell work is
+// FP32 and FP64 is taken only where the result needs it:
+//  * the largest u^2: each cell's FP32 estimate (within 4e-7 relative of the FP64 value) is
+//    compared with the thread's best so far; the warp takes the FP64 path only if one of its
+//    lanes may reach it, which after a thread's first cell is rare;
+//  * the sphere masks: FP32 decides outside a band of 1e-5 relative around r^2; a cell inside
+//    the band takes the FP64 distance and the correctly rounded square root;
+//  * the energy and pressure sums: FP32 per cell and over a thread's cells, FP64 beyond.
 template <int Q, int SCHEME, bool GEN, int S>
-__global__ void __launch_bounds__(kRedThreads)
+__global__ void __launch_bounds__(kRedThreads, 2)
 diag_kernel(const Params P, const void* __restrict__ fg, const float* __restrict__ phi_fd, const DiagArgs A,
             DiagAcc* __restrict__ partials) {
-    DiagAcc a{-1.0, -1, 0.0, 0.0, 0.0, 0, 0};
-    for (long long c = (long long)blockIdx.x * kRedThreads + threadIdx.x; c < P.N;
-         c += (long long)gridDim.x * kRedThreads) {
-        const int z = (int)(c / P.nxy);
-        const int r = (int)(c - (long long)z * P.nxy);
-        const int y = r / P.nx, x = r - y * P.nx;
-        Macro m;
-        int phi_fx;
-        cell_fields<Q, SCHEME, GEN, S>(P, fg, phi_fd, x, y, z, m, phi_fx);
-        const double ux = m.u[0], uy = m.u[1], uz = m.u[2];
-        const double s2 = __dadd_rn(__dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy)), __dmul_rn(uz, uz));
-        if (s2 > a.s2) {  // cells come in increasing order: the first of equal values stays
-            a.s2 = s2;
-            a.arg = c;
+    double best = -1.0;  // FP64 u^2 of the thread's best cell
+    long long arg = -1;
+    float best_lo = -1.0f;  // FP32 threshold a cell's estimate must reach to be a candidate
+    float kin = 0.f, pin = 0.f, pout = 0.f;
+    long long nin = 0, nout = 0;
+    const unsigned lane_mask = 0xffffffffu;
+    for (long long base = (long long)blockIdx.x * kRedThreads; base < P.N; base += (long long)gridDim.x * kRedThreads) {
+        const long long c = base + threadIdx.x;
+        const bool valid = c < P.N;
+        float s2f = -1.0f;
+        float ux = 0.f, uy = 0.f, uz = 0.f;
+        if (valid) {
+            const int z = (int)(c / P.nxy);
+            const int r = (int)(c - (long long)z * P.nxy);
+            const int y = r / P.nx, x = r - y * P.nx;
+            Macro m;
+            int phi_fx;
+            cell_fields<Q, SCHEME, GEN, S>(P, fg, phi_fd, x, y, z, m, phi_fx);
+            ux = m.u[0];
+            uy = m.u[1];
+            uz = m.u[2];
+            s2f = __fadd_rn(__fadd_rn(__fmul_rn(ux, ux), __fmul_rn(uy, uy)), __fmul_rn(uz, uz));
+            kin = __fadd_rn(kin, __fmul_rn(__fmul_rn(0.5f, m.rho), s2f));
+            const float d2f = __fadd_rn(__fadd_rn(__ldg(A.f2x + x), __ldg(A.f2y + y)), __ldg(A.f2z + z));
+            const bool near_in = d2f >= A.in2_lo && d2f <= A.in2_hi;
+            const bool near_out = d2f >= A.out2_lo && d2f <= A.out2_hi;
+            bool inside = d2f < A.in2_lo, outside = d2f > A.out2_hi;
+            if (near_in || near_out) {  // FP64, as the definition evaluates it
+                const double d = __dsqrt_rn(__dadd_rn(__dadd_rn(__ldg(A.d2x + x), __ldg(A.d2y + y)), __ldg(A.d2z + z)));
+                if (near_in) inside = d < A.r_in;
+                if (near_out) outside = d > A.r_out;
+            }
+            if (inside) {
+                pin = __fadd_rn(pin, m.P);
+                nin += 1;
+            }
+            if (outside) {
+                pout = __fadd_rn(pout, m.P);
+                nout += 1;
+            }
         }
-        const double phi = (double)phi_fx / kPhiFx;
-        const double rho = __dadd_rn(P.rho2_d, __dmul_rn(P.drho_d, phi));
-        a.kin = __dadd_rn(a.kin, __dmul_rn(__dmul_rn(0.5, rho), s2));
-        const double p = (P.w0d + (double)m.P) / 3.0;  // as lbm_moments writes it
-        const double d = __dsqrt_rn(__dadd_rn(__dadd_rn(axis_d2(x, A.cx, P.nx, P.walls & 1), axis_d2(y, A.cy, P.ny, P.walls & 2)),
-                                              axis_d2(z, A.cz, P.nz, P.walls & 4)));
-        if (d < A.r_in) {
-            a.pin = __dadd_rn(a.pin, p);
-            a.nin += 1;
-        }
-        if (d > A.r_out) {
-            a.pout = __dadd_rn(a.pout, p);
-            a.nout += 1;
+        const bool cand = valid && s2f >= best_lo;
+        if (__any_sync(lane_mask, cand)) {
+            if (cand) {
+                const double dx = ux, dy = uy, dz = uz;
+                const double s2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                if (s2 > best) {  // a thread's cells come in increasing order: the first of equal values stays
+                    best = s2;
+                    arg = c;
+                    // below 1e-30 the FP32 squares lose precision to underflow: every cell stays a candidate
+                    best_lo = best < 1e-30 ? 0.0f : __double2float_rd(best * (1.0 - 1e-6));
+                }
+            }
         }
     }
+    DiagAcc a{best, arg, (double)kin, (double)pin, (double)pout, nin, nout};
     diag_block(a);
     if (threadIdx.x == 0) partials[blockIdx.x] = a;
 }
@@ -465,7 +503,7 @@ diag_kernel(const Params P, const void* __restrict__ fg, const float* __restrict
 // result: max |u|, its cell (as double bits of the integer), kinetic, p_in, p_out, n_in, n_out
 // (doubles of the counts)
 __global__ void __launch_bounds__(kRedThreads)
-diag_finish(const DiagAcc* __restrict__ partials, int n, double* __restrict__ result) {
+diag_finish(const DiagAcc* __restrict__ partials, int n, double w0, double* __restrict__ result) {
     DiagAcc a{-1.0, -1, 0.0, 0.0, 0.0, 0, 0};
     for (int b = threadIdx.x; b < n; b += kRedThreads) diag_merge(a, partials[b]);
     diag_block(a);
@@ -473,8 +511,8 @@ diag_finish(const DiagAcc* __restrict__ partials, int n, double* __restrict__ re
         result[0] = __dsqrt_rn(a.s2);
         result[1] = __longlong_as_double(a.arg);
         result[2] = a.kin;
-        result[3] = a.nin ? a.pin / (double)a.nin : __longlong_as_double(0x7ff8000000000000ll);
-        result[4] = a.nout ? a.pout / (double)a.nout : __longlong_as_double(0x7ff8000000000000ll);
+        result[3] = a.nin ? (w0 + a.pin / (double)a.nin) / 3.0 : __longlong_as_double(0x7ff8000000000000ll);
+        result[4] = a.nout ? (w0 + a.pout / (double)a.nout) / 3.0 : __longlong_as_double(0x7ff8000000000000ll);
         result[5] = (double)a.nin;
         result[6] = (double)a.nout;
     }
@@ -497,9 +535,35 @@ static void diag_q(const Params& P, const void* fg, const float* phi_fd, const D
     else diag_qs<Q, SCHEME, STORE_F32>(P, fg, phi_fd, A, part, nb, s);
 }
 
-cudaError_t launch_diagnostics(const Params& P, int scheme, const void* fg, const float* phi_fd, const double centre[3],
+double axis_d2_host(int i, double c, int n, bool wall) {
+    if (n == 1) return 0.0;
+    double d = std::fabs((double)i - c);
+    if (!wall) {
+        if (d >= (double)n) d = std::fmod(d, (double)n);
+        d = std::fmin(d, (double)n - d);
+    }
+    return d * d;
+}
+
+cudaError_t launch_diagnostics(const Params& P, int scheme, const void* fg, const float* phi_fd, const double* d2_axes,
                                double r_in, double r_out, void* partials, int n_blocks, double* result, cudaStream_t s) {
-    const DiagArgs A{centre[0], centre[1], centre[2], r_in, r_out};
+    // bands of 1e-5 relative around r^2: far wider than the FP32 rounding of the axis terms and
+    // their sum (outside, FP32 decides the comparison of the correctly rounded FP64 distance)
+    auto band = [](double r, double& lo, double& hi) {
+        const double r2 = r * r;
+        lo = r > 0 ? r2 * (1.0 - 1e-5) : -1.0;
+        hi = r > 0 ? r2 * (1.0 + 1e-5) : 0.0;
+    };
+    const int n_axes = P.nx + P.ny + P.nz;
+    const float* f2 = reinterpret_cast<const float*>(d2_axes + n_axes);
+    DiagArgs A{r_in, r_out, 0, 0, 0, 0, d2_axes, d2_axes + P.nx, d2_axes + P.nx + P.ny, f2, f2 + P.nx, f2 + P.nx + P.ny};
+    double lo, hi;
+    band(r_in, lo, hi);
+    A.in2_lo = (float)lo;
+    A.in2_hi = (float)hi;
+    band(r_out, lo, hi);
+    A.out2_lo = (float)lo;
+    A.out2_hi = (float)hi;
     DiagAcc* part = static_cast<DiagAcc*>(partials);
     if (P.Q == 9) {
         if (scheme == SCHEME_DF) diag_q<9, SCHEME_DF>(P, fg, phi_fd, A, part, n_blocks, s);
@@ -508,7 +572,7 @@ cudaError_t launch_diagnostics(const Params& P, int scheme, const void* fg, cons
         if (scheme == SCHEME_DF) diag_q<19, SCHEME_DF>(P, fg, phi_fd, A, part, n_blocks, s);
         else diag_q<19, SCHEME_FD>(P, fg, phi_fd, A, part, n_blocks, s);
     }
-    diag_finish<<<1, kRedThreads, 0, s>>>(part, n_blocks, result);
+    diag_finish<<<1, kRedThreads, 0, s>>>(part, n_blocks, P.w0d, result);
     return cudaGetLastError();
 }
 

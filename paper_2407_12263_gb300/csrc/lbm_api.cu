@@ -636,18 +636,30 @@ int lbm_diagnostics(lbm_ctx* c, const double centre[3], double r_in, double r_ou
         return set_error(c, LBM_EINVAL, "centre, r_in and r_out must be finite");
     if (!c->initialised) return set_error(c, LBM_ESTATE, "no state: call lbm_init_phi first");
     const Params& P = c->P;
-    const int nb = c->n_partials;
+    // a few cells per thread: after its first, a thread rarely needs FP64 for the largest u^2
+    const int nb = std::max(1, std::min(c->n_partials, 1024));
     // scratch: the per-block partials, then the 7 result doubles
     const size_t part_doubles = (lbm::diag_partial_bytes(nb) + sizeof(double) - 1) / sizeof(double);
-    rc = ensure_staging(c, part_doubles + 8);
+    const size_t n_axes = (size_t)P.nx + P.ny + P.nz;
+    rc = ensure_staging(c, part_doubles + 8 + n_axes + (n_axes + 1) / 2);
     if (rc) return rc;
+    // the squared distance along each axis per coordinate, evaluated here with the operations the
+    // definition names (minimum image on periodic axes), then the same rounded to FP32
+    std::vector<double> d2(n_axes + (n_axes + 1) / 2);
+    for (int i = 0; i < P.nx; ++i) d2[i] = lbm::axis_d2_host(i, centre[0], P.nx, P.walls & 1);
+    for (int i = 0; i < P.ny; ++i) d2[P.nx + i] = lbm::axis_d2_host(i, centre[1], P.ny, P.walls & 2);
+    for (int i = 0; i < P.nz; ++i) d2[P.nx + P.ny + i] = lbm::axis_d2_host(i, centre[2], P.nz, P.walls & 4);
+    float* f2 = reinterpret_cast<float*>(d2.data() + n_axes);
+    for (size_t i = 0; i < n_axes; ++i) f2[i] = (float)d2[i];
+    double* d2_dev = c->staging + part_doubles + 8;
+    LBM_CUDA(c, cudaMemcpyAsync(d2_dev, d2.data(), d2.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     const void* fg = c->fg[c->cur];
     if (c->scheme == LBM_SCHEME_FINITE_DIFFERENCE) {
         LBM_CUDA(c, lbm::launch_fd_phi(P, fg, c->phi_fd, c->stream));
         c->launches += 1;
     }
     double* result = c->staging + part_doubles;
-    LBM_CUDA(c, lbm::launch_diagnostics(P, c->scheme, fg, c->phi_fd, centre, r_in, r_out, c->staging, nb, result,
+    LBM_CUDA(c, lbm::launch_diagnostics(P, c->scheme, fg, c->phi_fd, d2_dev, r_in, r_out, c->staging, nb, result,
                                         c->stream));
     c->launches += 2;
     double r[7];

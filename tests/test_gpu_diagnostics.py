@@ -6,7 +6,8 @@ output: the per-cell fields come from the same device code, but inlined into ano
 the compiler may fuse a multiply-add of the FP32 macroscopic stage differently, so a value can
 differ in its last FP32 bit (6e-8 relative). The counts agree exactly (distances from integer
 coordinates, FP64, every operation rounded once on both sides); the largest speed, the speed at
-the device's cell and the means and sums agree to 2e-7 relative. Against the FP64 oracle's own
+the device's cell and the mean pressures agree to 2e-7 relative, the kinetic energy (FP32 per
+cell on the device) to 1e-6. Against the FP64 oracle's own
 fields: within the FP32 parity bounds of the fields.
 """
 import math
@@ -46,8 +47,8 @@ def _same(dev, host):
     for k in ("kinetic", "p_in", "p_out"):
         if math.isnan(host[k]):
             assert math.isnan(dev[k])
-        else:
-            assert dev[k] == pytest.approx(host[k], rel=FP32_REL)
+        else:  # the kinetic terms are FP32 per cell and over a thread's few cells
+            assert dev[k] == pytest.approx(host[k], rel=1e-6 if k == "kinetic" else FP32_REL)
 
 
 CASES = [dict(Q=19, grid=(36, 20, 14), scheme=0, storage=0, walls=0, rho_ratio=1.0),
