@@ -379,7 +379,10 @@ def summary(value, df_long, fd, sixteen, bubbles, laplace, acc, rt_acc, tgv, rt,
         s["surrogate"] = {"accepted": a["accepted"], "x": a["speedup"], "shift": sig(a["interface_shift"], 3),
                           "limit": sig(a["interface_limit"], 3), "relax": sig(a["relax_ratio"], 3),
                           "relax_tol": sig(a["relax_tol"], 3), "projected": a["velocity_projected"],
-                          "phi_err": [a["phi_l1_error"]["surrogate"], a["phi_l1_error"]["persistence"]]}
+                          "phi_err": [a["phi_l1_error"]["surrogate"], a["phi_l1_error"]["persistence"]],
+                          "chain": {"accepted": [j["accepted"] for j in sg["chain"]["jumps"]],
+                                    "x": sg["chain"]["speedup"],
+                                    "phi_err": [sg["chain"]["phi_l1_error_end"], sg["chain"]["phi_l1_change_of_the_lbm"]]}}
     return s
 
 
@@ -642,6 +645,31 @@ def run_surrogate_on_stream(lbm, torch, stream, args, world):
                                     "surrogate_unprojected": sig(err(pred, [1, 2, 3]), 3),
                                     "persistence": sig(err(x0, [1, 2, 3]), 3)},
                      "sum_phi_change": jumper.mass()[0] - s0}}
+    # a chain: two more judged jumps of k steps from where the first one left the lattice, the
+    # LBM's own trajectory advanced to the same times beside it
+    t_now = 1600 + k + (judge_steps if rep["accepted"] else 0)
+    truth.step(t_now - (1600 + k))
+    jumps, secs_jumps, secs_lbm = [dict(accepted=rep["accepted"], relax=sig(rep["relax_ratio"], 3))], t_jump, 0.0
+    secs_lbm += t_lbm * (t_now - 1600) / k
+    for _ in range(2):
+        r = lbm.lbm_surrogate_jump(jumper.h, net, f, ms, k, judge_steps, 1e-2, relax_tol, 1.0)
+        dt = k + (judge_steps if r["accepted"] else 0)
+        ev0.record(stream)
+        truth.step(dt)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        secs_lbm += ev0.elapsed_time(ev1) / 1e3
+        secs_jumps += r["seconds"]
+        t_now += dt
+        jumps.append(dict(accepted=r["accepted"], relax=sig(r["relax_ratio"], 3),
+                          shift=sig(r["interface_shift"], 3)))
+    xe, xt_end = coarse(jumper, f), coarse(truth, f)
+    out["chain"] = {"jumps": jumps, "start_step": 1600, "end_step": t_now,
+                    "seconds_jumps": round(secs_jumps, 5), "seconds_lbm_same_steps": round(secs_lbm, 5),
+                    "speedup": round(secs_lbm / secs_jumps, 3),
+                    "phi_l1_error_end": sig(float((xe[0] - xt_end[0]).abs().mean()), 3),
+                    "phi_l1_change_of_the_lbm": sig(float((xt_end[0] - x0[0]).abs().mean()), 3),
+                    "sum_phi_change": jumper.mass()[0] - s0}
     truth.close()
     jumper.close()
     net.close()
