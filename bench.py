@@ -192,6 +192,9 @@ def time_region(torch, stream, step_fn, world):
     return max_over_ranks(ev0.elapsed_time(ev1) / 1e3, world)
 
 
+LEGS = ("small2d", "rt", "batch", "tgv", "surrogate", "laplace", "accuracy")
+
+
 def leg_warmup(warmup, graph_steps=32):
     """Warm-up steps of a leg other than the headline: at least --warmup, even, and at least one
     whole graph of the library's default graph_steps, so that the leg's timed region (an even
@@ -296,12 +299,15 @@ def run_ours(args):
                for name, st in (("fp16", lbm.LBM_STORAGE_FP16), ("bf16", lbm.LBM_STORAGE_BF16))}
 
     e2e = run_e2e(lbm, torch, grid, w, params, phi0, cells, args, world)
-    small = run_small_2d(lbm, torch, stream, args, world)
-    rt = run_rayleigh_taylor(lbm, torch, stream, args, world)
-    bubbles = run_batched_bubbles(lbm, torch, stream, args, world)
-    tgv = run_taylor_green(lbm, torch, stream, args, world)
-    sg = run_surrogate(lbm, torch, stream, args, world) if not args.no_surrogate else None
-    laplace = run_laplace(lbm, torch, stream, w, params, phi0)
+    legs = set(args.legs.split(",")) if args.legs else set(LEGS)
+    if args.no_surrogate:
+        legs.discard("surrogate")
+    small = run_small_2d(lbm, torch, stream, args, world) if "small2d" in legs else None
+    rt = run_rayleigh_taylor(lbm, torch, stream, args, world) if "rt" in legs else None
+    bubbles = run_batched_bubbles(lbm, torch, stream, args, world) if "batch" in legs else None
+    tgv = run_taylor_green(lbm, torch, stream, args, world) if "tgv" in legs else None
+    sg = run_surrogate(lbm, torch, stream, args, world) if "surrogate" in legs else None
+    laplace = run_laplace(lbm, torch, stream, w, params, phi0) if "laplace" in legs else None
 
     out = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(t_df / args.steps * 1e3, 5), "higher_is_better": True,
@@ -317,7 +323,7 @@ def run_ours(args):
               "droplet2d_64": small, "rayleigh_taylor_128x128x512": rt, "taylor_green_256": tgv,
               "batched_rising_bubbles": bubbles, "surrogate_taylor_green": sg}
     acc16 = rt_acc = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and "accuracy" in legs:
         out["cpu_baseline"], detail["accuracy"] = run_cpu_baseline(lbm, grid, w, params, phi0, cells, args)
         rt_acc = run_rt_accuracy(lbm)
         detail["accuracy"]["rayleigh_taylor_32x32x128"] = rt_acc
@@ -357,18 +363,22 @@ def summary(value, df_long, fd, sixteen, bubbles, laplace, acc, rt_acc, tgv, rt,
         if acc:  # max |dphi| and rel-L2(du) against the oracle after acc[...]["steps"] steps
             e["err"] = [sig(acc[name]["max_abs_phi"], 2), sig(acc[name]["rel_l2_u"], 2)]
         s[name] = e
-    s["tgv256_fp16_vs_fp32"] = tgv["fp16_speedup_vs_fp32"]
-    s["rt512_fp16_vs_fp32"] = rt["fp16"]["speedup_vs_fp32"]
+    if tgv:
+        s["tgv256_fp16_vs_fp32"] = tgv["fp16_speedup_vs_fp32"]
+    if rt:
+        s["rt512_fp16_vs_fp32"] = rt["fp16"]["speedup_vs_fp32"]
     b = bubbles
-    s["batch"] = {"one_per_launch": sig(b["one_case_per_launch_fp32"]),
-                  "group_only": sig(b["batched_fp32_group_launches_only"]["value"]),
-                  "group_only_hbm_frac": b["batched_fp32_group_launches_only"]["hbm_frac"],
-                  "fp32": sig(b["batched_fp32_default_tiles"]["value"]),
-                  "fp32_tuned": sig(b["batched_fp32_tuned"]["value"]),
-                  "auto_tuned": sig(b["batched_auto_tuned"]["value"]),
-                  "x": [b[k]["speedup_vs_one_case_per_launch"] for k in
-                        ("batched_fp32_default_tiles", "batched_fp32_tuned", "batched_auto_tuned")]}
-    s["droplet128_5000"] = laplace
+    if b:
+        s["batch"] = {"one_per_launch": sig(b["one_case_per_launch_fp32"]),
+                      "group_only": sig(b["batched_fp32_group_launches_only"]["value"]),
+                      "group_only_hbm_frac": b["batched_fp32_group_launches_only"]["hbm_frac"],
+                      "fp32": sig(b["batched_fp32_default_tiles"]["value"]),
+                      "fp32_tuned": sig(b["batched_fp32_tuned"]["value"]),
+                      "auto_tuned": sig(b["batched_auto_tuned"]["value"]),
+                      "x": [b[k]["speedup_vs_one_case_per_launch"] for k in
+                            ("batched_fp32_default_tiles", "batched_fp32_tuned", "batched_auto_tuned")]}
+    if laplace:
+        s["droplet128_5000"] = laplace
     if rt_acc:
         s["rt_tips_2400"] = {k: sig(rt_acc[k]["tip_error_cells"], 2) for k in ("fp32", "fp16", "bf16")}
         s["rt_field_2400"] = {"fp32": [sig(rt_acc["fp32"]["max_abs_phi"], 2), sig(rt_acc["fp32"]["rel_l2_u"], 2)],
@@ -1015,6 +1025,9 @@ def main(argv=None):
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(I.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate leg")
+    ap.add_argument("--legs", default="",
+                    help="comma-separated subset of the legs beside the headline, the FD and 16-bit steps and "
+                         "e2e (default all: " + ",".join(LEGS) + "); for short profiling runs")
     ap.add_argument("--batch-cases", type=int, default=256,
                     help="rising-bubble cases of the batched leg (the first N of the seeded 256)")
     ap.add_argument("--surrogate-iters", type=int, default=1500, help="training iterations of the surrogate leg")
@@ -1025,6 +1038,10 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    unknown = [l for l in args.legs.split(",") if l] if args.legs else []
+    unknown = [l for l in unknown if l not in LEGS]
+    if unknown:
+        ap.error(f"unknown legs {unknown}; choose from {','.join(LEGS)}")
     if args.workload != WORKLOAD:
         ap.error("the benchmark line is defined on droplet3d_128 only")
     if args.impl == "reference":

@@ -99,3 +99,9 @@ def test_leg_warmup_covers_a_whole_graph_and_is_even(warmup, want):
     sys.path.insert(0, str(ROOT))
     import bench
     assert bench.leg_warmup(warmup) == want
+
+
+def test_bench_rejects_unknown_legs():
+    r = subprocess.run([sys.executable, str(ROOT / "bench.py"), "--legs", "surrogate,nope"], capture_output=True,
+                       text=True, timeout=120)
+    assert r.returncode != 0 and "unknown legs" in r.stderr
