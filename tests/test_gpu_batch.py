@@ -226,3 +226,48 @@ def test_batch_errors_and_ownership():
     batch.step(2)
     assert np.isfinite(batch.case(0).moments()[0]).all()
     batch.close()
+
+
+def test_full_batch_of_rising_bubbles_in_the_benchmarked_configuration():
+    """The 256 seeded rising-bubble cases of the batched workload at full size, FP32, in the
+    default forms and with the graph-replayed step the benchmark times (32-step graphs after a
+    whole graph of warm-up): after 36 steps every case keeps its sum phi exactly, eight sampled
+    cases (group and dedicated forms) equal their own handles advanced alone bit for bit, and
+    one more step of a sampled case matches the FP64 oracle started from the batch's state
+    (the one-step bound of the parity tests, 2e-7, scaled by the populations' size where the
+    density ratio makes them larger than 1)."""
+    cases = I.rising_bubble_cases()
+    assert len(cases) == 256
+    structs = [lbm.make_case(**{k: c[k] for k in CASE_KEYS}, storage=lbm.LBM_STORAGE_FP32) for c in cases]
+    batch = lbm.Batch(structs)
+    for k, c in enumerate(cases):
+        batch.case(k).init_phi(I.bubble_phi(c))
+    sums = [batch.case(k).mass()[0] for k in range(len(cases))]
+    batch.step(32)
+    batch.step(36)
+    assert [batch.case(k).mass()[0] for k in range(len(cases))] == sums
+    forms = set()
+    for k in range(0, 256, 32):
+        c = cases[k]
+        forms.add(batch.config(k)[2])
+        s = lbm.Lattice(c["grid"], 19, **{key: c[key] for key in CASE_KEYS[2:]})
+        s.init_phi(I.bubble_phi(c))
+        s.step(68)
+        fb, gb = batch.case(k).get_pops()
+        fs, gs = s.get_pops()
+        np.testing.assert_array_equal(fb, fs, err_msg=f"case {k} f")
+        np.testing.assert_array_equal(gb, gs, err_msg=f"case {k} g")
+        s.close()
+    assert forms == {True, False}  # both forms among the samples
+    k = 96
+    c = cases[k]
+    ref = O.Oracle(19, c["grid"], c["tau_f"], c["tau_g"], c["M"], c["xi"], c["sigma"], c["rho_ratio"], c["mu_ratio"],
+                   c["body_force"], walls=c["walls"])
+    f0, g0 = batch.case(k).get_pops()
+    ref.set_pops(f0, g0)
+    batch.case(k).step(1)
+    ref.step(1)
+    (fb, gb), (fo, go) = batch.case(k).get_pops(), ref.get_pops()
+    np.testing.assert_allclose(fb, fo, rtol=0, atol=2e-7 * max(1.0, np.abs(fo).max()))
+    np.testing.assert_allclose(gb, go, rtol=0, atol=2e-7 * max(1.0, np.abs(go).max()))
+    batch.close()
