@@ -261,14 +261,13 @@ def run_ours(args):
     fd = long_leg(1, 0, BYTES_PER_CELL["fd"])
 
     # the headline: exactly --warmup untimed steps, then exactly --steps timed steps, replayed
-    # from a CUDA graph of gs steps that the warm-up steps capture (the library captures a graph
-    # the first time it replays one from a given buffer)
-    gs = headline_graph_steps(args.warmup, args.steps)
+    # from a CUDA graph of gs steps captured and uploaded after the warm-up without running it
+    gs = headline_graph_steps(args.steps)
     g = handle(graph_steps=gs)
     m0 = g.mass()[0]
-    odd = args.warmup % 2 if gs else 0
-    g.step(odd)                # the timed steps start from buffer warmup mod 2: so does the capture
-    g.step(args.warmup - odd)
+    g.step(args.warmup)
+    if gs:
+        g.graph_prepare()      # the graph from the buffer the timed steps start from
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     barrier(world)
@@ -338,12 +337,14 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def headline_graph_steps(warmup, steps):
-    """Steps per CUDA graph of the headline handle: the largest even count, at most 32, that the
-    warm-up can replay once (so that it captures the graph) and that divides --steps; 0 (direct
-    launches) when there is none."""
-    most = min(32, warmup - warmup % 2, steps)
-    for gs in range(most - most % 2, 1, -2):
+def headline_graph_steps(steps):
+    """Steps per CUDA graph of the headline handle: the whole timed region when --steps is even
+    and at most 64, else the largest even count up to 32 that divides --steps; 0 (direct
+    launches) when there is none. The graph is captured and uploaded after the warm-up without
+    running (lbm_graph_prepare), so the timed region replays it and nothing else."""
+    if steps % 2 == 0 and 2 <= steps <= 64:
+        return steps
+    for gs in range(32, 1, -2):
         if steps % gs == 0:
             return gs
     return 0

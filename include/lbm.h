@@ -153,6 +153,13 @@ int lbm_init_fields(lbm_ctx *ctx, const double *phi0, const double *u0, const do
  * are launched directly. Both give bit-identical results. */
 int lbm_step(lbm_ctx *ctx, int n);
 
+/* Capture the step graph that lbm_step replays from the current state's buffer, if it is not
+ * captured yet, and upload it to the device, without running it: the state does not change and
+ * no launch is counted. A later lbm_step(n) with n a multiple of graph_steps from this buffer
+ * then replays it with no capture and no first-launch upload. Synchronous. LBM_EINVAL if the
+ * handle replays no graphs (graph_steps 0), LBM_ESTATE before lbm_init_phi. */
+int lbm_graph_prepare(lbm_ctx *ctx);
+
 /*
  * Macroscopic fields of the current state: phi, p and u computed from the propagated
  * populations exactly as the next step computes them before colliding (phi = sum g_i,

@@ -509,6 +509,20 @@ int lbm_init_fields(lbm_ctx* c, const double* phi0, const double* u0, const doub
     return LBM_OK;
 }
 
+int lbm_graph_prepare(lbm_ctx* c) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (c->graph_steps <= 0) return set_error(c, LBM_EINVAL, "the handle replays no graphs (graph_steps 0)");
+    if (!c->initialised) return set_error(c, LBM_ESTATE, "no state: call lbm_init_phi first");
+    if (!c->graph_exec[c->cur]) {
+        rc = capture_graph(c, c->cur);
+        if (rc) return rc;
+    }
+    LBM_CUDA(c, cudaGraphUpload(c->graph_exec[c->cur], c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
 int lbm_step(lbm_ctx* c, int n) {
     int rc = check_ctx(c);
     if (rc) return rc;

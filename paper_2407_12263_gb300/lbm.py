@@ -71,6 +71,7 @@ SIGNATURES = [
     ("lbm_init_phi", ctypes.c_int, [ctypes.c_void_p, _dp, _dp, ctypes.c_double]),
     ("lbm_init_fields", ctypes.c_int, [ctypes.c_void_p, _dp, _dp, _dp, ctypes.c_double]),
     ("lbm_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("lbm_graph_prepare", ctypes.c_int, [ctypes.c_void_p]),
     ("lbm_moments", ctypes.c_int, [ctypes.c_void_p, _dp, _dp, _dp]),
     ("lbm_gradients", ctypes.c_int, [ctypes.c_void_p, _dp, _dp]),
     ("lbm_mass", ctypes.c_int, [ctypes.c_void_p, _dp, _dp]),
@@ -410,6 +411,10 @@ class Lattice:
             lbm_init_phi(self.h, phi0, u0, p0)
         else:
             lbm_init_fields(self.h, phi0, u0, np.ascontiguousarray(p, dtype=np.float64).reshape(self.shape), p0)
+
+    def graph_prepare(self):
+        """Capture and upload the step graph for the current buffer without running it."""
+        _check(self.h, load().lbm_graph_prepare(self.h))
 
     def step(self, n=1):
         lbm_step(self.h, n)

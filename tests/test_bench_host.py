@@ -70,17 +70,17 @@ def test_bench_rejects_too_few_warmup_steps():
     assert r.returncode != 0 and "warmup" in r.stderr
 
 
-@pytest.mark.parametrize("warmup,steps,want", [(5, 20, 4), (3, 20, 2), (50, 10000, 20), (5, 7, 0), (4, 20, 4),
-                                               (3, 3, 0), (6, 30, 6), (64, 64, 32)])
-def test_headline_graph_steps(warmup, steps, want):
-    """The headline's graph length: even, at most 32, replayable once within the warm-up (so the
-    warm-up captures it) and a divisor of --steps; 0 (direct launches) when none exists."""
+@pytest.mark.parametrize("steps,want", [(20, 20), (10000, 20), (7, 0), (64, 64), (66, 22), (3, 0), (30, 30),
+                                       (2, 2), (100, 20), (4096, 32)])
+def test_headline_graph_steps(steps, want):
+    """The headline's graph length: the whole timed region when --steps is even and at most 64,
+    else the largest even divisor of --steps up to 32; 0 (direct launches) when none exists."""
     sys.path.insert(0, str(ROOT))
     import bench
-    gs = bench.headline_graph_steps(warmup, steps)
+    gs = bench.headline_graph_steps(steps)
     assert gs == want
     if gs:
-        assert gs % 2 == 0 and gs <= 32 and steps % gs == 0 and gs <= warmup - warmup % 2
+        assert gs % 2 == 0 and steps % gs == 0 and (gs <= 32 or gs == steps)
 
 
 def test_summary_rounding_keeps_significant_digits():

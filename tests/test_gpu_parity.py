@@ -357,6 +357,42 @@ def test_graph_replay_matches_direct_launches(scheme):
         np.testing.assert_array_equal(a[1], b[1])
 
 
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_prepared_graph_changes_nothing_and_replays_the_same_bits(scheme):
+    """lbm_graph_prepare captures and uploads the graph for the current buffer without running
+    it: the state and the launch count stay as they are, and the replayed steps give the bits of
+    direct launches, from either buffer."""
+    grid = (24, 20, 16)
+    phi0 = I.multi_droplet_phi(grid, seed=83, count=2, r_range=(3.0, 6.0), xi=4.0)
+    u0 = I.smooth_velocity(grid, seed=84, amplitude=0.02)
+    ref = lbm.Lattice(grid, 19, 0.8, 0.8, 0.02, 4.0, 1e-3, scheme=scheme, graph_steps=0, **GENERAL)
+    ref.init_phi(phi0, u0)
+    g = lbm.Lattice(grid, 19, 0.8, 0.8, 0.02, 4.0, 1e-3, scheme=scheme, graph_steps=20, **GENERAL)
+    g.init_phi(phi0, u0)
+    for warm in (5, 2):                  # the timed steps start from buffer 1, then buffer 1 again
+        g.step(warm)
+        ref.step(warm)
+        before = g.get_pops()
+        n0 = g.launch_count
+        g.graph_prepare()
+        g.graph_prepare()                # a second call finds the graph captured
+        assert g.launch_count == n0
+        after = g.get_pops()
+        np.testing.assert_array_equal(before[0], after[0])
+        np.testing.assert_array_equal(before[1], after[1])
+        n0 = g.launch_count
+        g.step(20)
+        ref.step(20)
+        assert g.launch_count - n0 == 20 * (1 + scheme)
+        fa, ga = g.get_pops()
+        fb, gb = ref.get_pops()
+        np.testing.assert_array_equal(fa, fb)
+        np.testing.assert_array_equal(ga, gb)
+    with pytest.raises(lbm.LBMError) as e:
+        ref.graph_prepare()              # a handle without graphs
+    assert e.value.status == lbm.LBM_EINVAL
+
+
 def test_launch_count_is_one_kernel_per_step():
     grid = (16, 16, 16)
     for scheme, per_step in ((0, 1), (1, 2)):
