@@ -168,22 +168,46 @@ __device__ __forceinline__ Axis interp_axis(int i, int f, int nc, bool wall) {
             r.b = nc - 1;
             if (r.a == r.b) r.t = 0.f;
         }
-    } else {
-        r.a = (r.a % nc + nc) % nc;
-        r.b = (r.b % nc + nc) % nc;
+    } else {  // r.a is in [-1, nc - 1] and r.b = r.a + 1: one period at most on either side
+        if (r.a < 0) r.a += nc;
+        if (r.b >= nc) r.b -= nc;
     }
     return r;
 }
 
-__device__ __forceinline__ float trilinear(const float* __restrict__ q, int ncx, int ncy, const Axis& X, const Axis& Y,
-                                           const Axis& Z) {
-    auto at = [&](int z, int y, int x) { return __ldg(q + ((long long)z * ncy + y) * ncx + x); };
+// The offsets of the eight coarse corners around a fine cell (the coarse grid holds fewer than
+// 2^31 cells), computed once for all the fields interpolated there.
+struct Corners {
+    int o[8];  // (z, y, x) in {a, b}^3, x fastest
+    float tx, ty, tz;
+};
+
+__device__ __forceinline__ Corners corners(int ncx, int ncy, const Axis& X, const Axis& Y, const Axis& Z) {
+    Corners c;
+    const int za = Z.a * ncy, zb = Z.b * ncy;
+    const int r00 = (za + Y.a) * ncx, r01 = (za + Y.b) * ncx, r10 = (zb + Y.a) * ncx, r11 = (zb + Y.b) * ncx;
+    c.o[0] = r00 + X.a;
+    c.o[1] = r00 + X.b;
+    c.o[2] = r01 + X.a;
+    c.o[3] = r01 + X.b;
+    c.o[4] = r10 + X.a;
+    c.o[5] = r10 + X.b;
+    c.o[6] = r11 + X.a;
+    c.o[7] = r11 + X.b;
+    c.tx = X.t;
+    c.ty = Y.t;
+    c.tz = Z.t;
+    return c;
+}
+
+// Trilinear interpolation of q at the corners: along x, then y, then z
+__device__ __forceinline__ float trilinear(const float* __restrict__ q, const Corners& c) {
     auto lerp = [](float u, float v, float t) { return fmaf(t, v - u, u); };
-    const float c00 = lerp(at(Z.a, Y.a, X.a), at(Z.a, Y.a, X.b), X.t);
-    const float c01 = lerp(at(Z.a, Y.b, X.a), at(Z.a, Y.b, X.b), X.t);
-    const float c10 = lerp(at(Z.b, Y.a, X.a), at(Z.b, Y.a, X.b), X.t);
-    const float c11 = lerp(at(Z.b, Y.b, X.a), at(Z.b, Y.b, X.b), X.t);
-    return lerp(lerp(c00, c01, Y.t), lerp(c10, c11, Y.t), Z.t);
+    const float c00 = lerp(__ldg(q + c.o[0]), __ldg(q + c.o[1]), c.tx);
+    const float c01 = lerp(__ldg(q + c.o[2]), __ldg(q + c.o[3]), c.tx);
+    const float c10 = lerp(__ldg(q + c.o[4]), __ldg(q + c.o[5]), c.tx);
+    const float c11 = lerp(__ldg(q + c.o[6]), __ldg(q + c.o[7]), c.tx);
+    return lerp(lerp(c00, c01, c.ty), lerp(c10, c11, c.ty), c.tz);
 }
 
 // The initial-state construction of init_kernel (equilibria of the upsampled phi, u, p plus the
@@ -198,8 +222,8 @@ __global__ void phi_fine_kernel(const Params P, const float* __restrict__ coarse
     const int z = blockIdx.z;
     if (x >= P.nx || y >= P.ny) return;
     const int ncx = P.nx / f, ncy = P.ny / f, ncz = P.nz / f;
-    const float v = trilinear(coarse, ncx, ncy, interp_axis(x, f, ncx, P.walls & 1), interp_axis(y, f, ncy, P.walls & 2),
-                              interp_axis(z, f, ncz, P.walls & 4));
+    const float v = trilinear(coarse, corners(ncx, ncy, interp_axis(x, f, ncx, P.walls & 1),
+                                              interp_axis(y, f, ncy, P.walls & 2), interp_axis(z, f, ncz, P.walls & 4)));
     phi[((long long)z * P.ny + y) * P.nx + x] = fminf(fmaxf(v, -1.0f), 1.5f);
 }
 
@@ -215,14 +239,16 @@ __global__ void restart_kernel(const Params P, const float* __restrict__ coarse,
     // neighbour rows and columns: periodic images, or across a wall the cell itself (so that
     // the normal gradient vanishes there)
     int xs[3], ys[3], zs[3];
+    // x + d lies in [-1, nx]: a periodic image is one period away at most
+    auto wrap1 = [](int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); };
 #pragma unroll
     for (int d = -1; d <= 1; ++d) {
-        xs[d + 1] = (P.walls & 1) ? min(max(x + d, 0), P.nx - 1) : (x + d + P.nx) % P.nx;
-        ys[d + 1] = (P.walls & 2) ? min(max(y + d, 0), P.ny - 1) : (y + d + P.ny) % P.ny;
-        zs[d + 1] = (P.walls & 4) ? min(max(z + d, 0), P.nz - 1) : (z + d + P.nz) % P.nz;
+        xs[d + 1] = (P.walls & 1) ? min(max(x + d, 0), P.nx - 1) : wrap1(x + d, P.nx);
+        ys[d + 1] = (P.walls & 2) ? min(max(y + d, 0), P.ny - 1) : wrap1(y + d, P.ny);
+        zs[d + 1] = (P.walls & 4) ? min(max(z + d, 0), P.nz - 1) : wrap1(z + d, P.nz);
     }
-    auto phi_at = [&](int dx, int dy, int dz) {
-        return __ldg(phi_fine + ((long long)zs[dz + 1] * P.ny + ys[dy + 1]) * P.nx + xs[dx + 1]);
+    auto phi_at = [&](int dx, int dy, int dz) {  // the grid holds fewer than 2^31 cells
+        return __ldg(phi_fine + (zs[dz + 1] * P.ny + ys[dy + 1]) * P.nx + xs[dx + 1]);
     };
     const float phi = phi_at(0, 0, 0);
     float gx = 0.f, gy = 0.f, gz = 0.f;
@@ -236,11 +262,10 @@ __global__ void restart_kernel(const Params P, const float* __restrict__ coarse,
     gx *= 3.f;
     gy *= 3.f;
     gz *= 3.f;
-    const Axis ax = interp_axis(x, f, ncx, P.walls & 1), ay = interp_axis(y, f, ncy, P.walls & 2),
-               az = interp_axis(z, f, ncz, P.walls & 4);
-    const float u[3] = {trilinear(coarse + nc, ncx, ncy, ax, ay, az), trilinear(coarse + 2 * nc, ncx, ncy, ax, ay, az),
-                        trilinear(coarse + 3 * nc, ncx, ncy, ax, ay, az)};
-    const float pc = trilinear(coarse + 4 * nc, ncx, ncy, ax, ay, az);
+    const Corners cc = corners(ncx, ncy, interp_axis(x, f, ncx, P.walls & 1), interp_axis(y, f, ncy, P.walls & 2),
+                               interp_axis(z, f, ncz, P.walls & 4));
+    const float u[3] = {trilinear(coarse + nc, cc), trilinear(coarse + 2 * nc, cc), trilinear(coarse + 3 * nc, cc)};
+    const float pc = trilinear(coarse + 4 * nc, cc);
     const float g2 = gx * gx + gy * gy + gz * gz;
     const float gn = sqrtf(g2);
     const float inv = (g2 > kNormalGuard) ? 1.0f / gn : 0.f;
