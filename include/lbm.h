@@ -194,7 +194,7 @@ int lbm_mass(lbm_ctx *ctx, double *sum_phi, double *sum_rho_phi);
  *   max_speed  sqrt of the largest (u_x^2 + u_y^2) + u_z^2 over the cells;
  *   argmax     the cell index (x fastest) of that value, the smallest index on ties;
  *   kinetic    sum over cells of rho |u|^2 / 2, rho = 1 + (rho_ratio - 1) phi, each cell's term
- *              and a thread's few cells summed in FP32 (rho and u are FP32 fields), FP64 beyond:
+ *              and runs of 8 cells summed in FP32 (rho and u are FP32 fields), the runs in FP64:
  *              within about 1e-6 relative of the same sum in FP64;
  *   p_in/n_in  mean p over, and count of, the cells whose centre (integer coordinates) lies
  *              closer than r_in to centre; p_out/n_out the same farther than r_out. The

@@ -435,7 +435,8 @@ struct DiagArgs {
 //    lanes may reach it, which after a thread's first cell is rare;
 //  * the sphere masks: FP32 decides outside a band of 1e-5 relative around r^2; a cell inside
 //    the band takes the FP64 distance and the correctly rounded square root;
-//  * the energy and pressure sums: FP32 per cell and over a thread's cells, FP64 beyond.
+//  * the energy and pressure sums: FP32 per cell and over runs of 8 of a thread's cells, each run
+//    then added to FP64 sums (one FP64 add per 8 cells whatever the grid size).
 template <int Q, int SCHEME, bool GEN, int S>
 __global__ void __launch_bounds__(kRedThreads, 2)
 diag_kernel(const Params P, const void* __restrict__ fg, const float* __restrict__ phi_fd, const DiagArgs A,
@@ -443,9 +444,11 @@ diag_kernel(const Params P, const void* __restrict__ fg, const float* __restrict
     double best = -1.0;  // FP64 u^2 of the thread's best cell
     long long arg = -1;
     float best_lo = -1.0f;  // FP32 threshold a cell's estimate must reach to be a candidate
-    float kin = 0.f, pin = 0.f, pout = 0.f;
+    float kin = 0.f, pin = 0.f, pout = 0.f;        // the current run of 8 cells
+    double kin_d = 0.0, pin_d = 0.0, pout_d = 0.0;  // the finished runs
     long long nin = 0, nout = 0;
     const unsigned lane_mask = 0xffffffffu;
+    int run = 0;  // the same in every thread of the block: the loop bounds are block-uniform
     for (long long base = (long long)blockIdx.x * kRedThreads; base < P.N; base += (long long)gridDim.x * kRedThreads) {
         const long long c = base + threadIdx.x;
         const bool valid = c < P.N;
@@ -494,8 +497,15 @@ diag_kernel(const Params P, const void* __restrict__ fg, const float* __restrict
                 }
             }
         }
+        if (++run == 8) {
+            kin_d += (double)kin;
+            pin_d += (double)pin;
+            pout_d += (double)pout;
+            kin = pin = pout = 0.f;
+            run = 0;
+        }
     }
-    DiagAcc a{best, arg, (double)kin, (double)pin, (double)pout, nin, nout};
+    DiagAcc a{best, arg, kin_d + (double)kin, pin_d + (double)pin, pout_d + (double)pout, nin, nout};
     diag_block(a);
     if (threadIdx.x == 0) partials[blockIdx.x] = a;
 }
