@@ -6,7 +6,8 @@
  * post-collision populations f* (one-fluid pressure PDF, Sec. 2.2) and g* (conservative
  * phase-field PDF, Sec. 2.3), held as (f_i, g_i) pairs in planes [Q][nz][ny][nx] with x
  * fastest, in two ping-pong copies; the moving pairs are FP32, FP16 or BF16 (lbm_storage), all
- * arithmetic is FP32. Every step is one fused stream-collide kernel launch (difference-free
+ * arithmetic is FP32. With 16-bit storage each opposite pair of populations (i, and j with
+ * e_j = -e_i) shares one plane of 8-byte words, the pair of i then that of j per cell. Every step is one fused stream-collide kernel launch (difference-free
  * scheme), or two launches for the finite-difference variant.
  *
  * Units are lattice units: dx = 1 and dt = 1 in every collision, moment and forcing

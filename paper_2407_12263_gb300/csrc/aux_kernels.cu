@@ -83,7 +83,7 @@ __global__ void init_kernel(const Params P, int z0, const double* __restrict__ p
         const float pis = sg * ((float)Lat<Q>::e2(i) - en * en - trc3);
         const float fdev = t * (dP + rho * gam - 4.5f * pis);                       // f*_i - t_i w0
         const float gdev = t * (Phi + phi * gam + P.tau_phi * es) - t * tnq * eg;  // g*_i - t_i phi_ref
-        Store<S>::store(moving_plane<S>(fg, P.N, i) + c, fdev, gdev, P);
+        Store<S>::store(pop_ptr<Q, S>(fg, P.N, i, c), fdev, gdev, P);
     }
     // plane 0: the zeroth moments sum f - w0 = p / cs^2 - w0 (FP32) and phi as the integer phi * 2^30
     moment_plane(fg)[c] = make_float2((float)(3.0 * pc - P.w0d), __int_as_float((int)llrint(phid * kPhiFx)));
@@ -243,7 +243,7 @@ mass_kernel(const Params P, const void* __restrict__ fg, double* __restrict__ pa
         bad += !isfinite(m0.x);
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
-            const float2 v = Store<S>::load(moving_plane<S>(fg, P.N, i) + c, P);
+            const float2 v = Store<S>::load(pop_ptr<Q, S>(fg, P.N, i, c), P);
             bad += !isfinite(v.x) + !isfinite(v.y);
         }
         bad_sum += bad;
@@ -603,7 +603,7 @@ __global__ void pops_to_f64(const Params P, const void* __restrict__ src, int is
         double rest = is_f ? ref + (double)m0.x : (double)__float_as_int(m0.y) / kPhiFx;
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
-            const float2 p = Store<S>::load(moving_plane<S>(src, P.N, i) + base + l, P);
+            const float2 p = Store<S>::load(pop_ptr<Q, S>(src, P.N, i, (long long)(base + l)), P);
             const double v = (double)(is_f ? p.x : p.y) + Lat<Q>::wd(i) * ref;
             dst[i * n + l] = v;
             rest -= v;
@@ -623,7 +623,7 @@ __global__ void pops_from_f64(const Params P, const double* __restrict__ src, in
         for (int i = 1; i < Q; ++i) {
             const double v = src[i * n + l];
             sum += v;
-            typename Store<S>::T* slot = moving_plane<S>(dst, P.N, i) + base + l;
+            typename Store<S>::T* slot = pop_ptr<Q, S>(dst, P.N, i, (long long)(base + l));
             float2 p = Store<S>::load(slot, P);
             const float w = (float)(v - Lat<Q>::wd(i) * ref);
             if (is_f) p.x = w;

@@ -154,8 +154,36 @@ __device__ __forceinline__ void pull(const Params& P, const void* __restrict__ s
         // x - e_i and x + e_i; for j = opposite of i they are x + e_j and x - e_j
         const unsigned im = (unsigned)(c + link_offset<Q>(nb, i, -1)), ip = (unsigned)(c + link_offset<Q>(nb, i, +1));
         typename St::Raw rmi, r0i, rpi, rmj, r0j, rpj;
-        load_link<Q, S, WALLS>(P, state, (unsigned)c, im, ip, ws, i, rmi, r0i, rpi);
-        load_link<Q, S, WALLS>(P, state, (unsigned)c, ip, im, ws, j, rmj, r0j, rpj);
+        if constexpr (St::kPaired) {
+            // one 8-byte load per stencil cell brings (i, j): at x - e_i the pair of i at
+            // x - e_i and that of j at x + e_j, at x + e_i the reverse
+            const uint2* pp = pair_plane(state, P.N, k);
+            const uint2* qm;
+            const uint2* qp;
+            if constexpr (St::kUnsignedIndex) {
+                qm = pp + im;
+                qp = pp + ip;
+            } else {
+                qm = pp + c + ((int)im - c);
+                qp = pp + c + ((int)ip - c);
+            }
+            const uint2 vm = __ldg(qm), v0 = __ldg(pp + c), vp = __ldg(qp);
+            rmi = vm.x;
+            rpj = vm.y;
+            r0i = v0.x;
+            r0j = v0.y;
+            rpi = vp.x;
+            rmj = vp.y;
+            if (WALLS) {  // half-way bounce-back: beyond a wall, the opposite pair of this cell
+                if (crosses_wall<Q>(ws, i, -1)) rmi = r0j;
+                if (crosses_wall<Q>(ws, i, +1)) rpi = r0j;
+                if (crosses_wall<Q>(ws, j, -1)) rmj = r0i;
+                if (crosses_wall<Q>(ws, j, +1)) rpj = r0i;
+            }
+        } else {
+            load_link<Q, S, WALLS>(P, state, (unsigned)c, im, ip, ws, i, rmi, r0i, rpi);
+            load_link<Q, S, WALLS>(P, state, (unsigned)c, ip, im, ws, j, rmj, r0j, rpj);
+        }
         const float2 v0i = St::cvt(r0i), v0j = St::cvt(r0j);
         // the Lax-Wendroff corrections of (f_i, g_i) and (f_j, g_j), both members at once
         // (packed FP32 arithmetic, each lane rounded as its scalar form would be)
@@ -443,7 +471,15 @@ __device__ __forceinline__ void step_cell(const Params& P, const void* __restric
     collide<Q, GEN, S>(P, m, fb, gb);
 
     // streaming stores: the output is not re-read this step
-    if constexpr (Store<S>::kUnsignedIndex) {
+    if constexpr (Store<S>::kPaired) {
+        __stcs(moment_plane(fg_out) + c, make_float2(fb[0], __int_as_float(phi_fx)));
+#pragma unroll
+        for (int k = 0; k < Lat<Q>::kPairs; ++k) {  // one 8-byte store per opposite pair
+            const int i = Lat<Q>::pair_first(k), j = Lat<Q>::pair_second(k);
+            __stcs(pair_plane(fg_out, P.N, k) + c,
+                   make_uint2(Store<S>::pack_raw(fb[i], gb[i]), Store<S>::pack_raw(fb[j], gb[j])));
+        }
+    } else if constexpr (Store<S>::kUnsignedIndex) {
         const unsigned cu = (unsigned)c;
         __stcs(moment_plane(fg_out) + cu, make_float2(fb[0], __int_as_float(phi_fx)));
 #pragma unroll

@@ -1,11 +1,15 @@
 // storage.cuh -- how the (f_i, g_i) pairs are held in device memory.
 //
 // The state buffer holds plane 0 (the zeroth moments of the shifted sets) as FP32 pairs,
-// followed by planes 1..Q-1 (the shifted moving populations) in the storage type:
-//   STORE_F32   float2 (8 bytes per pair)
+// followed by the shifted moving populations in the storage type:
+//   STORE_F32   float2 (8 bytes per pair), planes 1..Q-1 in population order
 //   STORE_F16   __half2 (4 bytes), f scaled by 2^12 and g by 2^10 before rounding, so the
 //               deviations sit in the normal FP16 range (|f - t w0| < 16, |g - t phi_ref| < 64)
 //   STORE_BF16  __nv_bfloat162 (4 bytes), no scaling (BF16 has the FP32 exponent range)
+// The 16-bit kinds interleave each opposite pair of the velocity set: pair plane k holds, per
+// cell, the pair of population pair_first(k) then that of pair_second(k) (8 bytes). The
+// Lax-Wendroff stencils of a population and its opposite read the same three cells, so one
+// 8-byte load serves both and the step issues half the loads and stores.
 // All arithmetic is FP32 in every case. Plane 0 is 8 bytes whatever the storage: sum_i f_i - w0
 // as FP32 and phi as the 32-bit integer phi * 2^30 (resolution 9.3e-10, range [-2, 2)). Each
 // step adds to it the face fluxes of g rounded to that grid one face at a time; the two cells
@@ -16,6 +20,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "lattice.cuh"
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -55,6 +60,7 @@ struct Store<STORE_F32> {
     using T = float2;
     using Raw = float2;
     static constexpr bool kUnsignedIndex = true;  // neighbour addresses from unsigned cell indices
+    static constexpr bool kPaired = false;        // planes 1..Q-1 in population order
     __device__ __forceinline__ static Raw ld(const T* p) { return __ldg(p); }
     __device__ __forceinline__ static float2 cvt(Raw r) { return r; }
     __device__ __forceinline__ static float sub_f(Raw r, float c) { return __fsub_rn(r.x, c); }
@@ -73,6 +79,7 @@ struct Store<STORE_F16> {
     using T = __half2;
     using Raw = unsigned int;
     static constexpr bool kUnsignedIndex = false;
+    static constexpr bool kPaired = true;  // opposite populations interleaved in pair planes
     __device__ __forceinline__ static Raw ld(const T* p) { return __ldg(reinterpret_cast<const unsigned int*>(p)); }
     __device__ __forceinline__ static float2 cvt(Raw r) {
         return __half22float2(*reinterpret_cast<const __half2*>(&r));
@@ -115,6 +122,7 @@ struct Store<STORE_BF16> {
     using T = __nv_bfloat162;
     using Raw = unsigned int;
     static constexpr bool kUnsignedIndex = true;
+    static constexpr bool kPaired = true;
     __device__ __forceinline__ static Raw ld(const T* p) { return __ldg(reinterpret_cast<const unsigned int*>(p)); }
     __device__ __forceinline__ static float2 cvt(Raw r) {
         return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r));
@@ -168,6 +176,40 @@ template <int S>
 __host__ __device__ __forceinline__ typename Store<S>::T* moving_plane(void* state, long long N, int i) {
     return reinterpret_cast<typename Store<S>::T*>(static_cast<char*>(state) + (size_t)N * sizeof(float2)) +
            (size_t)(i - 1) * (size_t)N;
+}
+
+// The pair plane of an opposite pair k (position of population i: pair_of, slot_of).
+template <int Q>
+__host__ __device__ constexpr int pair_of(int i) {
+    for (int k = 0; k < Lat<Q>::kPairs; ++k)
+        if (Lat<Q>::pair_first(k) == i || Lat<Q>::pair_second(k) == i) return k;
+    return -1;
+}
+template <int Q>
+__host__ __device__ constexpr int slot_of(int i) {
+    return Lat<Q>::pair_second(pair_of<Q>(i)) == i ? 1 : 0;
+}
+__host__ __device__ __forceinline__ const uint2* pair_plane(const void* state, long long N, int k) {
+    return reinterpret_cast<const uint2*>(static_cast<const char*>(state) + (size_t)N * sizeof(float2)) + (size_t)k * (size_t)N;
+}
+__host__ __device__ __forceinline__ uint2* pair_plane(void* state, long long N, int k) {
+    return reinterpret_cast<uint2*>(static_cast<char*>(state) + (size_t)N * sizeof(float2)) + (size_t)k * (size_t)N;
+}
+
+// The stored pair of population i >= 1 at cell c, in the layout of the storage kind.
+template <int Q, int S>
+__host__ __device__ __forceinline__ const typename Store<S>::T* pop_ptr(const void* state, long long N, int i, long long c) {
+    if constexpr (Store<S>::kPaired)
+        return reinterpret_cast<const typename Store<S>::T*>(pair_plane(state, N, pair_of<Q>(i)) + c) + slot_of<Q>(i);
+    else
+        return moving_plane<S>(state, N, i) + c;
+}
+template <int Q, int S>
+__host__ __device__ __forceinline__ typename Store<S>::T* pop_ptr(void* state, long long N, int i, long long c) {
+    if constexpr (Store<S>::kPaired)
+        return reinterpret_cast<typename Store<S>::T*>(pair_plane(state, N, pair_of<Q>(i)) + c) + slot_of<Q>(i);
+    else
+        return moving_plane<S>(state, N, i) + c;
 }
 
 // Bytes of one state buffer.

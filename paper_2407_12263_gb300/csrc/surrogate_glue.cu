@@ -293,7 +293,7 @@ __global__ void restart_kernel(const Params P, const float* __restrict__ coarse,
         const float fdev = t * (dP + rho * gam - 4.5f * pis);                        // f*_i - t_i w0
         const float gdev = t * (Phi + phi * gam + P.tau_phi * es) - t * tnq * eg;  // g*_i - t_i phi_ref
         fsum += fdev;
-        if (i > 0) Store<S>::store(moving_plane<S>(fg, P.N, i) + c, fdev, gdev, P);
+        if (i > 0) Store<S>::store(pop_ptr<Q, S>(fg, P.N, i, c), fdev, gdev, P);
     }
     // plane 0: sum_i f*_i - w0, and phi (= sum_i g*_i) as the integer phi * 2^30
     moment_plane(fg)[c] = make_float2(fsum, __int_as_float(__float2int_rn(phi * 1073741824.0f)));
