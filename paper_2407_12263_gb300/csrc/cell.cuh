@@ -104,35 +104,13 @@ __device__ __forceinline__ int link_offset(const Nbr& n, int i, int s) {
 // difference negated; IEEE subtraction, products and round-to-nearest are odd in sign, so it
 // gets -N bit for bit, the integers cancel in pairs and sum phi over the grid never changes.
 // At a wall the two terms of N read the same values of this cell, so N = 0 exactly.
-// im, ip: the cell indices of x - e_i and x + e_i. Indices are unsigned, so each address is one
-// wide multiply-add on the plane's (grid-uniform) base: 817 -> 776 instructions per cell for the
-// FP32 step. The FP16 step, held at 96 registers, ran slower that way (78.4 against 70.4 us per
-// 128^3 step, measured; the instruction count fell but issue did too), so its loads and stores
-// keep the addresses formed from signed offsets (Store<S>::kUnsignedIndex).
-template <int Q, int S, bool WALLS>
-__device__ __forceinline__ void load_link(const Params& P, const void* __restrict__ state, unsigned c, unsigned im,
-                                          unsigned ip, const WallSide& ws, int i, typename Store<S>::Raw& rm,
-                                          typename Store<S>::Raw& r0, typename Store<S>::Raw& rp) {
-    const typename Store<S>::T* q = moving_plane<S>(state, P.N, i);
-    const typename Store<S>::T* pm;
-    const typename Store<S>::T* pp;
-    if constexpr (Store<S>::kUnsignedIndex) {
-        pm = q + im;
-        pp = q + ip;
-    } else {
-        pm = q + (int)c + ((int)im - (int)c);
-        pp = q + (int)c + ((int)ip - (int)c);
-    }
-    if (WALLS) {
-        const typename Store<S>::T* back = moving_plane<S>(state, P.N, Lat<Q>::opp(i)) + c;
-        if (crosses_wall<Q>(ws, i, -1)) pm = back;
-        if (crosses_wall<Q>(ws, i, +1)) pp = back;
-    }
-    r0 = Store<S>::ld(q + c);
-    rm = Store<S>::ld(pm);
-    rp = Store<S>::ld(pp);
-}
-
+// Each load brings the words of an opposite pair (i, j) at one stencil cell (storage.cuh): at
+// x - e_i the pair of i there and that of j at x + e_j, at x + e_i the reverse, so 3 loads serve
+// both stencils. With walls, a stencil point beyond a wall takes the opposite pair of this cell
+// instead (half-way bounce-back), from the word loaded at x. im, ip: the cell indices of x - e_i
+// and x + e_i; with unsigned indices each address is one wide multiply-add on the plane's base
+// (the FP32 step), the 16-bit steps, held at 96 registers, form them from signed offsets
+// (Store<S>::kUnsignedIndex), which ran faster there.
 // RAW: fb[i], gb[i] (i >= 1) stay in storage units (see storage.cuh); fb[0], gb[0] are always in
 // population units. Every difference of two stored values is taken as (neighbour) - (FP32 of
 // this cell's value) with one rounding; a difference a - b in the flux is written -(b - a),
@@ -154,35 +132,30 @@ __device__ __forceinline__ void pull(const Params& P, const void* __restrict__ s
         // x - e_i and x + e_i; for j = opposite of i they are x + e_j and x - e_j
         const unsigned im = (unsigned)(c + link_offset<Q>(nb, i, -1)), ip = (unsigned)(c + link_offset<Q>(nb, i, +1));
         typename St::Raw rmi, r0i, rpi, rmj, r0j, rpj;
-        if constexpr (St::kPaired) {
-            // one 8-byte load per stencil cell brings (i, j): at x - e_i the pair of i at
-            // x - e_i and that of j at x + e_j, at x + e_i the reverse
-            const uint2* pp = pair_plane(state, P.N, k);
-            const uint2* qm;
-            const uint2* qp;
+        {
+            const typename St::Word* pw = pair_plane<S>(state, P.N, k);
+            const typename St::Word* qm;
+            const typename St::Word* qp;
             if constexpr (St::kUnsignedIndex) {
-                qm = pp + im;
-                qp = pp + ip;
+                qm = pw + im;
+                qp = pw + ip;
             } else {
-                qm = pp + c + ((int)im - c);
-                qp = pp + c + ((int)ip - c);
+                qm = pw + c + ((int)im - c);
+                qp = pw + c + ((int)ip - c);
             }
-            const uint2 vm = __ldg(qm), v0 = __ldg(pp + c), vp = __ldg(qp);
-            rmi = vm.x;
-            rpj = vm.y;
-            r0i = v0.x;
-            r0j = v0.y;
-            rpi = vp.x;
-            rmj = vp.y;
+            const typename St::Word vm = __ldg(qm), v0 = __ldg(pw + c), vp = __ldg(qp);
+            rmi = St::lo(vm);
+            rpj = St::hi(vm);
+            r0i = St::lo(v0);
+            r0j = St::hi(v0);
+            rpi = St::lo(vp);
+            rmj = St::hi(vp);
             if (WALLS) {  // half-way bounce-back: beyond a wall, the opposite pair of this cell
                 if (crosses_wall<Q>(ws, i, -1)) rmi = r0j;
                 if (crosses_wall<Q>(ws, i, +1)) rpi = r0j;
                 if (crosses_wall<Q>(ws, j, -1)) rmj = r0i;
                 if (crosses_wall<Q>(ws, j, +1)) rpj = r0i;
             }
-        } else {
-            load_link<Q, S, WALLS>(P, state, (unsigned)c, im, ip, ws, i, rmi, r0i, rpi);
-            load_link<Q, S, WALLS>(P, state, (unsigned)c, ip, im, ws, j, rmj, r0j, rpj);
         }
         const float2 v0i = St::cvt(r0i), v0j = St::cvt(r0j);
         // the Lax-Wendroff corrections of (f_i, g_i) and (f_j, g_j), both members at once
@@ -470,24 +443,12 @@ __device__ __forceinline__ void step_cell(const Params& P, const void* __restric
     macro_pressure<GEN>(P, m);
     collide<Q, GEN, S>(P, m, fb, gb);
 
-    // streaming stores: the output is not re-read this step
-    if constexpr (Store<S>::kPaired) {
-        __stcs(moment_plane(fg_out) + c, make_float2(fb[0], __int_as_float(phi_fx)));
+    // streaming stores: the output is not re-read this step; one word per opposite pair
+    __stcs(moment_plane(fg_out) + c, make_float2(fb[0], __int_as_float(phi_fx)));
 #pragma unroll
-        for (int k = 0; k < Lat<Q>::kPairs; ++k) {  // one 8-byte store per opposite pair
-            const int i = Lat<Q>::pair_first(k), j = Lat<Q>::pair_second(k);
-            __stcs(pair_plane(fg_out, P.N, k) + c,
-                   make_uint2(Store<S>::pack_raw(fb[i], gb[i]), Store<S>::pack_raw(fb[j], gb[j])));
-        }
-    } else if constexpr (Store<S>::kUnsignedIndex) {
-        const unsigned cu = (unsigned)c;
-        __stcs(moment_plane(fg_out) + cu, make_float2(fb[0], __int_as_float(phi_fx)));
-#pragma unroll
-        for (int i = 1; i < Q; ++i) Store<S>::store_raw(moving_plane<S>(fg_out, P.N, i) + cu, fb[i], gb[i]);
-    } else {
-        __stcs(moment_plane(fg_out) + c, make_float2(fb[0], __int_as_float(phi_fx)));
-#pragma unroll
-        for (int i = 1; i < Q; ++i) Store<S>::store_raw(moving_plane<S>(fg_out, P.N, i) + c, fb[i], gb[i]);
+    for (int k = 0; k < Lat<Q>::kPairs; ++k) {
+        const int i = Lat<Q>::pair_first(k), j = Lat<Q>::pair_second(k);
+        __stcs(pair_plane<S>(fg_out, P.N, k) + c, Store<S>::word(fb[i], gb[i], fb[j], gb[j]));
     }
 }
 

@@ -1,15 +1,16 @@
 // storage.cuh -- how the (f_i, g_i) pairs are held in device memory.
 //
-// The state buffer holds plane 0 (the zeroth moments of the shifted sets) as FP32 pairs,
-// followed by the shifted moving populations in the storage type:
-//   STORE_F32   float2 (8 bytes per pair), planes 1..Q-1 in population order
+// The state buffer holds plane 0 (the zeroth moments of the shifted sets) as FP32 pairs
+// (padded to a multiple of 16 bytes for FP32 storage), followed by the shifted moving populations in the storage
+// type:
+//   STORE_F32   float2 (8 bytes per pair)
 //   STORE_F16   __half2 (4 bytes), f scaled by 2^12 and g by 2^10 before rounding, so the
 //               deviations sit in the normal FP16 range (|f - t w0| < 16, |g - t phi_ref| < 64)
 //   STORE_BF16  __nv_bfloat162 (4 bytes), no scaling (BF16 has the FP32 exponent range)
-// The 16-bit kinds interleave each opposite pair of the velocity set: pair plane k holds, per
-// cell, the pair of population pair_first(k) then that of pair_second(k) (8 bytes). The
-// Lax-Wendroff stencils of a population and its opposite read the same three cells, so one
-// 8-byte load serves both and the step issues half the loads and stores.
+// Each opposite pair of the velocity set is interleaved: pair plane k holds, per cell, the pair
+// of population pair_first(k) then that of pair_second(k), one word of 16 bytes (FP32) or 8
+// (16-bit). The Lax-Wendroff stencils of a population and its opposite read the same three
+// cells, so one load serves both and the step issues half the loads and stores.
 // All arithmetic is FP32 in every case. Plane 0 is 8 bytes whatever the storage: sum_i f_i - w0
 // as FP32 and phi as the 32-bit integer phi * 2^30 (resolution 9.3e-10, range [-2, 2)). Each
 // step adds to it the face fluxes of g rounded to that grid one face at a time; the two cells
@@ -35,7 +36,8 @@ struct Store;
 // in them, the scales are powers of two (exact in FP32), so only the moments need rescaling and
 // the results are the same bits as in population units.
 //
-// Raw pair access for the propagation: ld() returns the pair as loaded, cvt() converts it to
+// Raw pair access for the propagation: lo() and hi() take the pairs of a population and its
+// opposite out of a loaded word, word() packs two for the store, cvt() converts a pair to
 // FP32, sub_f(r, c) / sub_g(r, c) return (FP32 of r's f or g) - c with one rounding, sub2 both
 // (for FP32 pairs one packed subtraction). For the
 // 16-bit types these are the mixed-precision forms of sub (a 16-bit operand widened exactly to
@@ -59,9 +61,13 @@ template <>
 struct Store<STORE_F32> {
     using T = float2;
     using Raw = float2;
+    using Word = float4;  // the pairs of a population and its opposite
     static constexpr bool kUnsignedIndex = true;  // neighbour addresses from unsigned cell indices
-    static constexpr bool kPaired = false;        // planes 1..Q-1 in population order
-    __device__ __forceinline__ static Raw ld(const T* p) { return __ldg(p); }
+    __device__ __forceinline__ static Raw lo(Word w) { return make_float2(w.x, w.y); }
+    __device__ __forceinline__ static Raw hi(Word w) { return make_float2(w.z, w.w); }
+    __device__ __forceinline__ static Word word(float fi, float gi, float fj, float gj) {
+        return make_float4(fi, gi, fj, gj);
+    }
     __device__ __forceinline__ static float2 cvt(Raw r) { return r; }
     __device__ __forceinline__ static float sub_f(Raw r, float c) { return __fsub_rn(r.x, c); }
     __device__ __forceinline__ static float sub_g(Raw r, float c) { return __fsub_rn(r.y, c); }
@@ -78,9 +84,10 @@ template <>
 struct Store<STORE_F16> {
     using T = __half2;
     using Raw = unsigned int;
+    using Word = uint2;
     static constexpr bool kUnsignedIndex = false;
-    static constexpr bool kPaired = true;  // opposite populations interleaved in pair planes
-    __device__ __forceinline__ static Raw ld(const T* p) { return __ldg(reinterpret_cast<const unsigned int*>(p)); }
+    __device__ __forceinline__ static Raw lo(Word w) { return w.x; }
+    __device__ __forceinline__ static Raw hi(Word w) { return w.y; }
     __device__ __forceinline__ static float2 cvt(Raw r) {
         return __half22float2(*reinterpret_cast<const __half2*>(&r));
     }
@@ -115,15 +122,19 @@ struct Store<STORE_F16> {
     __device__ __forceinline__ static void store_raw(T* p, float f, float g) {
         __stcs(reinterpret_cast<unsigned int*>(p), pack_raw(f, g));
     }
+    __device__ __forceinline__ static Word word(float fi, float gi, float fj, float gj) {
+        return make_uint2(pack_raw(fi, gi), pack_raw(fj, gj));
+    }
 };
 
 template <>
 struct Store<STORE_BF16> {
     using T = __nv_bfloat162;
     using Raw = unsigned int;
+    using Word = uint2;
     static constexpr bool kUnsignedIndex = true;
-    static constexpr bool kPaired = true;
-    __device__ __forceinline__ static Raw ld(const T* p) { return __ldg(reinterpret_cast<const unsigned int*>(p)); }
+    __device__ __forceinline__ static Raw lo(Word w) { return w.x; }
+    __device__ __forceinline__ static Raw hi(Word w) { return w.y; }
     __device__ __forceinline__ static float2 cvt(Raw r) {
         return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r));
     }
@@ -152,6 +163,9 @@ struct Store<STORE_BF16> {
     __device__ __forceinline__ static void store_raw(T* p, float f, float g) {
         __stcs(reinterpret_cast<unsigned int*>(p), pack_raw(f, g));
     }
+    __device__ __forceinline__ static Word word(float fi, float gi, float fj, float gj) {
+        return make_uint2(pack_raw(fi, gi), pack_raw(fj, gj));
+    }
 };
 
 // kInvG of a storage kind, for host code.
@@ -167,15 +181,13 @@ __host__ __device__ __forceinline__ const float2* moment_plane(const void* state
 }
 __host__ __device__ __forceinline__ float2* moment_plane(void* state) { return static_cast<float2*>(state); }
 
+// Bytes before the moving planes: plane 0, padded to a multiple of 16 for FP32 storage (its pair
+// words are 16-byte loads). The 16-bit words need 8, which plane 0 always is; padding their offset
+// too cost the 16-bit steps (held at 96 registers) spills and 2% of their rate (measured).
 template <int S>
-__host__ __device__ __forceinline__ const typename Store<S>::T* moving_plane(const void* state, long long N, int i) {
-    return reinterpret_cast<const typename Store<S>::T*>(static_cast<const char*>(state) + (size_t)N * sizeof(float2)) +
-           (size_t)(i - 1) * (size_t)N;
-}
-template <int S>
-__host__ __device__ __forceinline__ typename Store<S>::T* moving_plane(void* state, long long N, int i) {
-    return reinterpret_cast<typename Store<S>::T*>(static_cast<char*>(state) + (size_t)N * sizeof(float2)) +
-           (size_t)(i - 1) * (size_t)N;
+__host__ __device__ __forceinline__ size_t moving_offset(long long N) {
+    if constexpr (S == STORE_F32) return ((size_t)N * sizeof(float2) + 15) & ~(size_t)15;
+    else return (size_t)N * sizeof(float2);
 }
 
 // The pair plane of an opposite pair k (position of population i: pair_of, slot_of).
@@ -189,33 +201,30 @@ template <int Q>
 __host__ __device__ constexpr int slot_of(int i) {
     return Lat<Q>::pair_second(pair_of<Q>(i)) == i ? 1 : 0;
 }
-__host__ __device__ __forceinline__ const uint2* pair_plane(const void* state, long long N, int k) {
-    return reinterpret_cast<const uint2*>(static_cast<const char*>(state) + (size_t)N * sizeof(float2)) + (size_t)k * (size_t)N;
+template <int S>
+__host__ __device__ __forceinline__ const typename Store<S>::Word* pair_plane(const void* state, long long N, int k) {
+    return reinterpret_cast<const typename Store<S>::Word*>(static_cast<const char*>(state) + moving_offset<S>(N)) +
+           (size_t)k * (size_t)N;
 }
-__host__ __device__ __forceinline__ uint2* pair_plane(void* state, long long N, int k) {
-    return reinterpret_cast<uint2*>(static_cast<char*>(state) + (size_t)N * sizeof(float2)) + (size_t)k * (size_t)N;
+template <int S>
+__host__ __device__ __forceinline__ typename Store<S>::Word* pair_plane(void* state, long long N, int k) {
+    return reinterpret_cast<typename Store<S>::Word*>(static_cast<char*>(state) + moving_offset<S>(N)) + (size_t)k * (size_t)N;
 }
 
-// The stored pair of population i >= 1 at cell c, in the layout of the storage kind.
+// The stored pair of population i >= 1 at cell c.
 template <int Q, int S>
 __host__ __device__ __forceinline__ const typename Store<S>::T* pop_ptr(const void* state, long long N, int i, long long c) {
-    if constexpr (Store<S>::kPaired)
-        return reinterpret_cast<const typename Store<S>::T*>(pair_plane(state, N, pair_of<Q>(i)) + c) + slot_of<Q>(i);
-    else
-        return moving_plane<S>(state, N, i) + c;
+    return reinterpret_cast<const typename Store<S>::T*>(pair_plane<S>(state, N, pair_of<Q>(i)) + c) + slot_of<Q>(i);
 }
 template <int Q, int S>
 __host__ __device__ __forceinline__ typename Store<S>::T* pop_ptr(void* state, long long N, int i, long long c) {
-    if constexpr (Store<S>::kPaired)
-        return reinterpret_cast<typename Store<S>::T*>(pair_plane(state, N, pair_of<Q>(i)) + c) + slot_of<Q>(i);
-    else
-        return moving_plane<S>(state, N, i) + c;
+    return reinterpret_cast<typename Store<S>::T*>(pair_plane<S>(state, N, pair_of<Q>(i)) + c) + slot_of<Q>(i);
 }
 
 // Bytes of one state buffer.
 inline size_t state_bytes(int Q, long long N, int storage) {
-    const size_t pair = (storage == STORE_F32) ? sizeof(float2) : 4;
-    return (size_t)N * sizeof(float2) + (size_t)(Q - 1) * (size_t)N * pair;
+    if (storage == STORE_F32) return moving_offset<STORE_F32>(N) + (size_t)(Q - 1) * (size_t)N * sizeof(float2);
+    return moving_offset<STORE_F16>(N) + (size_t)(Q - 1) * (size_t)N * 4;
 }
 
 }  // namespace lbm

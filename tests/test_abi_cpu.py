@@ -207,13 +207,16 @@ def test_rising_bubble_recipe_matches_its_groups():
         assert np.sqrt(g * D) == pytest.approx(c["U"], rel=1e-12) and 0.04 <= c["U"] <= 0.1
 
 
-@pytest.mark.parametrize("Q,grid,storage,per_cell", [
-    (19, (128, 128, 128), 0, 8 + 18 * 8), (19, (37, 21, 19), 1, 8 + 18 * 4), (19, (8, 8, 8), 2, 8 + 18 * 4),
-    (9, (64, 64, 1), 0, 8 + 8 * 8), (9, (45, 39, 1), 1, 8 + 8 * 4),
+@pytest.mark.parametrize("Q,grid,storage,pair", [
+    (19, (128, 128, 128), 0, 8), (19, (37, 21, 19), 1, 4), (19, (8, 8, 8), 2, 4), (19, (9, 7, 5), 0, 8), (19, (9, 7, 5), 1, 4),
+    (9, (64, 64, 1), 0, 8), (9, (45, 39, 1), 1, 4),
 ])
-def test_state_bytes_is_the_documented_layout(lib, Q, grid, storage, per_cell):
-    """8 B of zeroth moments plus Q - 1 moving pairs of 8 B (FP32) or 4 B (16-bit) per cell."""
-    assert lbm.lbm_state_bytes(Q, grid, storage) == per_cell * grid[0] * grid[1] * grid[2]
+def test_state_bytes_is_the_documented_layout(lib, Q, grid, storage, pair):
+    """8 B of zeroth moments per cell (padded to a multiple of 16 B for FP32 storage) plus Q - 1
+    moving pairs of 8 B (FP32) or 4 B (16-bit) per cell."""
+    n = grid[0] * grid[1] * grid[2]
+    moments = (8 * n + 15) // 16 * 16 if storage == 0 else 8 * n
+    assert lbm.lbm_state_bytes(Q, grid, storage) == moments + (Q - 1) * pair * n
 
 
 def test_state_bytes_rejects_invalid_arguments(lib):
