@@ -2,13 +2,16 @@
 // (Zhao, Patel & Lee, arXiv:2407.12263) and its finite-difference twin.
 //
 // Difference-free step: ONE kernel per time step. Each thread owns one cell; it pulls the
-// Lax-Wendroff-propagated f and g (three 8-byte loads of the (f_i, g_i) pair per moving
-// population, Sec. 2.2), computes phi, rho, u, the central moment K1, n, S, grad phi and p in
-// registers (Sec. 2.3), collides both sets (Eqs. c-n_m and c-n_c) and streams the Q
-// post-collision pairs out. The neighbour loads of adjacent threads overlap, so DRAM sees each
-// stored value about once per step; everything else is L1/L2 reuse. Interleaving f and g halves
-// the memory instructions per cell, and that count (not bytes) is what limits a 3-point stencil
-// over 38 planes: with separate planes the same step ran at 74% of the HBM copy bandwidth.
+// Lax-Wendroff-propagated f and g (Sec. 2.2: for each opposite pair of populations, three loads
+// of the word that holds both (f, g) pairs, at x - e_i, x and x + e_i), computes phi, rho, u,
+// the central moment K1, n, S, grad phi and p in registers (Sec. 2.3), collides both sets
+// (Eqs. c-n_m and c-n_c) and streams the Q post-collision pairs out, one word per opposite
+// pair. The neighbour loads of adjacent threads overlap, so DRAM sees each stored value about
+// once per step; everything else is L1/L2 reuse. Interleaving f with g, and a population with
+// its opposite, divides the memory instructions per cell by four, and that count (not bytes) is
+// what limits a 3-point stencil over 38 planes: with separate planes the same step ran at 74%
+// of the HBM copy bandwidth, with (f, g) pairs at 0.98, with opposite pairs interleaved too at
+// the copy bandwidth.
 //
 // Finite-difference variant (the "previous method" of Sec. 3.4): a first kernel propagates g
 // and writes the phi plane; the second is the fused step with grad phi taken from the
