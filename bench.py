@@ -135,10 +135,38 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- profile summary (traffic)
+def strip_comments(src: str) -> str:
+    """C/C++/CUDA source without its comments, whitespace runs collapsed to one space; string
+    and character literals are kept as written."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            out.append(" ")
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_source_hash() -> str:
+    """SHA-256 (first 16 hex digits) of the step kernel's sources with their comments removed:
+    a change of code invalidates a profile taken before it, a change of comments does not."""
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES:
-        h.update((ROOT / rel).read_bytes())
+        h.update(strip_comments((ROOT / rel).read_text()).encode())
+        h.update(b"\0")
     return h.hexdigest()[:16]
 
 

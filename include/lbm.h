@@ -4,12 +4,13 @@
  *
  * One handle owns one periodic lattice (D2Q9 or D3Q19) and its device state: the
  * post-collision populations f* (one-fluid pressure PDF, Sec. 2.2) and g* (conservative
- * phase-field PDF, Sec. 2.3), held as (f_i, g_i) pairs in planes [Q][nz][ny][nx] with x
- * fastest, in two ping-pong copies; the moving pairs are FP32, FP16 or BF16 (lbm_storage), all
- * arithmetic is FP32. Each opposite pair of populations (i, and j with e_j = -e_i) shares one
- * plane of words, the pair of i then that of j per cell (16 B for FP32, 8 B for 16-bit), after
- * the zeroth-moment plane (padded to a multiple of 16 B for FP32). Every step is one fused stream-collide kernel launch (difference-free
- * scheme), or two launches for the finite-difference variant.
+ * phase-field PDF, Sec. 2.3), held as (f_i, g_i) pairs with x fastest, in two ping-pong
+ * copies; the moving pairs are FP32, FP16 or BF16 (lbm_storage), all arithmetic is FP32. A
+ * state buffer holds the zeroth-moment plane (8 B per cell, padded to a multiple of 16 B for
+ * FP32 storage), then one plane of words [nz][ny][nx] per opposite pair of populations (i, and
+ * j with e_j = -e_i): per cell the pair of i then that of j, 16 B for FP32, 8 B for 16-bit.
+ * Every step is one fused stream-collide kernel launch (difference-free scheme), or two
+ * launches for the finite-difference variant.
  *
  * Units are lattice units: dx = 1 and dt = 1 in every collision, moment and forcing
  * formula; the Courant number only enters the Lax-Wendroff propagation (Sec. 2.2).
@@ -109,8 +110,9 @@ int lbm_create(lbm_ctx **out, const int grid[3], int lattice, double tau_f, doub
                const double body_force[3], const lbm_opts *opts);
 
 /* Bytes of one state buffer (a handle holds two) for this lattice, grid and storage: 8 B per
- * cell for the zeroth moments (padded to a multiple of 16 B for FP32 storage), plus Q - 1 moving (f, g) pairs of
- * 8 B (FP32) or 4 B (FP16, BF16) per cell. Host-only; 0 for invalid arguments. */
+ * cell for the zeroth moments (padded to a multiple of 16 B for FP32 storage), plus Q - 1
+ * moving (f, g) pairs of 8 B (FP32) or 4 B (FP16, BF16) per cell. Host-only; 0 for invalid
+ * arguments. */
 long long lbm_state_bytes(int lattice, const int grid[3], int storage);
 
 /*

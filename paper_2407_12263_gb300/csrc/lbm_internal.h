@@ -43,12 +43,13 @@ struct Params {
 enum Scheme { SCHEME_DF = 0, SCHEME_FD = 1 };
 enum StorageKind { STORE_F32 = 0, STORE_F16 = 1, STORE_BF16 = 2 };
 
-// Launchers (return the launch's cudaError_t). The state is one buffer of Q planes of N (f, g)
-// pairs: plane i >= 1 holds (f_i - t_i w0, g_i - t_i phi_ref) in the storage type (FP32, FP16
-// or BF16, see storage.cuh); plane 0 holds the zeroth moments, sum_i f_i - w0 as FP32 and
-// phi = sum_i g_i as a 32-bit fixed-point integer phi * 2^30, in place of the rest populations,
-// which they determine exactly. f_i and g_i share their propagation stencil, so one load
-// serves both.
+// Launchers (return the launch's cudaError_t). The state is one buffer (storage.cuh): plane 0
+// holds the zeroth moments, sum_i f_i - w0 as FP32 and phi = sum_i g_i as a 32-bit fixed-point
+// integer phi * 2^30, in place of the rest populations, which they determine exactly; then one
+// plane of words per opposite pair of moving populations (i, j), each word the pairs
+// (f_i - t_i w0, g_i - t_i phi_ref) and (f_j - t_j w0, g_j - t_j phi_ref) of one cell in the
+// storage type (FP32, FP16 or BF16). f_i and g_i share their propagation stencil, and so do a
+// population and its opposite, so one load serves all four values.
 cudaError_t launch_step(const Params& P, int scheme, const void* fg_in, void* fg_out, float* phi_fd,
                         cudaStream_t s, int* launches);
 cudaError_t launch_fd_phi(const Params& P, const void* fg_in, float* phi_fd, cudaStream_t s);

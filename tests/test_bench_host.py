@@ -105,3 +105,15 @@ def test_bench_rejects_unknown_legs():
     r = subprocess.run([sys.executable, str(ROOT / "bench.py"), "--legs", "surrogate,nope"], capture_output=True,
                        text=True, timeout=120)
     assert r.returncode != 0 and "unknown legs" in r.stderr
+
+
+def test_kernel_hash_ignores_comments_and_whitespace_but_not_code():
+    """The profile's source hash: comments and whitespace runs do not change the stripped text,
+    code and string literals do."""
+    sys.path.insert(0, str(ROOT))
+    import bench
+    a = bench.strip_comments('int a = 1; // one\n/* two\n lines */ float b = "//x";')
+    assert a == 'int a = 1; float b = "//x";'
+    assert bench.strip_comments("int  a =\n 1;") == bench.strip_comments("int a = 1; /* c */")
+    assert bench.strip_comments("int a = 1;") != bench.strip_comments("int a = 2;")
+    assert bench.strip_comments("x = '/'; // c") == "x = '/';"
