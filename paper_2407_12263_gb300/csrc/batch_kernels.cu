@@ -12,8 +12,19 @@
 
 namespace lbm {
 
+// Register budget: 5 blocks (96 registers) per SM for the general kernels (walls, forces,
+// density ratio), 4 (128) for the periodic ones. The wall-bounded boxes batches hold keep a
+// group launch waiting on DRAM latency at 16 warps per SM; at 20 the FP32 group launches of
+// 256 rising-bubble cases ran 4.7% faster (15.94 -> 16.69 G cell/s) although the FP32 kernel
+// spills 16 bytes there, and the 16-bit ones fit without spilling. The periodic 16-bit kernels
+// would spill 8 to 16 bytes at 96.
+template <bool GEN, int S>
+constexpr int batch_min_blocks() {
+    return GEN ? 5 : 4;
+}
+
 template <int Q, bool GEN, int S>
-__global__ void __launch_bounds__(kBatchThreads, 4)
+__global__ void __launch_bounds__(kBatchThreads, (batch_min_blocks<GEN, S>()))
 batch_step_kernel(const __grid_constant__ BatchLaunch L) {
     const LaunchCase& C = L.cases[blockIdx.y];
     // The host groups cases that share every parameter except their fluid properties (see
